@@ -1,0 +1,411 @@
+"""Pins for the CPU oracle: each check compares it with something other than
+itself -- a closed form, a symmetry, an invariant, a convergence order, or a
+consistency relation between two independently written functions (a force
+against the derivative of a potential) -- chosen so that a dropped term, a
+wrong sign, index or exponent anywhere in the oracle fails at least one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1003_3896_gb300 import ics
+
+
+def _params(orc, **kw):
+    return orc.Params(**kw)
+
+
+# ---------------------------------------------------------------- force sum
+
+def test_two_body_closed_form(orc):
+    """N = 2: a_1 = G m_2 r_12 / (r^2 + eps^2)^{3/2} and a_2 = -(m_1/m_2) a_1
+    (eq. 1 with r_ij = r_j - r_i, softened as in eq. 5)."""
+    rng = np.random.default_rng(1)
+    for eps in (0.0, 0.3):
+        pos = rng.normal(size=(2, 3))
+        m = np.array([0.7, 2.9])
+        G = 1.7
+        a = orc.accel_int(pos, m, G, eps)
+        r = pos[1] - pos[0]
+        d2 = r @ r + eps * eps
+        want = G * m[1] * r / d2 ** 1.5
+        np.testing.assert_allclose(a[0], want, rtol=1e-14)
+        np.testing.assert_allclose(a[1], -m[0] * want / m[1], rtol=1e-14)
+
+
+@pytest.mark.parametrize("n,eps", [(3, 0.0), (7, 0.0), (12, 0.05), (64, 0.2)])
+def test_ring_closed_form(orc, n, eps):
+    """n equal masses on a tilted circle of radius R: by symmetry every
+    acceleration points to the centre, with magnitude
+    G m sum_k 2R sin^2(pi k/n) / ((2R sin(pi k/n))^2 + eps^2)^{3/2}
+    (chord length 2R sin(pi k/n), radial projection of the chord 2R sin^2)."""
+    R, m, G = 1.3, 0.25, 1.0
+    th = 2 * math.pi * np.arange(n) / n
+    ring = np.stack([R * np.cos(th), R * np.sin(th), np.zeros(n)], axis=1)
+    # rotate into a generic orientation and shift away from the origin
+    q, _ = np.linalg.qr(np.random.default_rng(5).normal(size=(3, 3)))
+    centre = np.array([3.0, -1.0, 2.0])
+    pos = ring @ q.T + centre
+    a = orc.accel_int(pos, np.full(n, m), G, eps)
+    k = np.arange(1, n)
+    s = np.sin(math.pi * k / n)
+    mag = G * m * np.sum(2 * R * s * s / ((2 * R * s) ** 2 + eps * eps) ** 1.5)
+    inward = (centre - pos) / R
+    np.testing.assert_allclose(a, mag * inward, rtol=1e-13, atol=1e-13 * mag)
+
+
+def test_cube_centre_zero_and_outside(orc):
+    """Symmetric shells: zero acceleration at the centre of a cube of masses;
+    on the cube's diagonal far away the field tends to G M / d^2."""
+    c = np.array([[x, y, z] for x in (-1, 1) for y in (-1, 1) for z in (-1, 1)], float)
+    pos = np.vstack([c, np.zeros((1, 3))])
+    m = np.full(9, 0.5)
+    a = orc.accel_int(pos, m, 1.0, 0.01)
+    assert np.abs(a[8]).max() < 1e-15
+    d = 1e4
+    probe = np.vstack([c, [[d, 0.0, 0.0]]])
+    m2 = np.append(np.full(8, 0.5), 1e-9)
+    a = orc.accel_int(probe, m2, 1.0, 0.0)
+    np.testing.assert_allclose(a[8], [-4.0 / d ** 2, 0, 0], rtol=1e-6, atol=1e-20)
+
+
+def test_momentum_and_torque_free(orc):
+    """Antisymmetry F_ij = -F_ji (Sect. 2): sum m_i a_i = 0 and
+    sum m_i r_i x a_i = 0, with unequal masses (a sum over m_i instead of m_j
+    breaks both)."""
+    rng = np.random.default_rng(2)
+    n = 200
+    pos = rng.normal(size=(n, 3)) + np.array([50.0, 0, 0])
+    m = rng.uniform(0.1, 3.0, n)
+    a = orc.accel_int(pos, m, 1.0, 0.01)
+    f = m[:, None] * a
+    scale = np.abs(f).sum()
+    assert np.abs(f.sum(0)).max() < 1e-14 * scale
+    tq = np.cross(pos, f).sum(0)
+    assert np.abs(tq).max() < 1e-13 * np.abs(np.cross(pos, f)).sum()
+
+
+def test_translation_rotation_scaling(orc):
+    """a(r + c) = a(r); a(Q r) = Q a(r); a(l r; l eps) = a(r; eps) / l^2;
+    a linear in G and in the masses."""
+    rng = np.random.default_rng(3)
+    n = 50
+    pos = rng.normal(size=(n, 3))
+    m = rng.uniform(0.5, 2, n)
+    a = orc.accel_int(pos, m, 1.0, 0.05)
+    np.testing.assert_allclose(orc.accel_int(pos + [7.0, -3.0, 1.0], m, 1.0, 0.05), a,
+                               rtol=1e-11, atol=1e-12 * np.abs(a).max())
+    q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    np.testing.assert_allclose(orc.accel_int(pos @ q.T, m, 1.0, 0.05), a @ q.T,
+                               rtol=1e-11, atol=1e-12 * np.abs(a).max())
+    lam = 3.0
+    np.testing.assert_allclose(orc.accel_int(lam * pos, m, 1.0, lam * 0.05), a / lam ** 2,
+                               rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(orc.accel_int(pos, 2 * m, 3.0, 0.05), 6 * a, rtol=1e-14)
+
+
+def test_self_term_skipped_unsoftened(orc):
+    """eps = 0 needs the j != i exclusion of eq. 2; the result is finite."""
+    pos = np.array([[0.0, 0, 0], [2.0, 0, 0], [0, 3.0, 0]])
+    a = orc.accel_int(pos, np.ones(3), 1.0, 0.0)
+    assert np.isfinite(a).all()
+    np.testing.assert_allclose(a[0], [1 / 4, 1 / 9, 0], rtol=1e-15)
+
+
+def test_force_is_minus_gradient_of_pair_potential(orc):
+    """Eq. 4 and eq. 5 written independently (energy routine vs force
+    routine): dW/dr_i = -m_i a_i, central finite differences."""
+    rng = np.random.default_rng(4)
+    n = 12
+    pos = rng.normal(size=(n, 3))
+    vel = np.zeros((n, 3))
+    m = rng.uniform(0.5, 2, n)
+    p = _params(orc, G=1.3, eps=0.1)
+    a = orc.accel_int(pos, m, 1.3, 0.1)
+    h = 1e-5
+    for i in (0, 5, 11):
+        for k in range(3):
+            pp = pos.copy(); pp[i, k] += h
+            pm = pos.copy(); pm[i, k] -= h
+            dW = (orc.energy(pp, vel, m, p).W - orc.energy(pm, vel, m, p).W) / (2 * h)
+            assert abs(dW + m[i] * a[i, k]) < 1e-7 * max(1.0, abs(m[i] * a[i, k]))
+
+
+def test_plummer_mean_field(orc):
+    """Large sampled Plummer sphere: the mean radial acceleration at radius r
+    approaches the analytic -G M r / (r^2 + a^2)^{3/2} (statistical pin on
+    exponent and sign of the whole sum)."""
+    n = 12000
+    pos, vel, m = ics.plummer(n, seed=11)
+    a = orc.accel_int(pos, m, 1.0, 0.01)
+    r = np.linalg.norm(pos, axis=1)
+    ar = (a * pos).sum(1) / r
+    want = -r / (r * r + 1.0) ** 1.5
+    for lo, hi in [(0.5, 0.8), (0.8, 1.2), (1.2, 2.0), (2.0, 4.0)]:
+        sel = (r > lo) & (r < hi)
+        rel = np.mean(ar[sel] - want[sel]) / np.mean(np.abs(want[sel]))
+        assert abs(rel) < 0.04, (lo, hi, rel)
+
+
+# ----------------------------------------------------------- external field
+
+def _fd_grad(orc, p, x, h=2e-4):
+    """Fourth-order central differences (truncation ~ (h / b_d)^4)."""
+    g = np.zeros(3)
+    for k in range(3):
+        f = []
+        for s in (-2, -1, 1, 2):
+            y = x.copy(); y[k] += s * h
+            f.append(orc.ext_phi(p, y))
+        g[k] = (f[0] - 8 * f[1] + 8 * f[2] - f[3]) / (12 * h)
+    return g
+
+
+def test_ext_accel_is_minus_grad_phi(orc):
+    """F_ext = grad U_ext = -grad Phi (eq. 3): the closed-form acceleration
+    against central differences of the independently written potential."""
+    p = _params(orc, ext_on=True)
+    rng = np.random.default_rng(6)
+    pts = np.vstack([[50.0, 0, 0], [49.2, 1.1, 0.3], [0.5, -0.2, 0.05],
+                     rng.normal(scale=10, size=(6, 3))])
+    for x in pts:
+        a = orc.ext_accel(p, x)[0]
+        g = _fd_grad(orc, p, x)
+        np.testing.assert_allclose(a, -g, rtol=1e-7, atol=1e-9 * np.abs(a).max())
+
+
+def test_ext_phi_limits(orc):
+    """Miyamoto-Nagai with a_d = 0 is a Plummer sphere of scale b_d; far away
+    the model tends to a point mass M_d + M_b; at the bulge centre the bulge
+    potential is -G M_b / a_b."""
+    x = np.array([0.3, -0.7, 0.4])
+    p = _params(orc, ext_on=True, Md=2.0, ad=0.0, bd=0.8, Mb=0.0, ab=1.0)
+    assert abs(orc.ext_phi(p, x) + 2.0 / math.sqrt(x @ x + 0.64)) < 1e-15
+    p = _params(orc, ext_on=True)
+    far = np.array([3e5, 1e5, -2e5])
+    r = np.linalg.norm(far)
+    assert abs(orc.ext_phi(p, far) * r / -115.0 - 1) < 1e-4
+    p = _params(orc, ext_on=True, Md=0.0)
+    assert abs(orc.ext_phi(p, np.zeros(3)) + 15.0 / 0.7) < 1e-14
+
+
+def test_ext_symmetries(orc):
+    """Axisymmetric about z and mirror-symmetric in z."""
+    p = _params(orc, ext_on=True)
+    x = np.array([12.0, 5.0, 0.7])
+    a = orc.ext_accel(p, x)[0]
+    c, s = math.cos(0.9), math.sin(0.9)
+    Rz = np.array([[c, -s, 0], [s, c, 0], [0, 0, 1]])
+    np.testing.assert_allclose(orc.ext_accel(p, Rz @ x)[0], Rz @ a, rtol=1e-13, atol=1e-16)
+    xm = x * [1, 1, -1]
+    np.testing.assert_allclose(orc.ext_accel(p, xm)[0], a * [1, 1, -1], rtol=1e-14)
+
+
+def test_circular_speed_constant(orc):
+    """VC_R50 (input module constant) equals sqrt(R |a_R|) at R = 50, z = 0."""
+    p = _params(orc, ext_on=True)
+    a = orc.ext_accel(p, np.array([50.0, 0, 0]))[0]
+    assert abs(math.sqrt(50.0 * -a[0]) / ics.VC_R50 - 1) < 1e-14
+
+
+def test_circular_orbit_stays_circular(orc):
+    """A test particle started at R = 50 with v_c on the sixth-order scheme
+    keeps |R - 50| < 1e-9 over one full orbital period."""
+    p = _params(orc, ext_on=True, eps=0.01)
+    pos = np.array([[50.0, 0, 0]])
+    vel = np.array([[0.0, ics.VC_R50, 0]])
+    period = 2 * math.pi * 50 / ics.VC_R50
+    steps = 400
+    x, v = orc.run(pos, vel, [1.0], p, 6, period / steps, steps)
+    R = np.hypot(x[0, 0], x[0, 1])
+    assert abs(R - 50.0) < 1e-9
+    assert np.linalg.norm(x[0] - pos[0]) < 1e-6
+
+
+# ------------------------------------------------------------- integrators
+
+def _kepler_closed_form(pos0, vel0, m, t):
+    """Textbook two-body solution: Kepler's equation E - e sin E = n t by
+    Newton's method, starting from pericentre on +x with motion in +y."""
+    mu = m.sum()
+    rel0 = pos0[1] - pos0[0]
+    vrel0 = vel0[1] - vel0[0]
+    rp = np.linalg.norm(rel0)
+    vp = np.linalg.norm(vrel0)
+    a = 1.0 / (2.0 / rp - vp * vp / mu)
+    e = 1.0 - rp / a
+    nmot = math.sqrt(mu / a ** 3)
+    M = nmot * t
+    E = M if e < 0.8 else math.pi
+    for _ in range(60):
+        E -= (E - e * math.sin(E) - M) / (1 - e * math.cos(E))
+    rel = np.array([a * (math.cos(E) - e), a * math.sqrt(1 - e * e) * math.sin(E), 0.0])
+    return np.stack([-(m[1] / mu) * rel, (m[0] / mu) * rel])
+
+
+def _kepler_error(orc, order, nsteps, periods=1.0):
+    pos, vel, m = ics.kepler_pair(0.6, 0.4, 1.0, 0.5)
+    T = 2 * math.pi * periods
+    x, _ = orc.run(pos, vel, m, _params(orc, eps=0.0), order, T / nsteps, nsteps)
+    return np.abs(x - _kepler_closed_form(pos, vel, m, T)).max()
+
+
+def test_kepler_leapfrog_second_order(orc):
+    e1 = _kepler_error(orc, 2, 2000)
+    e2 = _kepler_error(orc, 2, 4000)
+    assert e1 < 1e-3
+    assert 3.7 < e1 / e2 < 4.3, e1 / e2
+
+
+def test_kepler_sixth_order(orc):
+    """Order 6: halving dt divides the error by ~64 (a wrong SI6A weight or
+    a reversed sequence gives 4th order or worse)."""
+    e1 = _kepler_error(orc, 6, 200)
+    e2 = _kepler_error(orc, 6, 400)
+    assert e1 < 1e-6
+    assert 50 < e1 / e2 < 80, (e1, e2, e1 / e2)
+
+
+def test_si6a_weights_consistency(orc):
+    w = orc.si6a_weights()
+    assert abs(w[0] + 2 * (w[1] + w[2] + w[3]) - 1) < 1e-15
+    # third-order condition of a symmetric composition: sum of w^3 vanishes
+    s3 = w[0] ** 3 + 2 * (w[1] ** 3 + w[2] ** 3 + w[3] ** 3)
+    assert abs(s3) < 1e-12
+    s5 = w[0] ** 5 + 2 * (w[1] ** 5 + w[2] ** 5 + w[3] ** 5)
+    assert abs(s5) < 1e-12
+
+
+def _energy_drift(orc, order, nsteps):
+    pos, vel, m = ics.kepler_pair(0.5, 0.5, 1.0, 0.5)
+    p = _params(orc, eps=0.0)
+    E0 = orc.energy(pos, vel, m, p).E
+    T = 2 * math.pi
+    h = T / nsteps
+    worst = 0.0
+    x, v = pos, vel
+    chunk = nsteps // 8
+    for _ in range(8):
+        x, v = orc.run(x, v, m, p, order, h, chunk)
+        worst = max(worst, abs(orc.energy(x, v, m, p).E - E0))
+    return worst / abs(E0)
+
+
+def test_energy_error_scaling(orc):
+    """Symplectic schemes: bounded energy error scaling as dt^2 and dt^6."""
+    r2 = _energy_drift(orc, 2, 4000) / _energy_drift(orc, 2, 8000)
+    assert 3.5 < r2 < 4.5, r2
+    r6 = _energy_drift(orc, 6, 400) / _energy_drift(orc, 6, 800)
+    assert 45 < r6 < 85, r6
+
+
+@pytest.mark.parametrize("order", [2, 6])
+def test_time_reversal(orc, order):
+    """Symmetric schemes are time reversible (Sect. 3.1): n steps, flip the
+    velocities, n steps gives back the initial positions."""
+    pos, vel, m = ics.plummer(32, seed=3)
+    p = _params(orc, eps=0.05, ext_on=True)
+    pos = pos + [50.0, 0, 0]
+    vel = vel + [0, ics.VC_R50, 0]
+    x, v = orc.run(pos, vel, m, p, order, 1 / 256, 40)
+    x2, v2 = orc.run(x, -v, m, p, order, 1 / 256, 40)
+    assert np.abs(x2 - pos).max() < 1e-12
+    assert np.abs(v2 + vel).max() < 1e-12
+
+
+def test_isolated_conservation(orc):
+    """No external field: total momentum and angular momentum are conserved
+    to round-off (Sect. 2), energy to the scheme's truncation level."""
+    pos, vel, m = ics.plummer(64, seed=4, masses=ics.salpeter_masses(64, 4))
+    p = _params(orc, eps=0.02)
+    e0 = orc.energy(pos, vel, m, p)
+    x, v = orc.run(pos, vel, m, p, 6, 1 / 512, 100)
+    e1 = orc.energy(x, v, m, p)
+    assert np.abs(e1.P - e0.P).max() < 1e-15
+    assert np.abs(e1.L - e0.L).max() < 1e-14
+    assert abs((e1.E - e0.E) / e0.E) < 1e-8
+
+
+def test_axisymmetric_field_conserves_lz(orc):
+    """In the axisymmetric disk + bulge field the z torque vanishes pairwise
+    and each drift preserves r x v, so L_z is conserved to round-off by the
+    discrete scheme (the paper's Table 2 finds L_z errors near 1e-17); L_x,
+    L_y change by the external torque of eq. 8."""
+    pos, vel, m = ics.plummer(64, seed=5)
+    pos, vel = ics.place_on_orbit(pos, vel)
+    pos[:, 2] += 0.3
+    p = _params(orc, eps=0.01, ext_on=True)
+    e0 = orc.energy(pos, vel, m, p)
+    x, v = orc.run(pos, vel, m, p, 6, 1 / 256, 50)
+    e1 = orc.energy(x, v, m, p)
+    assert abs(e1.L[2] - e0.L[2]) < 1e-13 * abs(e0.L[2])
+    assert abs((e1.E - e0.E) / e0.E) < 1e-10
+    tq = orc.torque(pos, m, p)
+    assert abs(tq[2]) < 1e-13 * np.abs(tq).max()
+    assert np.abs(tq[:2]).max() > 0
+
+
+def test_torque_closed_form(orc):
+    """Eq. 8 for one particle at (x, 0, z): torque about y equals
+    m (z a_x - x a_z), with a from the field routine; x component zero."""
+    p = _params(orc, ext_on=True)
+    x = np.array([[5.0, 0.0, 0.4]])
+    a = orc.ext_accel(p, x[0])[0]
+    t = orc.torque(x, [2.0], p)
+    np.testing.assert_allclose(t, [0.0, 2.0 * (0.4 * a[0] - 5.0 * a[2]), 0.0],
+                               rtol=1e-14, atol=1e-18)
+
+
+# ------------------------------------------------------------ diagnostics
+
+def test_energy_closed_forms(orc):
+    """Two bodies: K = sum m v^2/2, W = -G m1 m2 / sqrt(r^2 + eps^2) (eq. 4),
+    P = sum m v, L = sum m r x v."""
+    pos = np.array([[1.0, 2.0, 0.5], [-0.5, 0.0, 1.0]])
+    vel = np.array([[0.1, -0.2, 0.3], [0.0, 0.4, -0.1]])
+    m = np.array([2.0, 3.0])
+    p = _params(orc, G=1.5, eps=0.2)
+    e = orc.energy(pos, vel, m, p)
+    r2 = ((pos[0] - pos[1]) ** 2).sum()
+    assert abs(e.W + 1.5 * 6.0 / math.sqrt(r2 + 0.04)) < 1e-15
+    assert abs(e.K - 0.5 * (2 * 0.14 + 3 * 0.17)) < 1e-15
+    np.testing.assert_allclose(e.P, [0.2, 0.8, 0.3], atol=1e-16)
+    np.testing.assert_allclose(e.L, 2 * np.cross(pos[0], vel[0]) + 3 * np.cross(pos[1], vel[1]),
+                               atol=1e-15)
+    assert e.W_ext == 0.0
+
+
+def test_ext_energy_gradient(orc):
+    """W_ext = sum m Phi: its derivative in r_i is -m_i a_ext(r_i)."""
+    p = _params(orc, ext_on=True, eps=0.1)
+    pos = np.array([[49.0, 1.0, 0.2], [51.0, -0.5, -0.1]])
+    vel = np.zeros((2, 3))
+    m = np.array([0.3, 0.7])
+    h = 1e-5
+    ae = orc.ext_accel(p, pos)
+    for i in range(2):
+        for k in range(3):
+            pp = pos.copy(); pp[i, k] += h
+            pm = pos.copy(); pm[i, k] -= h
+            d = (orc.energy(pp, vel, m, p).W_ext - orc.energy(pm, vel, m, p).W_ext) / (2 * h)
+            assert abs(d + m[i] * ae[i, k]) < 1e-7 * max(1e-3, abs(m[i] * ae[i, k]))
+
+
+def test_plummer_virial_and_henon_energy(orc):
+    """Sampled Plummer sphere in Henon units: 2K/|W| = 1 and E = -1/4 within
+    sampling noise (a few / sqrt(N))."""
+    n = 8192
+    pos, vel, m = ics.henon_plummer(n, seed=0)
+    e = orc.energy(pos, vel, m, _params(orc, eps=1e-3))
+    q = 2 * e.K / abs(e.W)
+    assert abs(q - 1) < 4 / math.sqrt(n), q
+    assert abs(e.E + 0.25) < 0.25 * 4 / math.sqrt(n), e.E
+
+
+def test_uniform_sphere_virial_ratio(orc):
+    """The paper's workload: uniform sphere with expected Q = 0.3."""
+    n = 6000
+    pos, vel, m = ics.uniform_sphere(n, seed=0, q_vir=0.3)
+    e = orc.energy(pos, vel, m, _params(orc, eps=ics.paper_softening(n)))
+    assert abs(2 * e.K / abs(e.W) - 0.3) < 0.3 * 5 / math.sqrt(n)
