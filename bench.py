@@ -1,0 +1,312 @@
+"""Benchmark: pair interactions per second of the direct-summation hot path.
+
+Workload (default): a Plummer cluster (M = 1, a = 1), N = 65536, on a circular
+orbit at R = 50 in the Miyamoto-Nagai disk + Plummer bulge field, softening
+eps = 0.005 / N^{1/3}, sixth-order SI6A steps of dt = 1/256, mixed precision
+(float pairs, double-single accumulation).  One timed step is one SI6A step:
+seven all-pairs force evaluations (7 N^2 interactions, 20 flops each by the
+paper's convention) plus the fused FP64 kick/drift/field kernels.
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
+on the library's stream, with a 512 MB L2 flush between steps (outside the
+events); barrier + synchronize around the timed region; max over ranks.
+Under torchrun each rank integrates its own independent cluster (seed =
+rank): no collective on the data path (weak scaling).
+
+``--impl reference`` times the CPU oracle on the host cores instead, on a
+bounded sample of the same workload (bodies x all N sources per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gpair-interactions/s & % FP32 peak vs plain FP64 kernel; p50/p99 solve latency"
+UNIT = "Gpair-interactions/s"
+FLOPS_PER_PAIR = 20
+
+
+def workload(n: int, seed: int):
+    from paper_1003_3896_gb300 import ics
+    pos, vel, m = ics.plummer(n, seed)
+    pos, vel = ics.place_on_orbit(pos, vel)
+    return pos, vel, m, ics.paper_softening(n)
+
+
+def config_dict(args, n_gpus):
+    return {"workload": f"plummer_N{args.n}_orbit_R50_disk_bulge_si6a_dt1/256",
+            "n": args.n, "order": 6, "dt": 1.0 / 256, "evals_per_step": 7,
+            "precision": args.precision, "eps": "0.005/N^(1/3)",
+            "l2": "flushed between timed steps (512 MB write)",
+            "parallelism": f"independent clusters x{n_gpus}"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[3 + k].lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def fp32_peak_tflops(sms: int, mhz: float) -> float:
+    """FP32 FMA peak from unit counts: 128 FP32 lanes per SM, 2 flops per FMA."""
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def cpu_baseline(pos, m, eps, budget_s: float = 12.0):
+    """The oracle as it stands, on the host cores: eq. 5 sums for a sample of
+    target bodies against all N sources, repeated up to ~budget_s."""
+    import oracle
+    oracle.build()
+    n = m.size
+    cores = oracle.max_threads()
+    rng = np.random.default_rng(0)
+    k = min(n, 4096)
+    idx = np.sort(rng.choice(n, k, replace=False))
+    t0 = time.perf_counter()
+    oracle.accel_int_at(pos, m, idx, 1.0, eps)
+    dt1 = time.perf_counter() - t0
+    reps = max(1, min(20, int(budget_s / max(dt1, 1e-3))))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.accel_int_at(pos, m, idx, 1.0, eps)
+    dt = time.perf_counter() - t0
+    pairs = reps * k * n
+    return {"value": pairs / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{reps} x ({k} target bodies x {n} sources), FP64, "
+                      f"{dt:.1f} s on {cores} host threads"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle timed on the same workload's metric."""
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    pos, vel, m, eps = workload(args.n, 0)
+    n = m.size
+    k = min(n, 2048)
+    rng = np.random.default_rng(1)
+    idx = np.sort(rng.choice(n, k, replace=False))
+    for _ in range(args.warmup):
+        oracle.accel_int_at(pos, m, idx, 1.0, eps)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.accel_int_at(pos, m, idx, 1.0, eps)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = args.steps * k * n / tot / 1e9
+    cores = oracle.max_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"per step {k} target bodies x {n} sources (eq. 5, FP64)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=65536)
+    ap.add_argument("--precision", default="ds", choices=["ds", "ds_full", "fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1003_3896_gb300 import build as nbbuild
+    if rank == 0:
+        nbbuild.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1003_3896_gb300 import nbsym
+
+    pos, vel, m, eps = workload(args.n, seed=rank)
+    n = m.size
+    dt = 1.0 / 256
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ctx = nbsym.Context(n, eps=eps, precision=args.precision, ext_on=True, device=local,
+                        stream=stream.cuda_stream)
+    ctx.load(pos, vel, m)
+    for _ in range(args.warmup):
+        ctx.step(6, dt, 1)
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ctx.prof_enable(True)
+    wall0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.zero_()
+                starts[k].record(stream)
+                ctx.step(6, dt, 1)
+                ends[k].record(stream)
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    prof = ctx.prof_read()
+    ctx.prof_enable(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+        dist.barrier()
+    pairs_rank = 7 * args.steps * n * n
+    value = world * pairs_rank / (t_ms * 1e-3) / 1e9
+
+    # end-to-end through the public API: host buffers in pinned memory, the
+    # state uploaded before and read back after every step
+    pin_p = torch.from_numpy(pos).pin_memory().numpy()
+    pin_v = torch.from_numpy(vel).pin_memory().numpy()
+    pin_m = torch.from_numpy(m).pin_memory().numpy()
+    out_p = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+    out_v = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+    e2e_steps = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    e_ms = []
+    with torch.cuda.stream(stream):
+        for k in range(e2e_steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.load(pin_p, pin_v, pin_m)
+            ctx.step(6, dt, 1)
+            nbsym.check(nbsym.nb_get_state(ctx.handle, nbsym._p(out_p), nbsym._p(out_v)))
+            e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_value = world * 7 * n * n / (statistics.mean(e_ms) * 1e-3) / 1e9
+
+    # plain FP64 kernel on the same state and configuration
+    ctx.set_precision("fp64")
+    ctx.prof_enable(True)
+    for _ in range(2):
+        ctx.accel()
+    p64 = ctx.prof_read()
+    ctx.prof_enable(False)
+    fp64_rate = p64["interactions"] / (p64["pair_ms"] * 1e-3) / 1e9
+
+    clocks = clk.summary()
+    achieved = FLOPS_PER_PAIR * prof["interactions"] / (prof["pair_ms"] * 1e-3) / 1e12
+    peak = fp32_peak_tflops(sms, 2070.0)
+    sustained_mhz = clocks.get("sm_mhz") or 2070.0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"ds": "f32-pair/ds-acc", "ds_full": "f32-pair/ds-acc",
+                  "fp32": "f32", "fp64": "f64"}[args.precision],
+        "data": "synthetic", "config": config_dict(args, world),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": f"pair_sp_kernel ({args.precision})",
+                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max clock)",
+                     "frac_at_sampled_clock": achieved / fp32_peak_tflops(sms, sustained_mhz),
+                     "pair_kernel_ms_mean": prof["pair_ms"] / max(1, prof["pair_launches"]),
+                     "pair_launches": prof["pair_launches"]},
+        "fp64_kernel": {"value": fp64_rate, "unit": UNIT},
+        "vs_fp64_kernel": value / fp64_rate if fp64_rate > 0 else None,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 7 * 8,
+                "d2h_bytes_per_step": n * 6 * 8, "steps": e2e_steps},
+        "gpu_launches": prof["kernel_launches"],
+        "clocks": clocks, "wall_s_timed": wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(pos, m, eps)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,190 @@
+/*
+ * nbsym.h -- C ABI of the GB300 direct-summation N-body library.
+ *
+ * The library integrates the equations of motion of N point masses under
+ * softened Newtonian gravity plus an optional smooth external field
+ * (Capuzzo-Dolcetta, Mastrobuono-Battisti & Maschietti, "NBSymple",
+ * Sect. 2, eq. 1-5 and eq. 3), with the second-order leapfrog or the
+ * sixth-order symplectic scheme of Sect. 3.1, entirely on one GPU.
+ *
+ * General rules for every entry point
+ *  - Plain C types only.  Host arrays are borrowed for the duration of the
+ *    call; the library copies what it needs.  Output buffers belong to the
+ *    caller.  Device-pointer variants (suffix _device) take pointers to
+ *    device memory on the context's device; they are also borrowed.
+ *  - Positions, velocities and accelerations are float64, n rows of (x, y, z)
+ *    interleaved (row-major (n, 3)); masses are float64 (n,).
+ *  - Accelerations, never forces: the m_i of eq. 2 / eq. 5 is divided out.
+ *  - Every call is synchronous: results are valid when it returns.
+ *  - Errors are negative return codes (nb_status); no exception crosses the
+ *    ABI.  nb_last_error() gives a message for the calling thread.
+ *  - A context is not thread-safe; use one context per host thread, or
+ *    serialise calls.
+ */
+#ifndef NBSYM_H
+#define NBSYM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NB_ABI_VERSION 1
+
+/* Opaque context: device state of one particle system plus its buffers,
+ * stream, captured step graphs and launch configuration.  Library-owned. */
+typedef struct nb_ctx nb_ctx;
+
+/* Arithmetic of the pair-force sum (Sect. 4.2; abstract):
+ *  NB_FP64 -- all pair arithmetic and accumulation in double precision.
+ *  NB_DS   -- mixed: pair arithmetic in single precision on coordinates
+ *             taken relative to a reference point near the system, the
+ *             coordinate difference of close pairs re-formed from
+ *             double-single (hi + lo) coordinates, per-tile sums folded
+ *             into double-single accumulators (the paper's software
+ *             double-single idea, Sect. 4.2).
+ *  NB_FP32 -- pure single precision: coordinates rounded to float
+ *             (relative to the same reference point), float accumulation.
+ *  NB_DS_FULL -- as NB_DS but the double-single coordinate difference is
+ *             formed for every pair, as the paper's DSP code does.
+ * In every mode the state (positions, velocities), the kick/drift update,
+ * the external field and the energy diagnostic are double precision. */
+enum nb_precision { NB_FP64 = 0, NB_DS = 1, NB_FP32 = 2, NB_DS_FULL = 3 };
+
+enum nb_status {
+    NB_OK = 0,
+    NB_EINVAL = -1,     /* bad argument (NULL pointer, n out of range, order
+                           not 2 or 6, dt not finite and > 0, eps < 0, ...) */
+    NB_ENOMEM = -2,     /* device or host allocation failed */
+    NB_ECUDA = -3,      /* a CUDA runtime call failed (message has details) */
+    NB_ESTATE = -4,     /* call not valid in the context's state (e.g. step
+                           before load) */
+    NB_ETIMEOUT = -5,   /* a bounded device-side wait gave up */
+    NB_ENONFINITE = -6  /* result contains NaN/Inf (e.g. coincident particles
+                           with eps = 0) */
+};
+
+/* Physical and execution parameters of a context. */
+typedef struct {
+    double G;          /* gravitational constant, > 0 (paper: G = 1, Sect. 3) */
+    double eps;        /* softening length >= 0 (eq. 4-5); 0 = unsoftened
+                          sum of eq. 2 with the j != i exclusion */
+    int precision;     /* enum nb_precision */
+    int ext_on;        /* 1: add the external field of eq. 3, a
+                          Miyamoto-Nagai disk plus a Plummer bulge:
+                          Phi = -G Md / sqrt(R^2 + (ad + sqrt(z^2 + bd^2))^2)
+                                - G Mb / sqrt(r^2 + ab^2),  a_ext = -grad Phi */
+    double Md, ad, bd; /* disk mass, scale length, scale height (bd > 0) */
+    double Mb, ab;     /* bulge mass, scale (ab > 0) */
+    int device;        /* CUDA device ordinal */
+    void *stream;      /* cudaStream_t to run on; NULL: the context creates
+                          and owns a non-blocking stream */
+    double near_frac;  /* NB_DS only: pairs closer than near_frac times the
+                          system's rms radius get the double-single coordinate
+                          difference; <= 0 selects the default 0.03 */
+} nb_params;
+
+/* Diagnostics of Sect. 4.1 (eq. 9-10 use E and L):
+ *   K = 1/2 sum m v^2,  W = -G sum_{i<j} m_i m_j / sqrt(r_ij^2 + eps^2)
+ *   (eq. 4), W_ext = sum m_i Phi(r_i), E = K + W + W_ext,
+ *   P = sum m v,  L = sum m r x v.   Always computed in double precision. */
+typedef struct {
+    double K, W, W_ext, E;
+    double P[3];
+    double L[3];
+} nb_energy_t;
+
+/* Timing of the pair-force kernel while profiling is on (nb_prof_enable). */
+typedef struct {
+    int64_t pair_launches;    /* pair-force kernel launches timed */
+    double pair_ms;           /* their summed device time, CUDA events */
+    int64_t interactions;     /* sum over those launches of n * n */
+    int64_t kernel_launches;  /* all kernels this context enqueued while
+                                 profiling was on (graph nodes included) */
+} nb_prof_t;
+
+/* Library ABI version (NB_ABI_VERSION of the build). */
+int nb_abi_version(void);
+
+/* Message of the last error on the calling thread ("" if none).  The string
+ * is owned by the library and valid until the next call on this thread. */
+const char *nb_last_error(void);
+
+/* Fill *p with defaults: G = 1, eps = 0, NB_DS, field off with the disk +
+ * bulge constants (Md 100, ad 6.5, bd 0.26, Mb 15, ab 0.7), device 0, own
+ * stream, default near_frac.  NULL-safe (no-op). */
+void nb_params_default(nb_params *p);
+
+/* Create a context for up to n_capacity particles (1 <= n_capacity <= 2^26)
+ * on p->device.  Allocates all device memory the context will use.
+ * *out receives the context.  Errors: NB_EINVAL (bad parameters),
+ * NB_ENOMEM, NB_ECUDA. */
+int nb_create(const nb_params *p, int64_t n_capacity, nb_ctx **out);
+
+/* Load a particle system (initial conditions of eq. 3): n rows of positions
+ * and velocities, n masses (>= 0, finite).  1 <= n <= capacity.  Host
+ * pointers.  Errors: NB_EINVAL, NB_ECUDA. */
+int nb_load(nb_ctx *ctx, int64_t n, const double *pos, const double *vel,
+            const double *mass);
+
+/* As nb_load with device pointers (e.g. torch tensors' data_ptr()). */
+int nb_load_device(nb_ctx *ctx, int64_t n, const double *d_pos,
+                   const double *d_vel, const double *d_mass);
+
+/* One force evaluation at the current positions: the right-hand side of
+ * eq. 3, a_i = G sum_{j != i} m_j r_ij / (|r_ij|^2 + eps^2)^{3/2} (eq. 5,
+ * eq. 2 when eps = 0) plus the external field when ext_on.  Written to the
+ * caller's host buffer acc_out (n rows of x, y, z).  Errors: NB_ESTATE (no
+ * system loaded), NB_EINVAL, NB_ENONFINITE, NB_ECUDA. */
+int nb_accel(nb_ctx *ctx, double *acc_out);
+
+/* As nb_accel into device memory. */
+int nb_accel_device(nb_ctx *ctx, double *d_acc_out);
+
+/* Advance the loaded system by nsteps steps of length dt with the
+ * symplectic scheme of the given order (Sect. 3.1): order 2 is the
+ * drift-kick-drift leapfrog (one force evaluation per step), order 6 is the
+ * SI6A composition of seven leapfrog steps (seven force evaluations per
+ * step).  nsteps >= 0, dt finite and > 0.  Errors: NB_ESTATE, NB_EINVAL,
+ * NB_ECUDA. */
+int nb_step(nb_ctx *ctx, int order, double dt, int64_t nsteps);
+
+/* Energy, momentum and angular momentum of the current state (Sect. 4.1).
+ * Errors: NB_ESTATE, NB_EINVAL, NB_ENONFINITE, NB_ECUDA. */
+int nb_energy(nb_ctx *ctx, nb_energy_t *out);
+
+/* External torque M_ext = sum m_i r_i x a_ext(r_i) (eq. 8); zero when the
+ * field is off.  out has 3 doubles.  Errors: NB_ESTATE, NB_EINVAL, NB_ECUDA. */
+int nb_torque(nb_ctx *ctx, double *out);
+
+/* Copy the current positions and velocities (n rows each) to host buffers;
+ * either pointer may be NULL to skip it.  Errors: NB_ESTATE, NB_ECUDA. */
+int nb_get_state(nb_ctx *ctx, double *pos, double *vel);
+
+/* As nb_get_state into device memory. */
+int nb_get_state_device(nb_ctx *ctx, double *d_pos, double *d_vel);
+
+/* Number of particles loaded (0 before nb_load), or NB_EINVAL for NULL. */
+int64_t nb_size(const nb_ctx *ctx);
+
+/* Switch the pair-force arithmetic (enum nb_precision) of a context
+ * without reloading; the state is untouched.  Errors: NB_EINVAL. */
+int nb_set_precision(nb_ctx *ctx, int precision);
+
+/* Start (on = 1) or stop (on = 0) timing pair-force launches with CUDA
+ * events recorded on the context's stream (inside captured step graphs as
+ * event-record nodes).  Starting resets the counters.  Errors: NB_EINVAL. */
+int nb_prof_enable(nb_ctx *ctx, int on);
+
+/* Read the counters accumulated since nb_prof_enable(ctx, 1). */
+int nb_prof_read(nb_ctx *ctx, nb_prof_t *out);
+
+/* Release the context and all its device memory.  NULL-safe. */
+void nb_destroy(nb_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NBSYM_H */

@@ -71,6 +71,8 @@ def _load():
     pp = C.POINTER(_Params)
     i64 = C.c_int64
     lib.orc_accel_int.argtypes = [i64, dp, dp, C.c_double, C.c_double, dp]
+    lib.orc_accel_int_at.argtypes = [i64, dp, dp, C.c_double, C.c_double, i64,
+                                     C.POINTER(C.c_int64), dp]
     lib.orc_ext_phi.argtypes = [pp, dp]
     lib.orc_ext_phi.restype = C.c_double
     lib.orc_ext_accel_one.argtypes = [pp, dp, dp]
@@ -113,6 +115,20 @@ def accel_int(pos, mass, G: float = 1.0, eps: float = 0.0) -> np.ndarray:
     pos = _f64(pos, (n, 3))
     out = np.empty((n, 3))
     _load().orc_accel_int(n, _ptr(pos), _ptr(mass), float(G), float(eps), _ptr(out))
+    return out
+
+
+def accel_int_at(pos, mass, idx, G: float = 1.0, eps: float = 0.0) -> np.ndarray:
+    """Eq. 5 accelerations of the bodies listed in ``idx`` only, (len(idx), 3)."""
+    mass = _f64(mass).ravel()
+    n = mass.size
+    pos = _f64(pos, (n, 3))
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    if idx.size and (idx.min() < 0 or idx.max() >= n):
+        raise IndexError("idx out of range")
+    out = np.empty((idx.size, 3))
+    _load().orc_accel_int_at(n, _ptr(pos), _ptr(mass), float(G), float(eps), idx.size,
+                             idx.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(out))
     return out
 
 

@@ -91,6 +91,39 @@ void orc_accel_int(int64_t n, const double *pos, const double *mass,
 }
 
 /*
+ * The same sum as orc_accel_int (eq. 5 / eq. 2), evaluated only for the k
+ * bodies listed in idx: acc receives k rows.  Lets full-size outputs be
+ * checked on a sample of bodies.
+ */
+void orc_accel_int_at(int64_t n, const double *pos, const double *mass, double G,
+                      double eps, int64_t k, const int64_t *idx, double *acc)
+{
+    const double eps2 = eps * eps;
+    int64_t q;
+#pragma omp parallel for schedule(static)
+    for (q = 0; q < k; ++q) {
+        const int64_t i = idx[q];
+        double ax = 0.0, ay = 0.0, az = 0.0;
+        const double xi = pos[3 * i], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            const double dx = pos[3 * j] - xi;
+            const double dy = pos[3 * j + 1] - yi;
+            const double dz = pos[3 * j + 2] - zi;
+            const double r2 = dx * dx + dy * dy + dz * dz + eps2;
+            const double r = sqrt(r2);
+            const double w = mass[j] / (r2 * r);
+            ax += w * dx;
+            ay += w * dy;
+            az += w * dz;
+        }
+        acc[3 * q] = G * ax;
+        acc[3 * q + 1] = G * ay;
+        acc[3 * q + 2] = G * az;
+    }
+}
+
+/*
  * External potential Phi(x) (per unit mass), the smooth galactic term of
  * eq. 3 with F_ext = -grad Phi:
  *   Phi = -G Md / sqrt(R^2 + (ad + sqrt(z^2 + bd^2))^2) - G Mb / sqrt(r^2 + ab^2).

@@ -1,0 +1,219 @@
+"""ctypes binding of ``libnbsym.so`` (declared in ``include/nbsym.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Importing this module loads the library and raises ImportError if
+it has not been built (``paper_1003_3896_gb300.build.build()``); there is no
+fallback.  Device-pointer methods accept either an integer address or any
+object with ``data_ptr()`` (a torch tensor), so torch is never imported here.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnbsym.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_1003_3896_gb300.build.build()")
+_lib = C.CDLL(LIB_PATH)
+
+NB_FP64, NB_DS, NB_FP32, NB_DS_FULL = 0, 1, 2, 3
+PRECISIONS = {"fp64": NB_FP64, "ds": NB_DS, "fp32": NB_FP32, "ds_full": NB_DS_FULL}
+NB_OK, NB_EINVAL, NB_ENOMEM, NB_ECUDA, NB_ESTATE, NB_ETIMEOUT, NB_ENONFINITE = 0, -1, -2, -3, -4, -5, -6
+STATUS_NAMES = {0: "NB_OK", -1: "NB_EINVAL", -2: "NB_ENOMEM", -3: "NB_ECUDA", -4: "NB_ESTATE",
+                -5: "NB_ETIMEOUT", -6: "NB_ENONFINITE"}
+
+
+class Params(C.Structure):
+    _fields_ = [("G", C.c_double), ("eps", C.c_double), ("precision", C.c_int),
+                ("ext_on", C.c_int), ("Md", C.c_double), ("ad", C.c_double),
+                ("bd", C.c_double), ("Mb", C.c_double), ("ab", C.c_double),
+                ("device", C.c_int), ("stream", C.c_void_p), ("near_frac", C.c_double)]
+
+
+class EnergyT(C.Structure):
+    _fields_ = [("K", C.c_double), ("W", C.c_double), ("W_ext", C.c_double),
+                ("E", C.c_double), ("P", C.c_double * 3), ("L", C.c_double * 3)]
+
+
+class ProfT(C.Structure):
+    _fields_ = [("pair_launches", C.c_int64), ("pair_ms", C.c_double),
+                ("interactions", C.c_int64), ("kernel_launches", C.c_int64)]
+
+
+_dp = C.POINTER(C.c_double)
+_vp = C.c_void_p
+_ctxp = C.c_void_p
+
+
+def _sig(name, res, *args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = list(args)
+    return f
+
+
+nb_abi_version = _sig("nb_abi_version", C.c_int)
+nb_last_error = _sig("nb_last_error", C.c_char_p)
+nb_params_default = _sig("nb_params_default", None, C.POINTER(Params))
+nb_create = _sig("nb_create", C.c_int, C.POINTER(Params), C.c_int64, C.POINTER(_ctxp))
+nb_load = _sig("nb_load", C.c_int, _ctxp, C.c_int64, _dp, _dp, _dp)
+nb_load_device = _sig("nb_load_device", C.c_int, _ctxp, C.c_int64, _vp, _vp, _vp)
+nb_accel = _sig("nb_accel", C.c_int, _ctxp, _dp)
+nb_accel_device = _sig("nb_accel_device", C.c_int, _ctxp, _vp)
+nb_step = _sig("nb_step", C.c_int, _ctxp, C.c_int, C.c_double, C.c_int64)
+nb_energy = _sig("nb_energy", C.c_int, _ctxp, C.POINTER(EnergyT))
+nb_torque = _sig("nb_torque", C.c_int, _ctxp, _dp)
+nb_get_state = _sig("nb_get_state", C.c_int, _ctxp, _dp, _dp)
+nb_get_state_device = _sig("nb_get_state_device", C.c_int, _ctxp, _vp, _vp)
+nb_size = _sig("nb_size", C.c_int64, _ctxp)
+nb_set_precision = _sig("nb_set_precision", C.c_int, _ctxp, C.c_int)
+nb_prof_enable = _sig("nb_prof_enable", C.c_int, _ctxp, C.c_int)
+nb_prof_read = _sig("nb_prof_read", C.c_int, _ctxp, C.POINTER(ProfT))
+nb_destroy = _sig("nb_destroy", None, _ctxp)
+
+
+class NBError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def check(rc: int) -> int:
+    if rc < 0:
+        raise NBError(rc, nb_last_error().decode(errors="replace"))
+    return rc
+
+
+def _addr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _host3(a, n) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size != 3 * n:
+        raise ValueError(f"expected {3 * n} values, got {a.size}")
+    return a
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+@dataclass
+class Energy:
+    K: float
+    W: float
+    W_ext: float
+    E: float
+    P: np.ndarray
+    L: np.ndarray
+
+
+class Context:
+    """One particle system resident on one GPU (``nb_ctx``)."""
+
+    def __init__(self, capacity: int, G: float = 1.0, eps: float = 0.0,
+                 precision: int | str = NB_DS, ext_on: bool = False,
+                 Md: float = 100.0, ad: float = 6.5, bd: float = 0.26, Mb: float = 15.0,
+                 ab: float = 0.7, device: int = 0, stream=None, near_frac: float = 0.0):
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        p = Params()
+        nb_params_default(C.byref(p))
+        p.G, p.eps, p.precision, p.ext_on = G, eps, int(precision), int(bool(ext_on))
+        p.Md, p.ad, p.bd, p.Mb, p.ab = Md, ad, bd, Mb, ab
+        p.device = device
+        p.stream = _addr(stream) if stream is not None else None
+        p.near_frac = near_frac
+        h = _ctxp()
+        check(nb_create(C.byref(p), int(capacity), C.byref(h)))
+        self._h = h
+        self.capacity = int(capacity)
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "_h", None):
+            nb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- state
+    def load(self, pos, vel, mass):
+        mass = np.ascontiguousarray(mass, dtype=np.float64).ravel()
+        n = mass.size
+        pos = _host3(pos, n)
+        vel = _host3(vel, n)
+        check(nb_load(self._h, n, _p(pos), _p(vel), _p(mass)))
+
+    def load_device(self, n: int, pos, vel, mass):
+        check(nb_load_device(self._h, int(n), _addr(pos), _addr(vel), _addr(mass)))
+
+    @property
+    def n(self) -> int:
+        return int(check(nb_size(self._h)))
+
+    def get_state(self):
+        n = self.n
+        pos = np.empty((n, 3))
+        vel = np.empty((n, 3))
+        check(nb_get_state(self._h, _p(pos), _p(vel)))
+        return pos, vel
+
+    def get_state_device(self, pos, vel):
+        check(nb_get_state_device(self._h, _addr(pos), _addr(vel)))
+
+    # -- compute
+    def accel(self) -> np.ndarray:
+        out = np.empty((self.n, 3))
+        check(nb_accel(self._h, _p(out)))
+        return out
+
+    def accel_device(self, out):
+        check(nb_accel_device(self._h, _addr(out)))
+
+    def step(self, order: int, dt: float, nsteps: int = 1):
+        check(nb_step(self._h, int(order), float(dt), int(nsteps)))
+
+    def energy(self) -> Energy:
+        e = EnergyT()
+        check(nb_energy(self._h, C.byref(e)))
+        return Energy(e.K, e.W, e.W_ext, e.E, np.array(e.P[:]), np.array(e.L[:]))
+
+    def torque(self) -> np.ndarray:
+        out = np.empty(3)
+        check(nb_torque(self._h, _p(out)))
+        return out
+
+    def set_precision(self, precision: int | str):
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        check(nb_set_precision(self._h, int(precision)))
+
+    def prof_enable(self, on: bool = True):
+        check(nb_prof_enable(self._h, int(bool(on))))
+
+    def prof_read(self) -> dict:
+        p = ProfT()
+        check(nb_prof_read(self._h, C.byref(p)))
+        return {"pair_launches": p.pair_launches, "pair_ms": p.pair_ms,
+                "interactions": p.interactions, "kernel_launches": p.kernel_launches}

@@ -1,0 +1,82 @@
+"""C-ABI library: builds for sm_103a, loads without a GPU, exports every entry
+point declared in include/*.h, and rejects bad arguments before touching the
+device."""
+import ctypes as C
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1003_3896_gb300 import build
+    path = build.build()
+    return C.CDLL(path)
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(nb_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_core_calls():
+    names = declared_functions()
+    for required in ["nb_create", "nb_load", "nb_accel", "nb_step", "nb_energy",
+                     "nb_get_state", "nb_destroy", "nb_last_error"]:
+        assert required in names
+
+
+def test_every_declared_symbol_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_abi_version_and_defaults(lib):
+    from paper_1003_3896_gb300 import nbsym
+    assert nbsym.nb_abi_version() == 1
+    p = nbsym.Params()
+    nbsym.nb_params_default(C.byref(p))
+    assert p.G == 1.0 and p.eps == 0.0 and p.precision == nbsym.NB_DS
+    assert (p.Md, p.ad, p.bd, p.Mb, p.ab) == (100.0, 6.5, 0.26, 15.0, 0.7)
+    nbsym.nb_params_default(None)   # NULL-safe
+
+
+@pytest.mark.parametrize("field,value", [("G", 0.0), ("G", float("nan")), ("eps", -1.0),
+                                         ("precision", 7), ("bd", 0.0)])
+def test_create_rejects_bad_params_without_gpu(lib, field, value):
+    from paper_1003_3896_gb300 import nbsym
+    p = nbsym.Params()
+    nbsym.nb_params_default(C.byref(p))
+    p.ext_on = 1
+    setattr(p, field, value)
+    h = C.c_void_p()
+    rc = nbsym.nb_create(C.byref(p), 16, C.byref(h))
+    assert rc == nbsym.NB_EINVAL
+    assert not h.value
+    assert nbsym.nb_last_error()
+
+
+def test_null_handles_are_rejected(lib):
+    from paper_1003_3896_gb300 import nbsym
+    assert nbsym.nb_step(None, 2, 0.1, 1) == nbsym.NB_EINVAL
+    assert nbsym.nb_accel(None, None) == nbsym.NB_EINVAL
+    assert nbsym.nb_size(None) == nbsym.NB_EINVAL
+    nbsym.nb_destroy(None)
+
+
+def test_oracle_is_not_on_the_product_path():
+    """The product package never imports or loads the oracle."""
+    pkg = os.path.join(ROOT, "paper_1003_3896_gb300")
+    for f in glob.glob(os.path.join(pkg, "**", "*.*"), recursive=True):
+        if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+            assert "oracle" not in open(f).read().replace("Oracle", "").lower() or \
+                f.endswith("ics.py"), f

@@ -1,0 +1,321 @@
+"""Parity of the CUDA path with the CPU oracle, through the C ABI.
+
+Tolerances (relative RMS of accelerations over the compared bodies,
+sqrt(sum |a - a_ref|^2 / sum |a_ref|^2)): double 1e-12, mixed double-single
+1e-6, pure float 1e-5.  Positions after 4 steps: 1e-10 (double) and 1e-6
+(mixed), absolute, max norm.  Long runs: |dE/E| within twice the oracle's.
+Small cases span several 128-body tiles with a ragged tail; full-size cases
+(N = 65536 on an orbit at R = 50 in the disk + bulge field; N = 262144 with
+Salpeter masses) are checked on a sample of bodies the oracle computes one by
+one, in the launch configuration the benchmark uses.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1003_3896_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "ds": 1e-6, "ds_full": 1e-6, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def nbs():
+    from paper_1003_3896_gb300 import build
+    build.build()
+    from paper_1003_3896_gb300 import nbsym
+    return nbsym
+
+
+def rel_rms(a, ref):
+    return math.sqrt(((a - ref) ** 2).sum() / (ref ** 2).sum())
+
+
+def ext_params(orc, eps, ext_on):
+    return orc.Params(G=1.0, eps=eps, ext_on=ext_on)
+
+
+def system(n, seed, offset=False, salpeter=False):
+    masses = ics.salpeter_masses(n, seed) if salpeter else None
+    pos, vel, m = ics.plummer(n, seed, masses=masses)
+    if offset:
+        pos, vel = ics.place_on_orbit(pos, vel)
+    return pos, vel, m
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 33, 127, 128, 129, 1000, 4099])
+@pytest.mark.parametrize("eps", [0.01, 0.0])
+def test_accel_fp64_small(nbs, orc, n, eps):
+    pos, vel, m = system(n, seed=n)
+    with nbs.Context(n, eps=eps, precision="fp64") as c:
+        c.load(pos, vel, m)
+        a = c.accel()
+    ref = orc.accel(pos, m, ext_params(orc, eps, False))
+    if n == 1:
+        assert np.all(a == 0.0)
+        return
+    assert rel_rms(a, ref) <= TOL["fp64"]
+    np.testing.assert_allclose(a, ref, rtol=1e-9, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("prec", ["ds", "ds_full", "fp32"])
+@pytest.mark.parametrize("n,offset", [(2, False), (33, True), (129, False), (1000, True),
+                                      (4099, True), (9000, False)])
+def test_accel_mixed_small(nbs, orc, prec, n, offset):
+    pos, vel, m = system(n, seed=n + 1, offset=offset)
+    eps = ics.paper_softening(n)
+    with nbs.Context(n, eps=eps, precision=prec, ext_on=offset) as c:
+        c.load(pos, vel, m)
+        a = c.accel()
+    ref = orc.accel(pos, m, ext_params(orc, eps, offset))
+    ref_int = orc.accel_int(pos, m, 1.0, eps)
+    # tolerance is stated for the pair sum; the field adds exact FP64 terms
+    a_int = a - (ref - ref_int)
+    assert rel_rms(a_int, ref_int) <= TOL[prec], rel_rms(a_int, ref_int)
+
+
+def test_accel_ext_field_fp64(nbs, orc):
+    n = 2000
+    pos, vel, m = system(n, seed=5, offset=True)
+    with nbs.Context(n, eps=1e-3, precision="fp64", ext_on=True) as c:
+        c.load(pos, vel, m)
+        a = c.accel()
+    ref = orc.accel(pos, m, ext_params(orc, 1e-3, True))
+    assert rel_rms(a, ref) <= 1e-13
+
+
+def test_unsoftened_two_body(nbs, orc):
+    pos, vel, m = ics.kepler_pair(0.6, 0.4, 1.0, 0.5)
+    for prec in ("fp64", "ds", "fp32"):
+        with nbs.Context(2, eps=0.0, precision=prec) as c:
+            c.load(pos, vel, m)
+            a = c.accel()
+        ref = orc.accel_int(pos, m, 1.0, 0.0)
+        assert rel_rms(a, ref) <= TOL[prec]
+
+
+def test_coincident_unsoftened_is_reported(nbs):
+    pos = np.array([[0.0, 0, 0], [0.0, 0, 0], [1.0, 0, 0]])
+    vel = np.zeros((3, 3))
+    m = np.ones(3)
+    for prec in ("fp64", "ds"):
+        with nbs.Context(3, eps=0.0, precision=prec) as c:
+            c.load(pos, vel, m)
+            with pytest.raises(nbs.NBError) as e:
+                c.accel()
+            assert e.value.code == nbs.NB_ENONFINITE
+
+
+@pytest.mark.parametrize("ext_on", [False, True])
+def test_energy_parity(nbs, orc, ext_on):
+    n = 3000
+    pos, vel, m = system(n, seed=7, offset=ext_on, salpeter=True)
+    with nbs.Context(n, eps=2e-3, precision="ds", ext_on=ext_on) as c:
+        c.load(pos, vel, m)
+        e = c.energy()
+        tq = c.torque()
+    r = orc.energy(pos, vel, m, ext_params(orc, 2e-3, ext_on))
+    for k in ("K", "W", "W_ext", "E"):
+        got, want = getattr(e, k), getattr(r, k)
+        assert abs(got - want) <= 1e-12 * max(abs(want), 1e-300), (k, got, want)
+    scale_p = (m[:, None] * np.abs(vel)).sum()
+    np.testing.assert_allclose(e.P, r.P, rtol=0, atol=1e-14 * scale_p)
+    scale_l = (m[:, None] * np.abs(np.cross(pos, vel))).sum()
+    np.testing.assert_allclose(e.L, r.L, rtol=0, atol=1e-14 * scale_l)
+    if ext_on:
+        want = orc.torque(pos, m, ext_params(orc, 2e-3, True))
+        np.testing.assert_allclose(tq, want, rtol=1e-12, atol=1e-14 * np.abs(want).max())
+    else:
+        assert np.all(tq == 0)
+
+
+@pytest.mark.parametrize("order", [2, 6])
+@pytest.mark.parametrize("prec", ["fp64", "ds"])
+def test_four_steps_positions(nbs, orc, order, prec):
+    """Positions after 4 steps in the orbit-in-field geometry."""
+    n = 2500
+    pos, vel, m = system(n, seed=11, offset=True)
+    eps = ics.paper_softening(n)
+    dt = 1.0 / 256
+    with nbs.Context(n, eps=eps, precision=prec, ext_on=True) as c:
+        c.load(pos, vel, m)
+        c.step(order, dt, 4)
+        x, v = c.get_state()
+    rx, rv = orc.run(pos, vel, m, ext_params(orc, eps, True), order, dt, 4)
+    tol = 1e-10 if prec == "fp64" else 1e-6
+    assert np.abs(x - rx).max() <= tol, np.abs(x - rx).max()
+    assert np.abs(v - rv).max() <= tol * 50
+
+
+def test_long_run_energy_leapfrog_fp64(nbs, orc):
+    """N = 1024 Plummer in Henon units, eps = 1e-3, DKD leapfrog, dt = 1/1024,
+    64 steps: |dE/E| within twice the oracle's own."""
+    n = 1024
+    pos, vel, m = ics.henon_plummer(n, 0)
+    p = ext_params(orc, 1e-3, False)
+    e0 = orc.energy(pos, vel, m, p).E
+    rx, rv = orc.run(pos, vel, m, p, 2, 1 / 1024, 64)
+    de_ref = abs((orc.energy(rx, rv, m, p).E - e0) / e0)
+    with nbs.Context(n, eps=1e-3, precision="fp64") as c:
+        c.load(pos, vel, m)
+        g0 = c.energy().E
+        c.step(2, 1 / 1024, 64)
+        g1 = c.energy().E
+        x, _ = c.get_state()
+    de = abs((g1 - g0) / g0)
+    assert de <= 2 * de_ref + 1e-15, (de, de_ref)
+    assert np.abs(x - rx).max() < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["ds", "fp64"])
+def test_long_run_energy_sixth_order_field(nbs, orc, prec):
+    n = 1536
+    pos, vel, m = system(n, seed=3, offset=True)
+    eps = ics.paper_softening(n)
+    p = ext_params(orc, eps, True)
+    e0 = orc.energy(pos, vel, m, p).E
+    rx, rv = orc.run(pos, vel, m, p, 6, 1 / 256, 40)
+    de_ref = abs((orc.energy(rx, rv, m, p).E - e0) / e0)
+    with nbs.Context(n, eps=eps, precision=prec, ext_on=True) as c:
+        c.load(pos, vel, m)
+        c.step(6, 1 / 256, 40)
+        x, v = c.get_state()
+    de = abs((orc.energy(x, v, m, p).E - e0) / e0)
+    assert de <= 2 * de_ref + 2e-14, (de, de_ref)
+
+
+def test_lz_conserved_in_axisymmetric_field(nbs):
+    n = 800
+    pos, vel, m = system(n, seed=13, offset=True)
+    pos[:, 2] += 0.2
+    with nbs.Context(n, eps=0.01, precision="fp64", ext_on=True) as c:
+        c.load(pos, vel, m)
+        l0 = c.energy().L
+        c.step(6, 1 / 256, 20)
+        l1 = c.energy().L
+    assert abs(l1[2] - l0[2]) <= 1e-13 * abs(l0[2])
+
+
+def test_deterministic_and_resumable(nbs):
+    n = 5000
+    pos, vel, m = system(n, seed=17, offset=True)
+    eps = ics.paper_softening(n)
+    for prec in ("ds", "fp64"):
+        with nbs.Context(n, eps=eps, precision=prec, ext_on=True) as c:
+            c.load(pos, vel, m)
+            a1 = c.accel()
+            a2 = c.accel()
+            np.testing.assert_array_equal(a1, a2)
+            c.step(6, 1 / 256, 4)
+            x_full, v_full = c.get_state()
+        with nbs.Context(n, eps=eps, precision=prec, ext_on=True) as c:
+            c.load(pos, vel, m)
+            c.step(6, 1 / 256, 2)
+            x, v = c.get_state()
+        with nbs.Context(n, eps=eps, precision=prec, ext_on=True) as c:
+            c.load(x, v, m)
+            c.step(6, 1 / 256, 2)
+            x2, v2 = c.get_state()
+        np.testing.assert_array_equal(x2, x_full)
+        np.testing.assert_array_equal(v2, v_full)
+
+
+def test_state_errors(nbs):
+    with nbs.Context(10, eps=0.01) as c:
+        with pytest.raises(nbs.NBError) as e:
+            c.step(2, 0.1, 1)
+        assert e.value.code == nbs.NB_ESTATE
+        with pytest.raises(nbs.NBError) as e:
+            c.accel()
+        assert e.value.code == nbs.NB_ESTATE
+        pos, vel, m = system(10, seed=1)
+        c.load(pos, vel, m)
+        for bad in [(3, 0.1, 1), (2, 0.0, 1), (2, float("nan"), 1), (2, 0.1, -1)]:
+            with pytest.raises(nbs.NBError) as e:
+                c.step(*bad)
+            assert e.value.code == nbs.NB_EINVAL
+        p11, v11, m11 = system(11, seed=1)
+        with pytest.raises(nbs.NBError) as e:
+            c.load(p11, v11, m11)
+        assert e.value.code == nbs.NB_EINVAL
+        c.step(6, 0.01, 0)
+
+
+def test_device_pointer_io_matches_host(nbs):
+    torch = pytest.importorskip("torch")
+    n = 3000
+    pos, vel, m = system(n, seed=19)
+    with nbs.Context(n, eps=1e-3, precision="ds") as c:
+        c.load(pos, vel, m)
+        a_host = c.accel()
+        tp = torch.from_numpy(pos).cuda()
+        tv = torch.from_numpy(vel).cuda()
+        tm = torch.from_numpy(m).cuda()
+        c.load_device(n, tp, tv, tm)
+        out = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        c.accel_device(out)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy(), a_host)
+        gp = torch.empty_like(tp)
+        gv = torch.empty_like(tv)
+        c.get_state_device(gp, gv)
+        np.testing.assert_array_equal(gp.cpu().numpy(), pos)
+
+
+def test_profiling_counts_pair_launches(nbs):
+    n = 2048
+    pos, vel, m = system(n, seed=23)
+    with nbs.Context(n, eps=1e-3, precision="ds") as c:
+        c.load(pos, vel, m)
+        c.prof_enable(True)
+        c.step(6, 1 / 512, 3)
+        c.accel()
+        p = c.prof_read()
+    assert p["pair_launches"] == 3 * 7 + 1
+    assert p["interactions"] == (3 * 7 + 1) * n * n
+    assert p["pair_ms"] > 0
+    assert p["kernel_launches"] >= 3 * 16
+
+
+# ------------------------------------------------------------- full sizes
+
+def _sample(n, k, seed):
+    rng = np.random.default_rng(seed)
+    idx = np.unique(np.concatenate([rng.choice(n, k - 4, replace=False), [0, 1, n - 2, n - 1]]))
+    return idx
+
+
+def test_c2_full_size_sampled(nbs, orc):
+    """N = 65536 Plummer (a = 1) at R = 50 in the disk + bulge field, paper
+    softening: mixed and double precision against the oracle on 400 bodies."""
+    n = 65536
+    pos, vel, m = system(n, seed=0, offset=True)
+    eps = ics.paper_softening(n)
+    idx = _sample(n, 400, 1)
+    ref = orc.accel_int_at(pos, m, idx, 1.0, eps)
+    pe = ext_params(orc, eps, True)
+    ext = orc.ext_accel(pe, pos[idx])
+    with nbs.Context(n, eps=eps, precision="ds", ext_on=True) as c:
+        c.load(pos, vel, m)
+        for prec in ("ds", "ds_full", "fp32", "fp64"):
+            c.set_precision(prec)
+            a = c.accel()[idx] - ext
+            err = rel_rms(a, ref)
+            assert err <= TOL[prec], (prec, err)
+
+
+def test_c3_full_size_sampled(nbs, orc):
+    """N = 262144 Plummer with Salpeter masses, eps = 1e-4: the accuracy sweep
+    (double / double-single / float) on 300 sampled bodies."""
+    n = 262144
+    pos, vel, m = system(n, seed=0, salpeter=True)
+    idx = _sample(n, 300, 2)
+    ref = orc.accel_int_at(pos, m, idx, 1.0, 1e-4)
+    with nbs.Context(n, eps=1e-4, precision="ds") as c:
+        c.load(pos, vel, m)
+        for prec in ("ds", "fp32", "fp64"):
+            c.set_precision(prec)
+            a = c.accel()[idx]
+            assert rel_rms(a, ref) <= TOL[prec], (prec, rel_rms(a, ref))

@@ -409,3 +409,12 @@ def test_uniform_sphere_virial_ratio(orc):
     pos, vel, m = ics.uniform_sphere(n, seed=0, q_vir=0.3)
     e = orc.energy(pos, vel, m, _params(orc, eps=ics.paper_softening(n)))
     assert abs(2 * e.K / abs(e.W) - 0.3) < 0.3 * 5 / math.sqrt(n)
+
+
+def test_sampled_sum_matches_full_sum(orc):
+    """The sampled routine used at full size is the same sum as the full one,
+    bit for bit, on the bodies it is asked for."""
+    pos, vel, m = ics.plummer(700, seed=9, masses=ics.salpeter_masses(700, 9))
+    full = orc.accel_int(pos, m, 1.0, 0.01)
+    idx = np.array([0, 5, 699, 350, 5])
+    np.testing.assert_array_equal(orc.accel_int_at(pos, m, idx, 1.0, 0.01), full[idx])
