@@ -69,6 +69,7 @@ __global__ void unpack_kernel(DevState s, const double *__restrict__ pos,
     s.vy[i] = vel[3 * i + 1];
     s.vz[i] = vel[3 * i + 2];
     s.m[i] = mass[i];
+    s.mf[i] = __double2float_rn(mass[i]);   // masses never change after load
 }
 
 __global__ void pack_kernel(DevState s, double *__restrict__ pos, double *__restrict__ vel)
