@@ -159,9 +159,17 @@ __device__ __forceinline__ void split_one(const DevState &s, const Frame &f, int
     s.xh[i] = hx;
     s.yh[i] = hy;
     s.zh[i] = hz;
-    s.xl[i] = __double2float_rn(rx - (double)hx);
-    s.yl[i] = __double2float_rn(ry - (double)hy);
-    s.zl[i] = __double2float_rn(rz - (double)hz);
+    const float lx = __double2float_rn(rx - (double)hx);
+    const float ly = __double2float_rn(ry - (double)hy);
+    const float lz = __double2float_rn(rz - (double)hz);
+    s.xl[i] = lx;
+    s.yl[i] = ly;
+    s.zl[i] = lz;
+    const float m = s.mf[i];
+    s.jd[2 * i] = make_float4(hx, hx, hy, hy);
+    s.jd[2 * i + 1] = make_float4(hz, hz, m, m);
+    s.jl[2 * i] = make_float4(lx, lx, ly, ly);
+    s.jl[2 * i + 1] = make_float4(lz, lz, 0.f, 0.f);
 }
 
 __global__ void split_kernel(DevState s)
@@ -169,8 +177,8 @@ __global__ void split_kernel(DevState s)
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= s.n) return;
     const Frame f = *s.frame;
-    split_one(s, f, i, s.x[i], s.y[i], s.z[i]);
     s.mf[i] = __double2float_rn(s.m[i]);
+    split_one(s, f, i, s.x[i], s.y[i], s.z[i]);
 }
 
 cudaError_t launch_split(const DevState &s, cudaStream_t st)

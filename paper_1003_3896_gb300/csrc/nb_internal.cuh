@@ -36,6 +36,10 @@ struct DevState {
     double *vx = nullptr, *vy = nullptr, *vz = nullptr, *m = nullptr;
     float *xh = nullptr, *yh = nullptr, *zh = nullptr, *mf = nullptr;
     float *xl = nullptr, *yl = nullptr, *zl = nullptr;
+    // j-stream copies, two float4 per body, each coordinate duplicated so a
+    // packed f32x2 operand serves two i bodies: jd = (xh, xh, yh, yh),
+    // (zh, zh, m, m); jl = (xl, xl, yl, yl), (zl, zl, 0, 0).
+    float4 *jd = nullptr, *jl = nullptr;
     double *part = nullptr;     // partial sums [slot][3][cap]
     int64_t part_slots = 0;
     double *red = nullptr;      // block partials of reductions

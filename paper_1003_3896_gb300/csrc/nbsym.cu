@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -114,7 +115,12 @@ PairLaunch choose_pair(const nb_ctx *c, int mode, int64_t n)
     if (mode == PM_FP64)
         pl.I = 1;
     else
-        pl.I = n >= 32768 ? 4 : (n >= 4096 ? 2 : 1);
+        pl.I = n >= 16384 ? 4 : 2;
+    if (const char *env = getenv("NBSYM_PAIR_I")) {
+        // tuning override: bodies per thread of the pair kernel
+        const int I = atoi(env);
+        if (pair_variant_exists(mode, I)) pl.I = I;
+    }
     pl.blocks_per_sm = pair_occupancy(mode, pl.I);
     if (pl.blocks_per_sm < 1) pl.blocks_per_sm = 1;
     int64_t G = (int64_t)c->num_sms * pl.blocks_per_sm;
@@ -171,6 +177,8 @@ void free_state(nb_ctx *c)
     float *d32[] = {s.xh, s.yh, s.zh, s.mf, s.xl, s.yl, s.zl};
     for (float *q : d32)
         if (q) cudaFree(q);
+    if (s.jd) cudaFree(s.jd);
+    if (s.jl) cudaFree(s.jl);
     if (s.frame) cudaFree(s.frame);
     if (s.flag) cudaFree(s.flag);
     s = DevState();
@@ -412,6 +420,8 @@ int nb_create(const nb_params *p, int64_t n_capacity, nb_ctx **out)
     A64(&s.red, s.red_len);
     A64(&s.diag, 16);
     A64(&c->stage, 7 * s.cap);
+    if (ok && cudaMalloc(&s.jd, (size_t)(2 * s.cap) * sizeof(float4)) != cudaSuccess) ok = false;
+    if (ok && cudaMalloc(&s.jl, (size_t)(2 * s.cap) * sizeof(float4)) != cudaSuccess) ok = false;
     if (ok && cudaMalloc(&s.frame, sizeof(Frame)) != cudaSuccess) ok = false;
     if (ok && cudaMalloc(&s.flag, sizeof(int)) != cudaSuccess) ok = false;
     if (ok && cudaEventCreate(&c->pe0) != cudaSuccess) ok = false;

@@ -1,28 +1,31 @@
 // pair.cu -- all-pairs softened gravity (eq. 5; eq. 2 when eps = 0) on sm_103a.
 //
 // Every kernel here walks the same persistent decomposition (Decomp): a grid
-// of G blocks, one contiguous run of (i-block, j-tile) units per block.  A
-// j-tile of TILE bodies is staged in shared memory and broadcast to all
-// threads; each thread owns I i-bodies and accumulates their sums in
-// registers (the tiling of Sect. 3.2 after Nyland et al., with one thread
-// per body generalised to I bodies per thread and the j range split across
-// blocks so every SM gets the same amount of work).  Every pair of the N x N
-// array is evaluated, as in the paper (Sect. 3.2), not N(N-1)/2.
+// of G blocks, one contiguous run of (i-block, j-tile) units per block, so
+// every SM gets the same amount of work whatever N is.  Each thread owns I
+// i-bodies and keeps their sums in registers; every pair of the N x N array
+// is evaluated, as in the paper (Sect. 3.2), not N(N-1)/2.
 //
 // Single-precision family (one template, three modes):
 //   PM_DS_NEAR  float pair arithmetic on coordinates relative to the frame
-//               origin; pairs whose float r^2 falls below frame->th2 are
-//               recomputed with the double-single coordinate difference
+//               origin; pairs whose float r^2 + eps^2 falls below frame->th2
+//               are recomputed with the double-single coordinate difference
 //               (hi_j - hi_i) + (lo_j - lo_i) and their float contribution
 //               replaced; per-tile float sums are folded into double-single
 //               accumulators (Sect. 4.2's software double precision).
 //   PM_DS_FULL  the double-single coordinate difference on every pair.
 //   PM_FP32     float coordinates and float accumulation throughout (per-tile
 //               float sums added in float).
-// Arithmetic is written with explicit round-to-nearest intrinsics so the
-// near-pair fix-up can reproduce the main loop's float contribution bit for
-// bit.  Two j bodies share each packed f32x2 instruction; rsqrt runs on the
-// MUFU pipe (rsqrt.approx).
+//
+// Data movement: no block-wide barrier.  Each warp streams its j bodies in
+// chunks of 32 through a warp-private shared-memory buffer: lane l loads body
+// (chunk + l) one chunk ahead into registers, stores it, and after
+// __syncwarp every lane reads the chunk back as broadcasts.  j bodies are
+// stored pre-duplicated, (x, x, y, y) (z, z, m, m), so one packed f32x2
+// instruction serves two i bodies of the same thread with no register moves.
+// rsqrt runs on the MUFU pipe (rsqrt.approx).  Arithmetic uses explicit
+// round-to-nearest intrinsics so the near-pair fix-up reproduces the main
+// loop's float contribution bit for bit.
 #include "nb_internal.cuh"
 
 namespace nb {
@@ -61,146 +64,165 @@ __device__ __forceinline__ void ds_add(float &hi, float &lo, float t)
     hi = h;
 }
 
-template <int I>
-struct IBodies {
-    int idx[I];
-    float2 nx[I], ny[I], nz[I];      // (-x, -x): hi coordinates, negated, packed twice
-    float2 nlx[I], nly[I], nlz[I];   // lo coordinates, negated (full double-single mode)
+constexpr int CH = 32;            // j bodies per warp chunk
+constexpr int WARPS = TILE / 32;  // warps per block
+
+// Thread-private i bodies, two per packed register pair: pair p holds bodies
+// k = 2p (.x) and k = 2p + 1 (.y), body k = ib0 + tid + k * TILE.
+template <int P>
+struct IPairs {
+    float2 nx[P], ny[P], nz[P];     // negated hi coordinates
+    float2 nlx[P], nly[P], nlz[P];  // negated lo coordinates (full double-single mode)
+    float2 ax[P], ay[P], az[P];     // float sums of the current 128-j tile
 };
 
-// Near-pair fix-up for the 8 j bodies [jj, jj + 8) of the staged tile: for
-// each pair whose float r^2 + eps^2 is below th2, subtract the float
-// contribution the main loop added (recomputed identically) and add the one
-// formed from the double-single coordinate difference.
-template <int I>
-__device__ __forceinline__ void near_fixup(const float *sx, const float *sy, const float *sz,
-                                        const float *sm, int jj, int jglob, int n,
-                                        const IBodies<I> &bi, const float *__restrict__ xl,
-                                        const float *__restrict__ yl,
-                                        const float *__restrict__ zl, float eps2, float th2,
-                                        float2 (&ax)[I], float2 (&ay)[I], float2 (&az)[I])
-{
-#pragma unroll 1
-    for (int q = 0; q < 8; ++q) {
-        const int j = jglob + jj + q;
-        const float xj = sx[jj + q], yj = sy[jj + q], zj = sz[jj + q], mj = sm[jj + q];
-#pragma unroll
-        for (int k = 0; k < I; ++k) {
-            const float dx = __fadd_rn(xj, bi.nx[k].x);
-            const float dy = __fadd_rn(yj, bi.ny[k].x);
-            const float dz = __fadd_rn(zj, bi.nz[k].x);
-            float r2 = __fmaf_rn(dx, dx, eps2);
-            r2 = __fmaf_rn(dy, dy, r2);
-            r2 = __fmaf_rn(dz, dz, r2);
-            if (r2 < th2 && j != bi.idx[k]) {
-                const float ri = rsqrt_mufu(r2);
-                const float s = __fmul_rn(__fmul_rn(mj, ri), __fmul_rn(ri, ri));
-                // i past the end of the system mirrors body n-1 (its result is
-                // discarded); read its lo coordinates from a valid slot
-                const int ic = bi.idx[k] < n ? bi.idx[k] : n - 1;
-                const float ex = __fadd_rn(dx, __fsub_rn(xl[j], xl[ic]));
-                const float ey = __fadd_rn(dy, __fsub_rn(yl[j], yl[ic]));
-                const float ez = __fadd_rn(dz, __fsub_rn(zl[j], zl[ic]));
-                float e2 = __fmaf_rn(ex, ex, eps2);
-                e2 = __fmaf_rn(ey, ey, e2);
-                e2 = __fmaf_rn(ez, ez, e2);
-                const float re = rsqrt_mufu(e2);
-                const float se = __fmul_rn(__fmul_rn(mj, re), __fmul_rn(re, re));
-                const float cx = __fsub_rn(__fmul_rn(ex, se), __fmul_rn(dx, s));
-                const float cy = __fsub_rn(__fmul_rn(ey, se), __fmul_rn(dy, s));
-                const float cz = __fsub_rn(__fmul_rn(ez, se), __fmul_rn(dz, s));
-                if (q & 1) {
-                    ax[k].y = __fadd_rn(ax[k].y, cx);
-                    ay[k].y = __fadd_rn(ay[k].y, cy);
-                    az[k].y = __fadd_rn(az[k].y, cz);
-                } else {
-                    ax[k].x = __fadd_rn(ax[k].x, cx);
-                    ay[k].x = __fadd_rn(ay[k].x, cy);
-                    az[k].x = __fadd_rn(az[k].x, cz);
-                }
-            }
-        }
-    }
-}
-
-// One staged tile: TILE j bodies against the thread's I i bodies, two j per
-// packed instruction.  MASK zeroes the j == i term (eps = 0 diagonal tiles).
-template <int I, int MODE, bool MASK>
-__device__ __forceinline__ void tile_pass(const float *sx, const float *sy, const float *sz,
-                                          const float *sm, const float *slx, const float *sly,
-                                          const float *slz, int jglob, int n, const IBodies<I> &bi,
-                                          const float *__restrict__ xl,
-                                          const float *__restrict__ yl,
-                                          const float *__restrict__ zl, float eps2, float th2,
-                                          float2 (&ax)[I], float2 (&ay)[I], float2 (&az)[I])
+// One chunk of CH j bodies against the thread's 2P i bodies.  Returns a
+// bitmask with bit g set when group g (8 j bodies) held a pair closer than the
+// near-pair threshold.  MASK zeroes the j == i term (eps = 0, diagonal chunks).
+template <int P, int MODE, bool MASK>
+__device__ __forceinline__ unsigned chunk_pass(const float4 (*cb)[4], int j0, int ibase,
+                                               IPairs<P> &ip, float eps2, float th2)
 {
     const float2 e2 = make_float2(eps2, eps2);
+    unsigned gmask = 0;
 #pragma unroll 1
-    for (int jj = 0; jj < TILE; jj += 8) {
+    for (int g = 0; g < CH / 8; ++g) {
         bool near = false;
 #pragma unroll
-        for (int q = 0; q < 8; q += 2) {
-            const float2 xj = *reinterpret_cast<const float2 *>(sx + jj + q);
-            const float2 yj = *reinterpret_cast<const float2 *>(sy + jj + q);
-            const float2 zj = *reinterpret_cast<const float2 *>(sz + jj + q);
-            const float2 mj = *reinterpret_cast<const float2 *>(sm + jj + q);
-            float2 lxj, lyj, lzj;
+        for (int q = 0; q < 8; ++q) {
+            const int jj = g * 8 + q;
+            const float4 A = cb[jj][0];
+            const float4 B = cb[jj][1];
+            const float2 xx = make_float2(A.x, A.y), yy = make_float2(A.z, A.w);
+            const float2 zz = make_float2(B.x, B.y), mm = make_float2(B.z, B.w);
+            float2 lxx, lyy, lzz;
             if (MODE == PM_DS_FULL) {
-                lxj = *reinterpret_cast<const float2 *>(slx + jj + q);
-                lyj = *reinterpret_cast<const float2 *>(sly + jj + q);
-                lzj = *reinterpret_cast<const float2 *>(slz + jj + q);
+                const float4 C = cb[jj][2];
+                const float4 D = cb[jj][3];
+                lxx = make_float2(C.x, C.y);
+                lyy = make_float2(C.z, C.w);
+                lzz = make_float2(D.x, D.y);
             }
 #pragma unroll
-            for (int k = 0; k < I; ++k) {
-                float2 dx = __fadd2_rn(xj, bi.nx[k]);
-                float2 dy = __fadd2_rn(yj, bi.ny[k]);
-                float2 dz = __fadd2_rn(zj, bi.nz[k]);
+            for (int p = 0; p < P; ++p) {
+                float2 dx = __fadd2_rn(xx, ip.nx[p]);
+                float2 dy = __fadd2_rn(yy, ip.ny[p]);
+                float2 dz = __fadd2_rn(zz, ip.nz[p]);
                 if (MODE == PM_DS_FULL) {
-                    dx = __fadd2_rn(dx, __fadd2_rn(lxj, bi.nlx[k]));
-                    dy = __fadd2_rn(dy, __fadd2_rn(lyj, bi.nly[k]));
-                    dz = __fadd2_rn(dz, __fadd2_rn(lzj, bi.nlz[k]));
+                    dx = __fadd2_rn(dx, __fadd2_rn(lxx, ip.nlx[p]));
+                    dy = __fadd2_rn(dy, __fadd2_rn(lyy, ip.nly[p]));
+                    dz = __fadd2_rn(dz, __fadd2_rn(lzz, ip.nlz[p]));
                 }
                 float2 r2 = __ffma2_rn(dx, dx, e2);
                 r2 = __ffma2_rn(dy, dy, r2);
                 r2 = __ffma2_rn(dz, dz, r2);
                 if (MODE == PM_DS_NEAR) near |= (fminf(r2.x, r2.y) < th2);
                 const float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
-                float2 s = __fmul2_rn(__fmul2_rn(mj, ri), __fmul2_rn(ri, ri));
+                float2 s = __fmul2_rn(__fmul2_rn(mm, ri), __fmul2_rn(ri, ri));
                 if (MASK) {
-                    if (jglob + jj + q == bi.idx[k]) s.x = 0.f;
-                    if (jglob + jj + q + 1 == bi.idx[k]) s.y = 0.f;
+                    const int j = j0 + jj;
+                    if (j == ibase + 2 * p * TILE) s.x = 0.f;
+                    if (j == ibase + (2 * p + 1) * TILE) s.y = 0.f;
                 }
-                ax[k] = __ffma2_rn(dx, s, ax[k]);
-                ay[k] = __ffma2_rn(dy, s, ay[k]);
-                az[k] = __ffma2_rn(dz, s, az[k]);
+                ip.ax[p] = __ffma2_rn(dx, s, ip.ax[p]);
+                ip.ay[p] = __ffma2_rn(dy, s, ip.ay[p]);
+                ip.az[p] = __ffma2_rn(dz, s, ip.az[p]);
             }
         }
-        if (MODE == PM_DS_NEAR) {
-            if (__any_sync(0xffffffffu, near))
-                near_fixup<I>(sx, sy, sz, sm, jj, jglob, n, bi, xl, yl, zl, eps2, th2, ax, ay, az);
+        if (MODE == PM_DS_NEAR && near) gmask |= 1u << g;
+    }
+    return gmask;
+}
+
+// Near-pair fix-up for the flagged 8-body groups of a chunk: for each pair
+// whose float r^2 + eps^2 is below th2, subtract the float contribution the
+// main loop added (recomputed identically, element by element) and add the
+// one formed from the double-single coordinate difference.
+template <int P>
+__device__ __noinline__ void near_fixup(const float4 (*cb)[4], unsigned gmask, int j0,
+                                        int ibase, int n, IPairs<P> &ip,
+                                        const float *__restrict__ xl,
+                                        const float *__restrict__ yl,
+                                        const float *__restrict__ zl, float eps2, float th2)
+{
+    while (gmask) {
+        const int g = __ffs(gmask) - 1;
+        gmask &= gmask - 1;
+        for (int q = 0; q < 8; ++q) {
+            const int jj = g * 8 + q;
+            const int j = j0 + jj;
+            const float4 A = cb[jj][0];
+            const float4 B = cb[jj][1];
+            const float xj = A.x, yj = A.z, zj = B.x, mj = B.z;
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int i = ibase + (2 * p + h) * TILE;
+                    const float dx = __fadd_rn(xj, h ? ip.nx[p].y : ip.nx[p].x);
+                    const float dy = __fadd_rn(yj, h ? ip.ny[p].y : ip.ny[p].x);
+                    const float dz = __fadd_rn(zj, h ? ip.nz[p].y : ip.nz[p].x);
+                    float r2 = __fmaf_rn(dx, dx, eps2);
+                    r2 = __fmaf_rn(dy, dy, r2);
+                    r2 = __fmaf_rn(dz, dz, r2);
+                    if (!(r2 < th2) || j == i || j >= n) continue;
+                    const float ri = rsqrt_mufu(r2);
+                    const float s = __fmul_rn(__fmul_rn(mj, ri), __fmul_rn(ri, ri));
+                    // i past the end mirrors body n-1 (result discarded)
+                    const int ic = i < n ? i : n - 1;
+                    const float ex = __fadd_rn(dx, __fsub_rn(xl[j], xl[ic]));
+                    const float ey = __fadd_rn(dy, __fsub_rn(yl[j], yl[ic]));
+                    const float ez = __fadd_rn(dz, __fsub_rn(zl[j], zl[ic]));
+                    float e2 = __fmaf_rn(ex, ex, eps2);
+                    e2 = __fmaf_rn(ey, ey, e2);
+                    e2 = __fmaf_rn(ez, ez, e2);
+                    const float re = rsqrt_mufu(e2);
+                    const float se = __fmul_rn(__fmul_rn(mj, re), __fmul_rn(re, re));
+                    const float cx = __fsub_rn(__fmul_rn(ex, se), __fmul_rn(dx, s));
+                    const float cy = __fsub_rn(__fmul_rn(ey, se), __fmul_rn(dy, s));
+                    const float cz = __fsub_rn(__fmul_rn(ez, se), __fmul_rn(dz, s));
+                    if (h) {
+                        ip.ax[p].y = __fadd_rn(ip.ax[p].y, cx);
+                        ip.ay[p].y = __fadd_rn(ip.ay[p].y, cy);
+                        ip.az[p].y = __fadd_rn(ip.az[p].y, cz);
+                    } else {
+                        ip.ax[p].x = __fadd_rn(ip.ax[p].x, cx);
+                        ip.ay[p].x = __fadd_rn(ip.ay[p].x, cy);
+                        ip.az[p].x = __fadd_rn(ip.az[p].x, cz);
+                    }
+                }
+            }
         }
     }
 }
 
-template <int I, int MODE>
+template <int P, int MODE>
 __global__ void __launch_bounds__(TILE) pair_sp_kernel(
+    const float4 *__restrict__ jd, const float4 *__restrict__ jl,
     const float *__restrict__ xh, const float *__restrict__ yh, const float *__restrict__ zh,
-    const float *__restrict__ mf, const float *__restrict__ xl, const float *__restrict__ yl,
-    const float *__restrict__ zl, const Frame *__restrict__ frame, Decomp d, float eps2,
-    int mask_self, double G, double *__restrict__ part, int64_t cap)
+    const float *__restrict__ xl, const float *__restrict__ yl, const float *__restrict__ zl,
+    const Frame *__restrict__ frame, Decomp d, float eps2, int mask_self, double G,
+    double *__restrict__ part, int64_t cap)
 {
+    constexpr int I = 2 * P;
     constexpr bool FULL = (MODE == PM_DS_FULL);
     constexpr bool DSACC = (MODE != PM_FP32);
-    __shared__ __align__(16) float sx[TILE], sy[TILE], sz[TILE], sm[TILE];
-    __shared__ __align__(16) float slx[FULL ? TILE : 2], sly[FULL ? TILE : 2],
-        slz[FULL ? TILE : 2];
+    constexpr int NV = FULL ? 4 : 2;
+    __shared__ __align__(16) float4 cbuf[WARPS][CH][4];
+    __shared__ float acc_sh[6 * I][TILE];   // per-thread running sums: hi x,y,z then lo x,y,z
 
     const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int w = tid >> 5;
+    const float4(*cb)[4] = cbuf[w];
     const int n = (int)d.n;
     const int64_t g = blockIdx.x;
     int64_t u = d.U(g);
     const int64_t uend = d.U(g + 1);
     const float th2 = (MODE == PM_DS_NEAR) ? frame->th2 : 0.f;
+    const float4 far4 = make_float4(FAR_F, FAR_F, FAR_F, FAR_F);
+    const float4 farm = make_float4(FAR_F, FAR_F, 0.f, 0.f);
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
 
     while (u < uend) {
         const int64_t b = u / d.ntiles;
@@ -208,88 +230,98 @@ __global__ void __launch_bounds__(TILE) pair_sp_kernel(
         const int t1 = (int)((int64_t)t0 + (uend - u) < d.ntiles ? t0 + (uend - u) : d.ntiles);
         const int64_t slot = g - d.gfirst(b);
         const int ib0 = (int)(b * d.ipb);
+        const int ibase = ib0 + tid;
 
-        IBodies<I> bi;
-        float hx[I], hy[I], hz[I], lx[I], ly[I], lz[I];
-        float2 ax[I], ay[I], az[I];
+        IPairs<P> ip;
 #pragma unroll
-        for (int k = 0; k < I; ++k) {
-            const int i = ib0 + tid + k * TILE;
-            const int ic = i < n ? i : n - 1;
-            bi.idx[k] = i;
-            const float x = xh[ic], y = yh[ic], z = zh[ic];
-            bi.nx[k] = make_float2(-x, -x);
-            bi.ny[k] = make_float2(-y, -y);
-            bi.nz[k] = make_float2(-z, -z);
+        for (int p = 0; p < P; ++p) {
+            const int ia = ibase + 2 * p * TILE, ib = ia + TILE;
+            const int ca = ia < n ? ia : n - 1, cb2 = ib < n ? ib : n - 1;
+            ip.nx[p] = make_float2(-xh[ca], -xh[cb2]);
+            ip.ny[p] = make_float2(-yh[ca], -yh[cb2]);
+            ip.nz[p] = make_float2(-zh[ca], -zh[cb2]);
             if (FULL) {
-                const float a = xl[ic], c = yl[ic], e = zl[ic];
-                bi.nlx[k] = make_float2(-a, -a);
-                bi.nly[k] = make_float2(-c, -c);
-                bi.nlz[k] = make_float2(-e, -e);
+                ip.nlx[p] = make_float2(-xl[ca], -xl[cb2]);
+                ip.nly[p] = make_float2(-yl[ca], -yl[cb2]);
+                ip.nlz[p] = make_float2(-zl[ca], -zl[cb2]);
             }
-            hx[k] = hy[k] = hz[k] = lx[k] = ly[k] = lz[k] = 0.f;
-            ax[k] = ay[k] = az[k] = make_float2(0.f, 0.f);
+            ip.ax[p] = ip.ay[p] = ip.az[p] = make_float2(0.f, 0.f);
         }
-
-        for (int t = t0; t < t1; ++t) {
-            const int jglob = t * TILE;
-            const int j = jglob + tid;
-            __syncthreads();
-            if (j < n) {
-                sx[tid] = xh[j];
-                sy[tid] = yh[j];
-                sz[tid] = zh[j];
-                sm[tid] = mf[j];
-                if (FULL) {
-                    slx[tid] = xl[j];
-                    sly[tid] = yl[j];
-                    slz[tid] = zl[j];
-                }
-            } else {
-                sx[tid] = FAR_F;
-                sy[tid] = FAR_F;
-                sz[tid] = FAR_F;
-                sm[tid] = 0.f;
-                if (FULL) slx[tid] = sly[tid] = slz[tid] = 0.f;
-            }
-            __syncthreads();
-            const bool diag = mask_self && jglob < ib0 + d.ipb && jglob + TILE > ib0;
-            if (diag)
-                tile_pass<I, MODE, true>(sx, sy, sz, sm, slx, sly, slz, jglob, n, bi, xl, yl, zl,
-                                         eps2, th2, ax, ay, az);
-            else
-                tile_pass<I, MODE, false>(sx, sy, sz, sm, slx, sly, slz, jglob, n, bi, xl, yl, zl,
-                                          eps2, th2, ax, ay, az);
 #pragma unroll
-            for (int k = 0; k < I; ++k) {
-                const float tx = __fadd_rn(ax[k].x, ax[k].y);
-                const float ty = __fadd_rn(ay[k].x, ay[k].y);
-                const float tz = __fadd_rn(az[k].x, az[k].y);
-                if (DSACC) {
-                    ds_add(hx[k], lx[k], tx);
-                    ds_add(hy[k], ly[k], ty);
-                    ds_add(hz[k], lz[k], tz);
-                } else {
-                    // pure float: tile sums added in float (two-level summation)
-                    hx[k] = __fadd_rn(hx[k], tx);
-                    hy[k] = __fadd_rn(hy[k], ty);
-                    hz[k] = __fadd_rn(hz[k], tz);
+        for (int r = 0; r < 6 * I; ++r) acc_sh[r][tid] = 0.f;
+
+        const int J0 = t0 * TILE, J1 = t1 * TILE;
+        float4 pf[4];
+        {
+            const int j = J0 + lane;
+            pf[0] = j < n ? jd[2 * j] : far4;
+            pf[1] = j < n ? jd[2 * j + 1] : farm;
+            if (FULL) {
+                pf[2] = j < n ? jl[2 * j] : zero4;
+                pf[3] = j < n ? jl[2 * j + 1] : zero4;
+            }
+        }
+        for (int jc = J0; jc < J1; jc += CH) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) cbuf[w][lane][v] = pf[v];
+            __syncwarp();
+            if (jc + CH < J1) {
+                const int j = jc + CH + lane;
+                pf[0] = j < n ? jd[2 * j] : far4;
+                pf[1] = j < n ? jd[2 * j + 1] : farm;
+                if (FULL) {
+                    pf[2] = j < n ? jl[2 * j] : zero4;
+                    pf[3] = j < n ? jl[2 * j + 1] : zero4;
                 }
-                ax[k] = ay[k] = az[k] = make_float2(0.f, 0.f);
+            }
+            const bool diag = mask_self && jc < ib0 + d.ipb && jc + CH > ib0;
+            unsigned gm;
+            if (diag)
+                gm = chunk_pass<P, MODE, true>(cb, jc, ibase, ip, eps2, th2);
+            else
+                gm = chunk_pass<P, MODE, false>(cb, jc, ibase, ip, eps2, th2);
+            if (MODE == PM_DS_NEAR) {
+                if (__any_sync(0xffffffffu, gm != 0))
+                    near_fixup<P>(cb, gm, jc, ibase, n, ip, xl, yl, zl, eps2, th2);
+            }
+            __syncwarp();
+            if (((jc + CH - J0) & (TILE - 1)) == 0) {
+                // end of a 128-j tile: fold the tile sums into the running sums
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int k = 2 * p + h;
+                        const float t[3] = {h ? ip.ax[p].y : ip.ax[p].x,
+                                            h ? ip.ay[p].y : ip.ay[p].x,
+                                            h ? ip.az[p].y : ip.az[p].x};
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            float hi = acc_sh[c * I + k][tid];
+                            if (DSACC) {
+                                float lo = acc_sh[(3 + c) * I + k][tid];
+                                ds_add(hi, lo, t[c]);
+                                acc_sh[(3 + c) * I + k][tid] = lo;
+                            } else {
+                                hi = __fadd_rn(hi, t[c]);
+                            }
+                            acc_sh[c * I + k][tid] = hi;
+                        }
+                    }
+                    ip.ax[p] = ip.ay[p] = ip.az[p] = make_float2(0.f, 0.f);
+                }
             }
         }
 
 #pragma unroll
         for (int k = 0; k < I; ++k) {
-            const int i = bi.idx[k];
+            const int i = ibase + k * TILE;
             if (i < n) {
-                const double rx = (double)hx[k] + (double)lx[k];
-                const double ry = (double)hy[k] + (double)ly[k];
-                const double rz = (double)hz[k] + (double)lz[k];
-                double *p = part + (slot * 3) * cap + i;
-                p[0] = G * rx;
-                p[cap] = G * ry;
-                p[2 * cap] = G * rz;
+                double *o = part + (slot * 3) * cap + i;
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    o[c * cap] = G * ((double)acc_sh[c * I + k][tid] +
+                                      (double)acc_sh[(3 + c) * I + k][tid]);
             }
         }
         u += t1 - t0;
@@ -297,7 +329,10 @@ __global__ void __launch_bounds__(TILE) pair_sp_kernel(
 }
 
 // Double-precision pair kernel: the plain FP64 baseline (Sect. 3.2's DP mode
-// with structures of four doubles), same tiling and decomposition.
+// with structures of four doubles).  A j-tile of TILE bodies is staged in
+// shared memory per block and broadcast to one i body per thread.  With POT
+// it sums the softened potential m_j / sqrt(r^2 + eps^2) of eq. 4 instead
+// (j = i always excluded), for the energy diagnostic.
 template <int I, bool POT>
 __global__ void __launch_bounds__(TILE) pair_fp64_kernel(
     const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
@@ -388,19 +423,20 @@ __global__ void __launch_bounds__(TILE) pair_fp64_kernel(
 
 // ---- variant table -----------------------------------------------------------
 
-typedef void (*sp_kernel_t)(const float *, const float *, const float *, const float *,
-                            const float *, const float *, const float *, const Frame *,
-                            Decomp, float, int, double, double *, int64_t);
+typedef void (*sp_kernel_t)(const float4 *, const float4 *, const float *, const float *,
+                            const float *, const float *, const float *, const float *,
+                            const Frame *, Decomp, float, int, double, double *, int64_t);
 typedef void (*dp_kernel_t)(const double *, const double *, const double *, const double *,
                             Decomp, double, int, double, double *, int64_t);
 
+// I (bodies per thread) = 2P for the single-precision family.
 static sp_kernel_t sp_variant(int mode, int I)
 {
 #define NB_SP(M, II) \
-    if (mode == M && I == II) return pair_sp_kernel<II, M>;
-    NB_SP(PM_DS_NEAR, 1) NB_SP(PM_DS_NEAR, 2) NB_SP(PM_DS_NEAR, 4)
-    NB_SP(PM_DS_FULL, 1) NB_SP(PM_DS_FULL, 2) NB_SP(PM_DS_FULL, 4)
-    NB_SP(PM_FP32, 1) NB_SP(PM_FP32, 2) NB_SP(PM_FP32, 4)
+    if (mode == M && I == II) return pair_sp_kernel<II / 2, M>;
+    NB_SP(PM_DS_NEAR, 2) NB_SP(PM_DS_NEAR, 4) NB_SP(PM_DS_NEAR, 8)
+    NB_SP(PM_DS_FULL, 2) NB_SP(PM_DS_FULL, 4)
+    NB_SP(PM_FP32, 2) NB_SP(PM_FP32, 4) NB_SP(PM_FP32, 8)
 #undef NB_SP
     return nullptr;
 }
@@ -443,8 +479,8 @@ cudaError_t launch_pair(const DevState &s, const PairLaunch &pl, double G, doubl
     } else {
         sp_kernel_t k = sp_variant(pl.mode, pl.I);
         if (!k) return cudaErrorInvalidValue;
-        k<<<grid, block, 0, st>>>(s.xh, s.yh, s.zh, s.mf, s.xl, s.yl, s.zl, s.frame, pl.d,
-                                  (float)(eps * eps), mask_self, G, s.part, s.cap);
+        k<<<grid, block, 0, st>>>(s.jd, s.jl, s.xh, s.yh, s.zh, s.xl, s.yl, s.zl, s.frame,
+                                  pl.d, (float)(eps * eps), mask_self, G, s.part, s.cap);
     }
     return cudaGetLastError();
 }
