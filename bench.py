@@ -180,6 +180,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=65536)
     ap.add_argument("--precision", default="ds", choices=["ds", "ds_full", "fp32", "fp64"])
+    ap.add_argument("--near-frac", type=float, default=0.0,
+                    help="mixed mode near-pair radius in units of R_rms / N^(1/3) (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -209,7 +211,7 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     ctx = nbsym.Context(n, eps=eps, precision=args.precision, ext_on=True, device=local,
-                        stream=stream.cuda_stream)
+                        stream=stream.cuda_stream, near_frac=args.near_frac)
     ctx.load(pos, vel, m)
     for _ in range(args.warmup):
         ctx.step(6, dt, 1)

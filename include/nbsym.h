@@ -80,9 +80,11 @@ typedef struct {
     int device;        /* CUDA device ordinal */
     void *stream;      /* cudaStream_t to run on; NULL: the context creates
                           and owns a non-blocking stream */
-    double near_frac;  /* NB_DS only: pairs closer than near_frac times the
-                          system's rms radius get the double-single coordinate
-                          difference; <= 0 selects the default 0.03 */
+    double near_frac;  /* NB_DS only: pairs closer than near_frac * R_rms /
+                          N^{1/3} (R_rms = mass-weighted rms radius about the
+                          centre of mass, so the radius scales with the mean
+                          spacing) get the double-single coordinate
+                          difference; <= 0 selects the default 0.4 */
 } nb_params;
 
 /* Diagnostics of Sect. 4.1 (eq. 9-10 use E and L):

@@ -135,7 +135,11 @@ __global__ void frame_final_kernel(DevState s, double near_frac, double eps)
         f.cz = M > 0 ? v[3] / M : 0.0;
         double r2 = M > 0 ? v[4] / M - (f.cx * f.cx + f.cy * f.cy + f.cz * f.cz) : 0.0;
         f.r2rms = r2 > 0 ? r2 : 0.0;
-        f.th2 = (float)(near_frac * near_frac * f.r2rms + eps * eps);
+        // near-pair radius: near_frac times the rms radius over N^{1/3}, a
+        // mean-spacing scale like the paper's softening rule (Sect. 2), so
+        // the expected number of near neighbours per body is independent of N
+        const double spacing2 = f.r2rms / cbrt((double)s.n * (double)s.n);
+        f.th2 = (float)(near_frac * near_frac * spacing2 + eps * eps);
         f.pad = 0.f;
         *s.frame = f;
     }

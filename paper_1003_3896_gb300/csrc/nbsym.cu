@@ -156,7 +156,7 @@ ExtField ext_of(const nb_params &p)
     return e;
 }
 
-double near_frac_of(const nb_params &p) { return p.near_frac > 0 ? p.near_frac : 0.03; }
+double near_frac_of(const nb_params &p) { return p.near_frac > 0 ? p.near_frac : 0.4; }
 
 void free_graphs(nb_ctx *c)
 {
