@@ -276,6 +276,7 @@ def main():
     fp64_rate = p64["interactions"] / (p64["pair_ms"] * 1e-3) / 1e9
 
     clocks = clk.summary()
+    peaks = nbsym.measure_peaks(local)
     achieved = FLOPS_PER_PAIR * prof["interactions"] / (prof["pair_ms"] * 1e-3) / 1e12
     peak = fp32_peak_tflops(sms, 2070.0)
     sustained_mhz = clocks.get("sm_mhz") or 2070.0
@@ -291,6 +292,9 @@ def main():
                      "kernel": f"pair_sp_kernel ({args.precision})",
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max clock)",
                      "frac_at_sampled_clock": achieved / fp32_peak_tflops(sms, sustained_mhz),
+                     "frac_of_measured_fp32": achieved / max(peaks["ffma_tflops"],
+                                                             peaks["ffma2_tflops"]),
+                     "measured_peaks": peaks,
                      "pair_kernel_ms_mean": prof["pair_ms"] / max(1, prof["pair_launches"]),
                      "pair_launches": prof["pair_launches"]},
         "fp64_kernel": {"value": fp64_rate, "unit": UNIT},

@@ -106,6 +106,18 @@ typedef struct {
                                  profiling was on (graph nodes included) */
 } nb_prof_t;
 
+/* Measured arithmetic peaks of one device (see nb_measure_peaks). */
+typedef struct {
+    int sm_count;
+    double ffma_tflops;     /* scalar FP32 FMA, 2 flops each */
+    double ffma2_tflops;    /* packed f32x2 FMA, 4 flops each */
+    double dfma_tflops;     /* FP64 FMA, 2 flops each */
+    double rsqrt_gops;      /* MUFU reciprocal square roots per second, 1e9 */
+    double pairmix_gpairs;  /* the mixed pair kernel's arithmetic alone (packed
+                               sub/FMA/mul + MUFU rsqrt per pair, operands in
+                               registers), 1e9 pair interactions per second */
+} nb_peaks_t;
+
 /* Library ABI version (NB_ABI_VERSION of the build). */
 int nb_abi_version(void);
 
@@ -181,6 +193,14 @@ int nb_prof_enable(nb_ctx *ctx, int on);
 
 /* Read the counters accumulated since nb_prof_enable(ctx, 1). */
 int nb_prof_read(nb_ctx *ctx, nb_prof_t *out);
+
+/* Measure the arithmetic peaks the pair kernels are bounded by (the
+ * denominators of their plain-ALU roofline; the paper quotes nominal SP/DP
+ * peaks, Sect. 3.1): each micro-kernel runs independent FMA / MUFU chains on
+ * every SM for a few milliseconds, timed with CUDA events (best of three).
+ * Allocates 64 bytes of device memory and a stream for the duration of the
+ * call.  Errors: NB_EINVAL (NULL out, bad device), NB_ECUDA. */
+int nb_measure_peaks(int device, nb_peaks_t *out);
 
 /* Release the context and all its device memory.  NULL-safe. */
 void nb_destroy(nb_ctx *ctx);

@@ -139,7 +139,7 @@ __device__ __forceinline__ unsigned chunk_pass(const float4 (*cb)[4], int j0, in
 // main loop added (recomputed identically, element by element) and add the
 // one formed from the double-single coordinate difference.
 template <int P>
-__device__ __noinline__ void near_fixup(const float4 (*cb)[4], unsigned gmask, int j0,
+__device__ __forceinline__ void near_fixup(const float4 (*cb)[4], unsigned gmask, int j0,
                                         int ibase, int n, IPairs<P> &ip,
                                         const float *__restrict__ xl,
                                         const float *__restrict__ yl,
@@ -196,8 +196,12 @@ __device__ __noinline__ void near_fixup(const float4 (*cb)[4], unsigned gmask, i
     }
 }
 
+// Resident blocks per SM the register allocation is bounded for: 2P bodies per
+// thread trade registers against shared-memory broadcasts per pair.
+__host__ __device__ constexpr int sp_min_blocks(int P) { return P == 1 ? 8 : (P == 2 ? 6 : 3); }
+
 template <int P, int MODE>
-__global__ void __launch_bounds__(TILE) pair_sp_kernel(
+__global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
     const float4 *__restrict__ jd, const float4 *__restrict__ jl,
     const float *__restrict__ xh, const float *__restrict__ yh, const float *__restrict__ zh,
     const float *__restrict__ xl, const float *__restrict__ yl, const float *__restrict__ zl,

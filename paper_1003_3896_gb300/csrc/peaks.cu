@@ -1,0 +1,194 @@
+// peaks.cu -- measured arithmetic peaks of the device, the denominators of
+// the pair kernels' roofline (plain ALU bound: FP32 FMA pipe, MUFU, FP64).
+//
+// Each kernel runs CHAINS independent dependency chains per thread for ITERS
+// iterations on a grid of 8 resident 256-thread blocks per SM, so the pipe,
+// not latency, is the limit.  Results feed a dummy store so nothing is
+// eliminated.  Timed with CUDA events, best of three launches.
+#include <cuda_runtime.h>
+
+#include "nb_internal.cuh"
+#include "../../include/nbsym.h"
+
+namespace {
+
+constexpr int CHAINS = 8;
+constexpr int ITERS = 2048;
+constexpr int PT = 256;
+
+__global__ void __launch_bounds__(PT) k_ffma(float *out, float b, float c)
+{
+    float a[CHAINS];
+#pragma unroll
+    for (int k = 0; k < CHAINS; ++k) a[k] = threadIdx.x * 1e-3f + k;
+    for (int it = 0; it < ITERS; ++it)
+#pragma unroll
+        for (int k = 0; k < CHAINS; ++k) a[k] = __fmaf_rn(a[k], b, c);
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < CHAINS; ++k) s += a[k];
+    if (s == 1234.5f) out[0] = s;
+}
+
+__global__ void __launch_bounds__(PT) k_ffma2(float *out, float b, float c)
+{
+    float2 a[CHAINS];
+    const float2 bb = make_float2(b, b), cc = make_float2(c, c);
+#pragma unroll
+    for (int k = 0; k < CHAINS; ++k) a[k] = make_float2(threadIdx.x * 1e-3f + k, k * 0.5f);
+    for (int it = 0; it < ITERS; ++it)
+#pragma unroll
+        for (int k = 0; k < CHAINS; ++k) a[k] = __ffma2_rn(a[k], bb, cc);
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < CHAINS; ++k) s += a[k].x + a[k].y;
+    if (s == 1234.5f) out[0] = s;
+}
+
+__global__ void __launch_bounds__(PT) k_dfma(float *out, double b, double c)
+{
+    double a[CHAINS];
+#pragma unroll
+    for (int k = 0; k < CHAINS; ++k) a[k] = threadIdx.x * 1e-3 + k;
+    for (int it = 0; it < ITERS / 16; ++it)
+#pragma unroll
+        for (int k = 0; k < CHAINS; ++k) a[k] = fma(a[k], b, c);
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < CHAINS; ++k) s += a[k];
+    if (s == 1234.5) out[0] = (float)s;
+}
+
+__device__ __forceinline__ float mufu_rsqrt(float x)
+{
+    float y;
+    asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__global__ void __launch_bounds__(PT) k_mufu(float *out, float b)
+{
+    float a[CHAINS];
+#pragma unroll
+    for (int k = 0; k < CHAINS; ++k) a[k] = 1.0f + threadIdx.x * 1e-3f + k;
+    for (int it = 0; it < ITERS / 4; ++it)
+#pragma unroll
+        for (int k = 0; k < CHAINS; ++k) a[k] = mufu_rsqrt(a[k]) + b;
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < CHAINS; ++k) s += a[k];
+    if (s == 1234.5f) out[0] = s;
+}
+
+// The mixed pair kernel's arithmetic for two i bodies against a stream of
+// j bodies held in registers: 3 FADD2, 3 FFMA2 (r^2), 2 MUFU, 3 FMUL2,
+// 3 FFMA2 (accumulate) per two pairs; no memory traffic.
+__global__ void __launch_bounds__(PT) k_pairmix(float *out, float eps2)
+{
+    float2 nx[2], ny[2], nz[2], ax[2], ay[2], az[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        nx[p] = make_float2(-0.1f * p, -0.2f * p - threadIdx.x * 1e-4f);
+        ny[p] = make_float2(0.3f, -0.1f);
+        nz[p] = make_float2(0.05f * p, 0.2f);
+        ax[p] = ay[p] = az[p] = make_float2(0.f, 0.f);
+    }
+    const float2 e2 = make_float2(eps2, eps2);
+    float2 xx = make_float2(0.5f, 0.5f), yy = make_float2(0.25f, 0.25f),
+           zz = make_float2(-0.75f, -0.75f), mm = make_float2(1e-3f, 1e-3f);
+    const float2 step = make_float2(1e-6f, 1e-6f);
+    for (int it = 0; it < ITERS / 4; ++it) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                const float2 dx = __fadd2_rn(xx, nx[p]);
+                const float2 dy = __fadd2_rn(yy, ny[p]);
+                const float2 dz = __fadd2_rn(zz, nz[p]);
+                float2 r2 = __ffma2_rn(dx, dx, e2);
+                r2 = __ffma2_rn(dy, dy, r2);
+                r2 = __ffma2_rn(dz, dz, r2);
+                const float2 ri = make_float2(mufu_rsqrt(r2.x), mufu_rsqrt(r2.y));
+                const float2 s = __fmul2_rn(__fmul2_rn(mm, ri), __fmul2_rn(ri, ri));
+                ax[p] = __ffma2_rn(dx, s, ax[p]);
+                ay[p] = __ffma2_rn(dy, s, ay[p]);
+                az[p] = __ffma2_rn(dz, s, az[p]);
+            }
+            xx = __fadd2_rn(xx, step);
+        }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) s += ax[p].x + ay[p].y + az[p].x;
+    if (s == 1234.5f) out[0] = s;
+}
+
+template <typename F>
+int time_best(F launch, cudaStream_t st, float *ms_out)
+{
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return -1;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return -1;
+    }
+    float best = 1e30f;
+    for (int r = 0; r < 4; ++r) {
+        cudaEventRecord(a, st);
+        launch();
+        cudaEventRecord(b, st);
+        if (cudaEventSynchronize(b) != cudaSuccess) break;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        if (r > 0 && ms < best) best = ms;   // first launch is a warm-up
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *ms_out = best;
+    return cudaGetLastError() == cudaSuccess && best < 1e29f ? 0 : -1;
+}
+
+}  // namespace
+
+extern "C" int nb_measure_peaks(int device, nb_peaks_t *out)
+{
+    if (!out) return NB_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return NB_EINVAL;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(device);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    float *dummy = nullptr;
+    cudaStream_t st = nullptr;
+    int rc = NB_OK;
+    if (cudaMalloc(&dummy, 64) != cudaSuccess || cudaStreamCreate(&st) != cudaSuccess) {
+        rc = NB_ECUDA;
+    } else {
+        const dim3 grid(sms * 8), block(PT);
+        const double threads = (double)grid.x * PT;
+        float ms = 0;
+        out->sm_count = sms;
+        if (time_best([&] { k_ffma<<<grid, block, 0, st>>>(dummy, 0.999f, 1e-3f); }, st, &ms))
+            rc = NB_ECUDA;
+        out->ffma_tflops = 2.0 * CHAINS * ITERS * threads / (ms * 1e-3) / 1e12;
+        if (time_best([&] { k_ffma2<<<grid, block, 0, st>>>(dummy, 0.999f, 1e-3f); }, st, &ms))
+            rc = NB_ECUDA;
+        out->ffma2_tflops = 4.0 * CHAINS * ITERS * threads / (ms * 1e-3) / 1e12;
+        if (time_best([&] { k_dfma<<<grid, block, 0, st>>>(dummy, 0.999, 1e-3); }, st, &ms))
+            rc = NB_ECUDA;
+        out->dfma_tflops = 2.0 * CHAINS * (ITERS / 16) * threads / (ms * 1e-3) / 1e12;
+        if (time_best([&] { k_mufu<<<grid, block, 0, st>>>(dummy, 1.0f); }, st, &ms))
+            rc = NB_ECUDA;
+        out->rsqrt_gops = (double)CHAINS * (ITERS / 4) * threads / (ms * 1e-3) / 1e9;
+        if (time_best([&] { k_pairmix<<<grid, block, 0, st>>>(dummy, 1e-6f); }, st, &ms))
+            rc = NB_ECUDA;
+        out->pairmix_gpairs = 16.0 * (ITERS / 4) * threads / (ms * 1e-3) / 1e9;
+    }
+    if (st) cudaStreamDestroy(st);
+    if (dummy) cudaFree(dummy);
+    cudaSetDevice(prev);
+    return rc;
+}

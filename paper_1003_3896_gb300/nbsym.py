@@ -44,6 +44,12 @@ class ProfT(C.Structure):
                 ("interactions", C.c_int64), ("kernel_launches", C.c_int64)]
 
 
+class PeaksT(C.Structure):
+    _fields_ = [("sm_count", C.c_int), ("ffma_tflops", C.c_double),
+                ("ffma2_tflops", C.c_double), ("dfma_tflops", C.c_double),
+                ("rsqrt_gops", C.c_double), ("pairmix_gpairs", C.c_double)]
+
+
 _dp = C.POINTER(C.c_double)
 _vp = C.c_void_p
 _ctxp = C.c_void_p
@@ -74,6 +80,14 @@ nb_set_precision = _sig("nb_set_precision", C.c_int, _ctxp, C.c_int)
 nb_prof_enable = _sig("nb_prof_enable", C.c_int, _ctxp, C.c_int)
 nb_prof_read = _sig("nb_prof_read", C.c_int, _ctxp, C.POINTER(ProfT))
 nb_destroy = _sig("nb_destroy", None, _ctxp)
+nb_measure_peaks = _sig("nb_measure_peaks", C.c_int, C.c_int, C.POINTER(PeaksT))
+
+
+def measure_peaks(device: int = 0) -> dict:
+    """Measured FP32 (scalar / packed), FP64 and MUFU peaks of a device."""
+    p = PeaksT()
+    check(nb_measure_peaks(int(device), C.byref(p)))
+    return {k: getattr(p, k) for k, _ in PeaksT._fields_}
 
 
 class NBError(RuntimeError):

@@ -324,3 +324,14 @@ def test_c3_full_size_sampled(nbs, orc):
             c.set_precision(prec)
             a = c.accel()[idx]
             assert rel_rms(a, ref) <= TOL[prec], (prec, rel_rms(a, ref))
+
+
+def test_measured_peaks_are_plausible(nbs):
+    """The peak micro-kernels run and report rates within physical bounds of a
+    GPU with this SM count (<= 128 FP32 lanes x 2 flops x 2.2 GHz per SM)."""
+    p = nbs.measure_peaks(0)
+    cap = p["sm_count"] * 128 * 2 * 2.2e9 / 1e12
+    for k in ("ffma_tflops", "ffma2_tflops"):
+        assert 0.2 * cap < p[k] <= 2.05 * cap, (k, p[k], cap)
+    assert 0 < p["dfma_tflops"] < cap
+    assert p["rsqrt_gops"] > 0 and p["pairmix_gpairs"] > 0
