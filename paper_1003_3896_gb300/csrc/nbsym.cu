@@ -115,7 +115,9 @@ PairLaunch choose_pair(const nb_ctx *c, int mode, int64_t n)
     if (mode == PM_FP64)
         pl.I = 1;
     else
-        pl.I = n >= 16384 ? 4 : 2;
+        // measured at N = 65536: mixed is fastest at 4 bodies per thread, pure
+        // float (no near-pair test, fewer live registers) at 8
+        pl.I = n < 16384 ? 2 : (mode == PM_FP32 ? 8 : 4);
     if (const char *env = getenv("NBSYM_PAIR_I")) {
         // tuning override: bodies per thread of the pair kernel
         const int I = atoi(env);

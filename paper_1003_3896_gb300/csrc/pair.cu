@@ -51,6 +51,14 @@ __device__ __forceinline__ float rsqrt_mufu(float x)
     return y;
 }
 
+// Minimum of three floats in one instruction (three-input min, sm_100+).
+__device__ __forceinline__ float fmin3(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // Add float t to the double-single number (hi, lo): Knuth's two-sum of hi and
 // t, error folded into lo, then Dekker's fast two-sum to renormalise.
 __device__ __forceinline__ void ds_add(float &hi, float &lo, float t)
@@ -85,9 +93,9 @@ __device__ __forceinline__ unsigned chunk_pass(const float4 (*cb)[4], int j0, in
 {
     const float2 e2 = make_float2(eps2, eps2);
     unsigned gmask = 0;
-#pragma unroll 1
+#pragma unroll
     for (int g = 0; g < CH / 8; ++g) {
-        bool near = false;
+        float rmin = 3.0e38f;   // smallest float r^2 + eps^2 of the group
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int jj = g * 8 + q;
@@ -116,7 +124,7 @@ __device__ __forceinline__ unsigned chunk_pass(const float4 (*cb)[4], int j0, in
                 float2 r2 = __ffma2_rn(dx, dx, e2);
                 r2 = __ffma2_rn(dy, dy, r2);
                 r2 = __ffma2_rn(dz, dz, r2);
-                if (MODE == PM_DS_NEAR) near |= (fminf(r2.x, r2.y) < th2);
+                if (MODE == PM_DS_NEAR) rmin = fmin3(rmin, r2.x, r2.y);
                 const float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
                 float2 s = __fmul2_rn(__fmul2_rn(mm, ri), __fmul2_rn(ri, ri));
                 if (MASK) {
@@ -129,7 +137,7 @@ __device__ __forceinline__ unsigned chunk_pass(const float4 (*cb)[4], int j0, in
                 ip.az[p] = __ffma2_rn(dz, s, ip.az[p]);
             }
         }
-        if (MODE == PM_DS_NEAR && near) gmask |= 1u << g;
+        if (MODE == PM_DS_NEAR && rmin < th2) gmask |= 1u << g;
     }
     return gmask;
 }
