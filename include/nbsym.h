@@ -202,6 +202,31 @@ int nb_prof_read(nb_ctx *ctx, nb_prof_t *out);
  * call.  Errors: NB_EINVAL (NULL out, bad device), NB_ECUDA. */
 int nb_measure_peaks(int device, nb_peaks_t *out);
 
+/* One force evaluation that allocates nothing.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- hosts
+ * that give all device memory to their own pool allocator, loops that must
+ * never pay the implicit device synchronisation of cudaMalloc/cudaFree, and
+ * plug-in environments that forbid device allocation after start-up.
+ *
+ * Computes the same accelerations as nb_accel (internal sum of eq. 5 in the
+ * arithmetic p->precision selects, plus the external field when p->ext_on)
+ * for n bodies given as device pointers: d_pos (n rows of x, y, z), d_mass
+ * (n), result to d_acc_out (n rows), all caller-owned memory on p->device.
+ * Work is enqueued on p->stream (NULL = the legacy default stream); the call
+ * returns without synchronising, so the caller synchronises that stream
+ * before reading d_acc_out.  No non-finite check is made.
+ *
+ * Limit: 1 <= n <= 16384.  All working memory sits in one static device
+ * array of about 5.2 MB that every GPU loading the library keeps until the
+ * process exits.  The first call on a device looks up that array's address
+ * (cudaGetSymbolAddress) and must come before any stream capture.  Calls
+ * share the array: calls whose work overlaps on the GPU race, so serialise
+ * them.  Calls no cudaMalloc, cudaFree or allocating library routine.
+ * Errors: NB_EINVAL (NULL pointer, n out of range, bad parameters or
+ * device), NB_ECUDA. */
+int nb_accel_static(const nb_params *p, int64_t n, const double *d_pos,
+                    const double *d_mass, double *d_acc_out);
+
 /* Release the context and all its device memory.  NULL-safe. */
 void nb_destroy(nb_ctx *ctx);
 

@@ -81,6 +81,7 @@ nb_prof_enable = _sig("nb_prof_enable", C.c_int, _ctxp, C.c_int)
 nb_prof_read = _sig("nb_prof_read", C.c_int, _ctxp, C.POINTER(ProfT))
 nb_destroy = _sig("nb_destroy", None, _ctxp)
 nb_measure_peaks = _sig("nb_measure_peaks", C.c_int, C.c_int, C.POINTER(PeaksT))
+nb_accel_static = _sig("nb_accel_static", C.c_int, C.POINTER(Params), C.c_int64, _vp, _vp, _vp)
 
 
 def measure_peaks(device: int = 0) -> dict:
