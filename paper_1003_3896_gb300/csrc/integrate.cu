@@ -140,7 +140,7 @@ __global__ void frame_final_kernel(DevState s, double near_frac, double eps)
         // the expected number of near neighbours per body is independent of N
         const double spacing2 = f.r2rms / cbrt((double)s.n * (double)s.n);
         f.th2 = (float)(near_frac * near_frac * spacing2 + eps * eps);
-        f.pad = 0.f;
+        f.dth = (float)(near_frac * sqrt(spacing2));
         *s.frame = f;
     }
 }
@@ -204,6 +204,11 @@ __device__ __forceinline__ void sum_slots(const DevState &s, const Decomp &d, in
         ax += p[0];
         ay += p[s.cap];
         az += p[2 * s.cap];
+    }
+    if (s.corr) {
+        ax += s.corr[i];
+        ay += s.corr[s.cap + i];
+        az += s.corr[2 * s.cap + i];
     }
 }
 

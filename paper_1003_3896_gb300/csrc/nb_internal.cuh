@@ -25,7 +25,7 @@ struct Frame {
     double cx, cy, cz;   // reference point (mass-weighted centre)
     double r2rms;        // mass-weighted mean |x - c|^2
     float th2;           // near-pair threshold on r^2 + eps^2
-    float pad;
+    float dth;           // near-pair radius d_th (th2 = d_th^2 + eps^2)
 };
 
 // Device state of one particle system.  FP64 structure-of-arrays planes are
@@ -42,6 +42,13 @@ struct DevState {
     float4 *jd = nullptr, *jl = nullptr;
     double *part = nullptr;     // partial sums [slot][3][cap]
     int64_t part_slots = 0;
+    // near-pair correction of the mixed mode (nullptr corr: not applied)
+    double *corr = nullptr;     // [3][cap]
+    uint64_t *ng_key = nullptr; // cell key per body
+    int *ng_bucket = nullptr, *ng_entry = nullptr;   // per body
+    int *ng_count = nullptr, *ng_start = nullptr;    // per bucket (start: H + 1)
+    int *ng_bsum = nullptr;                          // scan block totals
+    int64_t ng_hcap = 0;                             // buckets allocated
     double *red = nullptr;      // block partials of reductions
     int64_t red_len = 0;
     double *aos = nullptr;      // (cap, 3) staging for interleaved I/O
@@ -104,6 +111,13 @@ cudaError_t launch_pair(const DevState &s, const PairLaunch &pl, double G, doubl
 // Potential sum phi_i = sum_{j != i} m_j / sqrt(r^2 + eps^2) (FP64) into
 // slot planes of s.part (component 0).
 cudaError_t launch_potential(const DevState &s, const Decomp &d, double eps, cudaStream_t st);
+
+// ---- near-pair correction (near.cu) ----------------------------------------
+// Hash-table buckets used for n bodies (power of two >= 2n).
+int64_t near_table_size(int64_t n);
+// corr_i = G sum over pairs closer than the frame's near radius of the
+// double-single minus the float contribution (written to s.corr).
+cudaError_t launch_near_correct(const DevState &s, double eps, double G, cudaStream_t st);
 
 // ---- launchers (integrate.cu) ----------------------------------------------
 cudaError_t launch_unpack(const DevState &s, const double *pos, const double *vel,

@@ -181,6 +181,11 @@ void free_state(nb_ctx *c)
         if (q) cudaFree(q);
     if (s.jd) cudaFree(s.jd);
     if (s.jl) cudaFree(s.jl);
+    if (s.corr) cudaFree(s.corr);
+    if (s.ng_key) cudaFree(s.ng_key);
+    int *di[] = {s.ng_bucket, s.ng_entry, s.ng_count, s.ng_start, s.ng_bsum};
+    for (int *q : di)
+        if (q) cudaFree(q);
     if (s.frame) cudaFree(s.frame);
     if (s.flag) cudaFree(s.flag);
     s = DevState();
@@ -210,6 +215,25 @@ int refresh_split(nb_ctx *c)
     NB_CUDA(launch_frame(c->s, near_frac_of(c->p), c->p.eps, c->stream));
     NB_CUDA(launch_split(c->s, c->stream));
     c->split_stale = false;
+    return NB_OK;
+}
+
+// The state as the consumers of the pair partial sums see it: the near-pair
+// correction plane is added only in the mixed (NB_DS) mode.
+DevState view(const nb_ctx *c)
+{
+    DevState s = c->s;
+    if (c->p.precision != NB_DS) s.corr = nullptr;
+    return s;
+}
+
+// Kernels enqueued by launch_near_correct (two memsets are not counted).
+constexpr int64_t NEAR_KERNELS = 7;
+
+int near_correct(nb_ctx *c)
+{
+    if (c->p.precision != NB_DS) return NB_OK;
+    NB_CUDA(launch_near_correct(c->s, c->p.eps, c->p.G, c->stream));
     return NB_OK;
 }
 
@@ -251,8 +275,9 @@ int enqueue_step(nb_ctx *c, int order, double h, StepGraph *g)
         NB_CUDA(launch_frame(c->s, near_frac_of(c->p), c->p.eps, c->stream));
         kernels += 2;
     }
+    const DevState sv = view(c);
     // drift of the first leapfrog's half step (and the split it feeds)
-    NB_CUDA(launch_kick_drift(c->s, c->pl.d, 0.0, 0.5 * wk[0] * h, 0, sp ? 1 : 0, ext, c->p.G,
+    NB_CUDA(launch_kick_drift(sv, c->pl.d, 0.0, 0.5 * wk[0] * h, 0, sp ? 1 : 0, ext, c->p.G,
                               c->stream));
     kernels += 1;
     for (int k = 0; k < K; ++k) {
@@ -265,7 +290,10 @@ int enqueue_step(nb_ctx *c, int order, double h, StepGraph *g)
         if (g && g->prof)
             NB_CUDA(cudaEventRecordWithFlags(g->ev[2 * k + 1], c->stream,
                                              cudaEventRecordExternal));
-        NB_CUDA(launch_kick_drift(c->s, c->pl.d, wk[k] * h, hd, 1, (sp && !last) ? 1 : 0, ext,
+        int rc = near_correct(c);
+        if (rc) return rc;
+        if (c->p.precision == NB_DS) kernels += NEAR_KERNELS;
+        NB_CUDA(launch_kick_drift(sv, c->pl.d, wk[k] * h, hd, 1, (sp && !last) ? 1 : 0, ext,
                                   c->p.G, c->stream));
         kernels += 2;
     }
@@ -424,6 +452,18 @@ int nb_create(const nb_params *p, int64_t n_capacity, nb_ctx **out)
     A64(&c->stage, 7 * s.cap);
     if (ok && cudaMalloc(&s.jd, (size_t)(2 * s.cap) * sizeof(float4)) != cudaSuccess) ok = false;
     if (ok && cudaMalloc(&s.jl, (size_t)(2 * s.cap) * sizeof(float4)) != cudaSuccess) ok = false;
+    // near-pair correction: correction planes and the hash grid
+    s.ng_hcap = near_table_size(s.cap);
+    A64(&s.corr, 3 * s.cap);
+    auto AI = [&](int **q, int64_t cnt) {
+        if (ok && cudaMalloc(q, (size_t)cnt * sizeof(int)) != cudaSuccess) ok = false;
+    };
+    AI(&s.ng_bucket, s.cap);
+    AI(&s.ng_entry, s.cap);
+    AI(&s.ng_count, s.ng_hcap);
+    AI(&s.ng_start, s.ng_hcap + 1);
+    AI(&s.ng_bsum, s.ng_hcap / 1024 + 1);
+    if (ok && cudaMalloc(&s.ng_key, (size_t)s.cap * sizeof(uint64_t)) != cudaSuccess) ok = false;
     if (ok && cudaMalloc(&s.frame, sizeof(Frame)) != cudaSuccess) ok = false;
     if (ok && cudaMalloc(&s.flag, sizeof(int)) != cudaSuccess) ok = false;
     if (ok && cudaEventCreate(&c->pe0) != cudaSuccess) ok = false;
@@ -500,9 +540,12 @@ static int accel_common(nb_ctx *c, double *out, bool host)
     if (rc) return rc;
     rc = launch_pair_timed(c);
     if (rc) return rc;
+    rc = near_correct(c);
+    if (rc) return rc;
+    if (c->prof_on && c->p.precision == NB_DS) c->prof.kernel_launches += NEAR_KERNELS + 1;
     NB_CUDA(cudaMemsetAsync(c->s.flag, 0, sizeof(int), c->stream));
     double *dst = host ? c->stage : out;
-    NB_CUDA(launch_accel_out(c->s, c->pl.d, ext_of(c->p), c->p.G, dst, c->stream));
+    NB_CUDA(launch_accel_out(view(c), c->pl.d, ext_of(c->p), c->p.G, dst, c->stream));
     if (host)
         NB_CUDA(cudaMemcpyAsync(out, dst, (size_t)(3 * c->s.n) * sizeof(double),
                                 cudaMemcpyDeviceToHost, c->stream));

@@ -40,7 +40,12 @@ constexpr int64_t OFF_J = OFF_F + align256(7 * NA_MAX_N * 4);               // j
 constexpr int64_t OFF_P = OFF_J + align256(4 * NA_MAX_N * 16);              // partial slots
 constexpr int64_t OFF_R = OFF_P + align256(NA_SLOTS * 3 * NA_MAX_N * 8);    // reductions
 constexpr int64_t OFF_G = OFF_R + align256(NA_RED * 8);                     // diag, frame, flag
-constexpr int64_t NA_BYTES = OFF_G + align256(16 * 8 + sizeof(Frame) + 16);
+constexpr int64_t NA_H = 32768;                                             // near_table_size(NA_MAX_N)
+constexpr int64_t OFF_C = OFF_G + align256(16 * 8 + sizeof(Frame) + 16);    // near-pair correction
+constexpr int64_t OFF_K = OFF_C + align256(3 * NA_MAX_N * 8);               // cell keys
+constexpr int64_t OFF_I = OFF_K + align256(NA_MAX_N * 8);                   // bucket, entry
+constexpr int64_t OFF_H = OFF_I + align256(2 * NA_MAX_N * 4);               // count, start, bsum
+constexpr int64_t NA_BYTES = OFF_H + align256((2 * NA_H + 1 + NA_H / 1024 + 1) * 4);
 
 static __device__ __align__(256) unsigned char na_scratch[NA_BYTES];
 
@@ -121,6 +126,18 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
         s.diag = reinterpret_cast<double *>(b + OFF_G);
         s.frame = reinterpret_cast<Frame *>(b + OFF_G + 16 * 8);
         s.flag = reinterpret_cast<int *>(b + OFF_G + 16 * 8 + sizeof(Frame));
+        s.corr = reinterpret_cast<double *>(b + OFF_C);
+        s.ng_key = reinterpret_cast<uint64_t *>(b + OFF_K);
+        s.ng_bucket = reinterpret_cast<int *>(b + OFF_I);
+        s.ng_entry = s.ng_bucket + NA_MAX_N;
+        s.ng_count = reinterpret_cast<int *>(b + OFF_H);
+        s.ng_start = s.ng_count + NA_H;
+        s.ng_bsum = s.ng_start + NA_H + 1;
+        s.ng_hcap = NA_H;
+        if (near_table_size(NA_MAX_N) != NA_H) {
+            rc = NB_ECUDA;
+            break;
+        }
 
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) !=
@@ -161,8 +178,20 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
             }
         }
         if (cudaMemsetAsync(s.flag, 0, sizeof(int), st) != cudaSuccess ||
-            launch_pair(s, pl, p->G, p->eps, st) != cudaSuccess ||
-            launch_accel_out(s, pl.d, ext, p->G, d_acc_out, st) != cudaSuccess)
+            launch_pair(s, pl, p->G, p->eps, st) != cudaSuccess) {
+            rc = NB_ECUDA;
+            break;
+        }
+        // the mixed mode re-forms near pairs from the double-single difference
+        if (pl.mode == PM_DS_NEAR) {
+            if (launch_near_correct(s, p->eps, p->G, st) != cudaSuccess) {
+                rc = NB_ECUDA;
+                break;
+            }
+        } else {
+            s.corr = nullptr;
+        }
+        if (launch_accel_out(s, pl.d, ext, p->G, d_acc_out, st) != cudaSuccess)
             rc = NB_ECUDA;
     } while (0);
     if (prev != p->device) cudaSetDevice(prev);

@@ -8,11 +8,11 @@
 //
 // Single-precision family (one template, three modes):
 //   PM_DS_NEAR  float pair arithmetic on coordinates relative to the frame
-//               origin; pairs whose float r^2 + eps^2 falls below frame->th2
-//               are recomputed with the double-single coordinate difference
-//               (hi_j - hi_i) + (lo_j - lo_i) and their float contribution
-//               replaced; per-tile float sums are folded into double-single
-//               accumulators (Sect. 4.2's software double precision).
+//               origin, per-tile float sums folded into double-single
+//               accumulators (Sect. 4.2's software double precision); pairs
+//               closer than the near radius are re-formed from the
+//               double-single coordinate difference (hi_j - hi_i) +
+//               (lo_j - lo_i) by the separate correction pass of near.cu.
 //   PM_DS_FULL  the double-single coordinate difference on every pair.
 //   PM_FP32     float coordinates and float accumulation throughout (per-tile
 //               float sums added in float).
@@ -24,7 +24,7 @@
 // stored pre-duplicated, (x, x, y, y) (z, z, m, m), so one packed f32x2
 // instruction serves two i bodies of the same thread with no register moves.
 // rsqrt runs on the MUFU pipe (rsqrt.approx).  Arithmetic uses explicit
-// round-to-nearest intrinsics so the near-pair fix-up reproduces the main
+// round-to-nearest intrinsics so the near-pair correction reproduces this
 // loop's float contribution bit for bit.
 #include "nb_internal.cuh"
 
@@ -49,14 +49,6 @@ __device__ __forceinline__ float rsqrt_mufu(float x)
     float y;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
-}
-
-// Minimum of three floats in one instruction (three-input min, sm_100+).
-__device__ __forceinline__ float fmin3(float a, float b, float c)
-{
-    float r;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
 }
 
 // Add float t to the double-single number (hi, lo): Knuth's two-sum of hi and
@@ -84,18 +76,15 @@ struct IPairs {
     float2 ax[P], ay[P], az[P];     // float sums of the current 128-j tile
 };
 
-// One chunk of CH j bodies against the thread's 2P i bodies.  Returns a
-// bitmask with bit g set when group g (8 j bodies) held a pair closer than the
-// near-pair threshold.  MASK zeroes the j == i term (eps = 0, diagonal chunks).
+// One chunk of CH j bodies against the thread's 2P i bodies.  MASK zeroes the
+// j == i term (eps = 0, diagonal chunks).
 template <int P, int MODE, bool MASK>
-__device__ __forceinline__ unsigned chunk_pass(const float4 (*cb)[4], int j0, int ibase,
-                                               IPairs<P> &ip, float eps2, float th2)
+__device__ __forceinline__ void chunk_pass(const float4 (*cb)[4], int j0, int ibase,
+                                           IPairs<P> &ip, float eps2)
 {
     const float2 e2 = make_float2(eps2, eps2);
-    unsigned gmask = 0;
 #pragma unroll
     for (int g = 0; g < CH / 8; ++g) {
-        float rmin = 3.0e38f;   // smallest float r^2 + eps^2 of the group
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int jj = g * 8 + q;
@@ -124,7 +113,6 @@ __device__ __forceinline__ unsigned chunk_pass(const float4 (*cb)[4], int j0, in
                 float2 r2 = __ffma2_rn(dx, dx, e2);
                 r2 = __ffma2_rn(dy, dy, r2);
                 r2 = __ffma2_rn(dz, dz, r2);
-                if (MODE == PM_DS_NEAR) rmin = fmin3(rmin, r2.x, r2.y);
                 const float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
                 float2 s = __fmul2_rn(__fmul2_rn(mm, ri), __fmul2_rn(ri, ri));
                 if (MASK) {
@@ -135,70 +123,6 @@ __device__ __forceinline__ unsigned chunk_pass(const float4 (*cb)[4], int j0, in
                 ip.ax[p] = __ffma2_rn(dx, s, ip.ax[p]);
                 ip.ay[p] = __ffma2_rn(dy, s, ip.ay[p]);
                 ip.az[p] = __ffma2_rn(dz, s, ip.az[p]);
-            }
-        }
-        if (MODE == PM_DS_NEAR && rmin < th2) gmask |= 1u << g;
-    }
-    return gmask;
-}
-
-// Near-pair fix-up for the flagged 8-body groups of a chunk: for each pair
-// whose float r^2 + eps^2 is below th2, subtract the float contribution the
-// main loop added (recomputed identically, element by element) and add the
-// one formed from the double-single coordinate difference.
-template <int P>
-__device__ __forceinline__ void near_fixup(const float4 (*cb)[4], unsigned gmask, int j0,
-                                        int ibase, int n, IPairs<P> &ip,
-                                        const float *__restrict__ xl,
-                                        const float *__restrict__ yl,
-                                        const float *__restrict__ zl, float eps2, float th2)
-{
-    while (gmask) {
-        const int g = __ffs(gmask) - 1;
-        gmask &= gmask - 1;
-        for (int q = 0; q < 8; ++q) {
-            const int jj = g * 8 + q;
-            const int j = j0 + jj;
-            const float4 A = cb[jj][0];
-            const float4 B = cb[jj][1];
-            const float xj = A.x, yj = A.z, zj = B.x, mj = B.z;
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int i = ibase + (2 * p + h) * TILE;
-                    const float dx = __fadd_rn(xj, h ? ip.nx[p].y : ip.nx[p].x);
-                    const float dy = __fadd_rn(yj, h ? ip.ny[p].y : ip.ny[p].x);
-                    const float dz = __fadd_rn(zj, h ? ip.nz[p].y : ip.nz[p].x);
-                    float r2 = __fmaf_rn(dx, dx, eps2);
-                    r2 = __fmaf_rn(dy, dy, r2);
-                    r2 = __fmaf_rn(dz, dz, r2);
-                    if (!(r2 < th2) || j == i || j >= n) continue;
-                    const float ri = rsqrt_mufu(r2);
-                    const float s = __fmul_rn(__fmul_rn(mj, ri), __fmul_rn(ri, ri));
-                    // i past the end mirrors body n-1 (result discarded)
-                    const int ic = i < n ? i : n - 1;
-                    const float ex = __fadd_rn(dx, __fsub_rn(xl[j], xl[ic]));
-                    const float ey = __fadd_rn(dy, __fsub_rn(yl[j], yl[ic]));
-                    const float ez = __fadd_rn(dz, __fsub_rn(zl[j], zl[ic]));
-                    float e2 = __fmaf_rn(ex, ex, eps2);
-                    e2 = __fmaf_rn(ey, ey, e2);
-                    e2 = __fmaf_rn(ez, ez, e2);
-                    const float re = rsqrt_mufu(e2);
-                    const float se = __fmul_rn(__fmul_rn(mj, re), __fmul_rn(re, re));
-                    const float cx = __fsub_rn(__fmul_rn(ex, se), __fmul_rn(dx, s));
-                    const float cy = __fsub_rn(__fmul_rn(ey, se), __fmul_rn(dy, s));
-                    const float cz = __fsub_rn(__fmul_rn(ez, se), __fmul_rn(dz, s));
-                    if (h) {
-                        ip.ax[p].y = __fadd_rn(ip.ax[p].y, cx);
-                        ip.ay[p].y = __fadd_rn(ip.ay[p].y, cy);
-                        ip.az[p].y = __fadd_rn(ip.az[p].y, cz);
-                    } else {
-                        ip.ax[p].x = __fadd_rn(ip.ax[p].x, cx);
-                        ip.ay[p].x = __fadd_rn(ip.ay[p].x, cy);
-                        ip.az[p].x = __fadd_rn(ip.az[p].x, cz);
-                    }
-                }
             }
         }
     }
@@ -231,7 +155,7 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
     const int64_t g = blockIdx.x;
     int64_t u = d.U(g);
     const int64_t uend = d.U(g + 1);
-    const float th2 = (MODE == PM_DS_NEAR) ? frame->th2 : 0.f;
+    (void)frame;
     const float4 far4 = make_float4(FAR_F, FAR_F, FAR_F, FAR_F);
     const float4 farm = make_float4(FAR_F, FAR_F, 0.f, 0.f);
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -287,15 +211,10 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
                 }
             }
             const bool diag = mask_self && jc < ib0 + d.ipb && jc + CH > ib0;
-            unsigned gm;
             if (diag)
-                gm = chunk_pass<P, MODE, true>(cb, jc, ibase, ip, eps2, th2);
+                chunk_pass<P, MODE, true>(cb, jc, ibase, ip, eps2);
             else
-                gm = chunk_pass<P, MODE, false>(cb, jc, ibase, ip, eps2, th2);
-            if (MODE == PM_DS_NEAR) {
-                if (__any_sync(0xffffffffu, gm != 0))
-                    near_fixup<P>(cb, gm, jc, ibase, n, ip, xl, yl, zl, eps2, th2);
-            }
+                chunk_pass<P, MODE, false>(cb, jc, ibase, ip, eps2);
             __syncwarp();
             if (((jc + CH - J0) & (TILE - 1)) == 0) {
                 // end of a 128-j tile: fold the tile sums into the running sums

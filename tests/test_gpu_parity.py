@@ -326,6 +326,24 @@ def test_c3_full_size_sampled(nbs, orc):
             assert rel_rms(a, ref) <= TOL[prec], (prec, rel_rms(a, ref))
 
 
+def test_near_pair_correction_is_what_makes_mixed_accurate(nbs, orc):
+    """Orbit geometry at N = 4099: with the near radius shrunk to nothing the
+    mixed result is the centred-float one (error set by the closest pairs);
+    the default radius brings it under 1e-6; a radius covering every pair
+    re-forms all of them from the double-single difference."""
+    n = 4099
+    pos, vel, m = system(n, seed=29, offset=True)
+    eps = ics.paper_softening(n)
+    ref = orc.accel(pos, m, ext_params(orc, eps, True))
+    err = {}
+    for nf in (1e-9, 0.0, 1e4):
+        with nbs.Context(n, eps=eps, precision="ds", ext_on=True, near_frac=nf) as c:
+            c.load(pos, vel, m)
+            err[nf] = rel_rms(c.accel(), ref)
+    assert err[0.0] <= TOL["ds"] and err[1e4] <= TOL["ds"], err
+    assert err[1e-9] > 2 * err[0.0], err
+
+
 def test_measured_peaks_are_plausible(nbs):
     """The peak micro-kernels run and report rates within physical bounds of a
     GPU with this SM count (<= 128 FP32 lanes x 2 flops x 2.2 GHz per SM)."""
