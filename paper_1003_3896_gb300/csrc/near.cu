@@ -159,10 +159,13 @@ __global__ void near_sort_kernel(DevState s, int64_t H)
     }
 }
 
+// One warp per body i; lane l < 27 visits neighbour cell (l % 3 - 1,
+// l / 3 % 3 - 1, l / 9 - 1); the lane sums are combined by a fixed shuffle tree.
 __global__ void near_correct_kernel(DevState s, float eps2, uint32_t mask, double G)
 {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= s.n) return;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= s.n) return;   // whole warps exit together
     const Frame f = *s.frame;
     const float th2 = f.th2;
     const float ih = inv_cell(f, eps2);
@@ -170,9 +173,10 @@ __global__ void near_correct_kernel(DevState s, float eps2, uint32_t mask, doubl
     const float lxi = s.xl[i], lyi = s.yl[i], lzi = s.zl[i];
     const int cx = cell_coord(xi, ih), cy = cell_coord(yi, ih), cz = cell_coord(zi, ih);
     double ax = 0.0, ay = 0.0, az = 0.0;
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
+    if (lane < 27) {
+        const int dx = lane % 3 - 1, dy = lane / 3 % 3 - 1, dz = lane / 9 - 1;
+        {
+            {
                 const uint64_t key = cell_key(cx + dx, cy + dy, cz + dz);
                 const uint32_t b = cell_bucket(cx + dx, cy + dy, cz + dz, mask);
                 const int lo = s.ng_start[b], hi = s.ng_start[b + 1];
@@ -204,9 +208,18 @@ __global__ void near_correct_kernel(DevState s, float eps2, uint32_t mask, doubl
                     az += (double)__fmul_rn(ez, se) - (double)__fmul_rn(ddz, sf);
                 }
             }
-    s.corr[i] = G * ax;
-    s.corr[s.cap + i] = G * ay;
-    s.corr[2 * s.cap + i] = G * az;
+        }
+    }
+    for (int w = 16; w > 0; w >>= 1) {
+        ax += __shfl_down_sync(0xffffffffu, ax, w);
+        ay += __shfl_down_sync(0xffffffffu, ay, w);
+        az += __shfl_down_sync(0xffffffffu, az, w);
+    }
+    if (lane == 0) {
+        s.corr[i] = G * ax;
+        s.corr[s.cap + i] = G * ay;
+        s.corr[2 * s.cap + i] = G * az;
+    }
 }
 
 int64_t near_table_size(int64_t cap)
@@ -235,7 +248,7 @@ cudaError_t launch_near_correct(const DevState &s, double eps, double G, cudaStr
     if (e != cudaSuccess) return e;
     near_scatter_kernel<<<nbn, 256, 0, st>>>(s);
     near_sort_kernel<<<nbh, 256, 0, st>>>(s, H);
-    near_correct_kernel<<<nbn, 256, 0, st>>>(s, eps2, mask, G);
+    near_correct_kernel<<<(unsigned)((s.n * 32 + 255) / 256), 256, 0, st>>>(s, eps2, mask, G);
     return cudaGetLastError();
 }
 
