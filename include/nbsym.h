@@ -136,6 +136,29 @@ void nb_params_default(nb_params *p);
  * NB_ENOMEM, NB_ECUDA. */
 int nb_create(const nb_params *p, int64_t n_capacity, nb_ctx **out);
 
+/* Create a context holding an ensemble of n_clusters independent systems of
+ * fixed sizes sizes[0..n_clusters-1] (each >= 1; 1 <= n_clusters <= 2^19,
+ * sum <= 2^26).  Each cluster obeys eq. 3 on its own: bodies of different
+ * clusters never interact.  Every force evaluation of the whole ensemble is
+ * one persistent kernel launch whose blocks share the pair work of all
+ * clusters evenly, and a step of every cluster is one CUDA graph.  nb_load
+ * then takes the clusters' bodies concatenated in cluster order (n = sum of
+ * sizes); nb_accel / nb_get_state return them in that order; every cluster
+ * starts with softening p->eps and step scale 1 (nb_set_cluster_params).
+ * The paper integrates one cluster at a time; this batches many.  Errors:
+ * NB_EINVAL, NB_ENOMEM, NB_ECUDA. */
+int nb_create_batch(const nb_params *p, int64_t n_clusters, const int64_t *sizes,
+                    nb_ctx **out);
+
+/* Per-cluster softening eps[k] >= 0 (eq. 4-5) and step scale dt_scale[k] > 0
+ * (cluster k advances by dt * dt_scale[k] per nb_step); either array may be
+ * NULL to keep the current values.  Arrays have nb_clusters() entries.
+ * Errors: NB_EINVAL, NB_ECUDA. */
+int nb_set_cluster_params(nb_ctx *ctx, const double *eps, const double *dt_scale);
+
+/* Number of clusters (1 for nb_create), or NB_EINVAL for NULL. */
+int64_t nb_clusters(const nb_ctx *ctx);
+
 /* Load a particle system (initial conditions of eq. 3): n rows of positions
  * and velocities, n masses (>= 0, finite).  1 <= n <= capacity.  Host
  * pointers.  Errors: NB_EINVAL, NB_ECUDA. */
@@ -164,12 +187,17 @@ int nb_accel_device(nb_ctx *ctx, double *d_acc_out);
  * NB_ECUDA. */
 int nb_step(nb_ctx *ctx, int order, double dt, int64_t nsteps);
 
-/* Energy, momentum and angular momentum of the current state (Sect. 4.1).
- * Errors: NB_ESTATE, NB_EINVAL, NB_ENONFINITE, NB_ECUDA. */
+/* Energy, momentum and angular momentum of the current state (Sect. 4.1),
+ * summed over the clusters of a batch.  Errors: NB_ESTATE, NB_EINVAL,
+ * NB_ENONFINITE, NB_ECUDA. */
 int nb_energy(nb_ctx *ctx, nb_energy_t *out);
 
-/* External torque M_ext = sum m_i r_i x a_ext(r_i) (eq. 8); zero when the
- * field is off.  out has 3 doubles.  Errors: NB_ESTATE, NB_EINVAL, NB_ECUDA. */
+/* The same per cluster: out has nb_clusters() entries. */
+int nb_energy_clusters(nb_ctx *ctx, nb_energy_t *out);
+
+/* External torque M_ext = sum m_i r_i x a_ext(r_i) (eq. 8), summed over the
+ * clusters; zero when the field is off.  out has 3 doubles.  Errors:
+ * NB_ESTATE, NB_EINVAL, NB_ECUDA. */
 int nb_torque(nb_ctx *ctx, double *out);
 
 /* Copy the current positions and velocities (n rows each) to host buffers;

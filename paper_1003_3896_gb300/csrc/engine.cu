@@ -1,0 +1,424 @@
+// engine.cu -- state pool, cluster-set tables, launch plans and the enqueue
+// functions shared by the context API and the serving loop.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "engine.h"
+
+namespace nb {
+
+namespace {
+thread_local std::string g_err;
+}
+
+int set_error(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+const char *last_error() { return g_err.c_str(); }
+
+// ---- pool --------------------------------------------------------------------
+
+int pool_create(Pool &P, int device, int64_t cap)
+{
+    P.device = device;
+    P.cap = cap;
+    if (cudaDeviceGetAttribute(&P.num_sms, cudaDevAttrMultiProcessorCount, device) !=
+        cudaSuccess)
+        return set_error(NB_ECUDA, "cudaDeviceGetAttribute failed");
+    DevState &s = P.s;
+    s.cap = cap;
+    // partial-sum slots: an i-block needs about G_max * ipb / n + 2 of them;
+    // memory stays near 24 * (G_max * 512 + 2 cap) bytes whatever cap is
+    const int64_t gmax = (int64_t)P.num_sms * 8;
+    int64_t slots = 2 + (gmax * 512 + cap - 1) / cap;
+    if (slots > 24) slots = 24;
+    s.part_slots = slots;
+    s.ng_hcap = near_table_size(cap);
+    s.red_len = 0;
+    bool ok = true;
+    auto A = [&](void **q, size_t bytes) {
+        if (ok && cudaMalloc(q, bytes) != cudaSuccess) {
+            *q = nullptr;
+            ok = false;
+        }
+    };
+    const size_t c8 = (size_t)cap * 8, c4 = (size_t)cap * 4;
+    A((void **)&s.x, c8); A((void **)&s.y, c8); A((void **)&s.z, c8);
+    A((void **)&s.vx, c8); A((void **)&s.vy, c8); A((void **)&s.vz, c8); A((void **)&s.m, c8);
+    A((void **)&s.xh, c4); A((void **)&s.yh, c4); A((void **)&s.zh, c4); A((void **)&s.mf, c4);
+    A((void **)&s.xl, c4); A((void **)&s.yl, c4); A((void **)&s.zl, c4);
+    A((void **)&s.jd, 2 * (size_t)cap * sizeof(float4));
+    A((void **)&s.jl, 2 * (size_t)cap * sizeof(float4));
+    A((void **)&s.part, (size_t)s.part_slots * 3 * c8);
+    A((void **)&s.corr, 3 * c8);
+    A((void **)&s.ng_key, c8);
+    A((void **)&s.ng_bucket, c4);
+    A((void **)&s.ng_entry, c4);
+    A((void **)&s.ng_count, (size_t)s.ng_hcap * 4);
+    A((void **)&s.ng_start, (size_t)(s.ng_hcap + 1) * 4);
+    A((void **)&s.ng_bsum, (size_t)(s.ng_hcap / 1024 + 1) * 4);
+    A((void **)&s.flag, sizeof(int));
+    A((void **)&P.stage, 7 * c8);
+    if (!ok) {
+        cudaGetLastError();
+        pool_destroy(P);
+        return set_error(NB_ENOMEM, "device allocation failed for %lld bodies",
+                         (long long)cap);
+    }
+    return NB_OK;
+}
+
+void pool_destroy(Pool &P)
+{
+    DevState &s = P.s;
+    void *ptrs[] = {s.x, s.y, s.z, s.vx, s.vy, s.vz, s.m, s.xh, s.yh, s.zh, s.mf, s.xl,
+                    s.yl, s.zl, s.jd, s.jl, s.part, s.corr, s.ng_key, s.ng_bucket,
+                    s.ng_entry, s.ng_count, s.ng_start, s.ng_bsum, s.flag, P.stage};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    s = DevState();
+    P.stage = nullptr;
+    P.cap = 0;
+}
+
+// ---- cluster sets ------------------------------------------------------------
+
+namespace {
+inline size_t al(size_t b) { return (b + 255) / 256 * 256; }
+}
+
+int set_create(ClusterSet &C, int32_t kcap, int64_t body_cap)
+{
+    C.kcap = kcap;
+    C.scap = (body_cap + SEG_BODIES - 1) / SEG_BODIES + kcap;
+    const size_t k8 = (size_t)kcap * 8, k81 = (size_t)(kcap + 1) * 8;
+    const size_t bytes = al(k8) * 2 + al(k81) * 3 + al((size_t)kcap * 4) * 2 + al(k8) * 2 +
+                         al((size_t)C.scap * 4) + al((size_t)C.scap * 8) * 2 +
+                         al((size_t)(kcap + 1) * 4) + al((size_t)kcap * sizeof(Frame)) +
+                         al((size_t)kcap * DIAG_STRIDE * 8);
+    if (cudaMalloc(&C.dmem, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        C.dmem = nullptr;
+        return set_error(NB_ENOMEM, "cluster tables: device allocation failed");
+    }
+    // reduction partials: one row of 16 doubles per segment
+    if (cudaMalloc(&C.red, (size_t)C.scap * 16 * 8) != cudaSuccess) {
+        cudaGetLastError();
+        C.red = nullptr;
+        set_destroy(C);
+        return set_error(NB_ENOMEM, "cluster tables: device allocation failed");
+    }
+    cudaMemset(C.dmem, 0, bytes);
+    return NB_OK;
+}
+
+void set_destroy(ClusterSet &C)
+{
+    if (C.dmem) cudaFree(C.dmem);
+    if (C.red) cudaFree(C.red);
+    C = ClusterSet();
+}
+
+int set_define(ClusterSet &C, int32_t K, const int64_t *boff, const int64_t *nk,
+               const double *eps, const double *dts)
+{
+    if (K < 1 || K > C.kcap) return set_error(NB_EINVAL, "cluster count %d outside [1, %d]", K, C.kcap);
+    C.K = K;
+    C.boff.assign(boff, boff + K);
+    C.nk.assign(nk, nk + K);
+    C.eps.assign(K, 0.0);
+    C.dts.assign(K, 1.0);
+    C.noff.assign(K + 1, 0);
+    for (int32_t k = 0; k < K; ++k) {
+        if (nk[k] < 1) return set_error(NB_EINVAL, "cluster %d has no bodies", k);
+        C.eps[k] = eps ? eps[k] : 0.0;
+        if (dts) C.dts[k] = dts[k];
+        C.noff[k + 1] = C.noff[k] + nk[k];
+    }
+    C.n = C.noff[K];
+    C.eps2d.resize(K);
+    C.eps2f.resize(K);
+    for (int32_t k = 0; k < K; ++k) {
+        C.eps2d[k] = C.eps[k] * C.eps[k];
+        C.eps2f[k] = (float)C.eps2d[k];
+    }
+    C.ipb = 0;   // layout pending
+    return NB_OK;
+}
+
+int set_layout(ClusterSet &C, int ipb, cudaStream_t st)
+{
+    const int32_t K = C.K;
+    C.ipb = ipb;
+    C.ntiles.resize(K);
+    C.uoff.assign(K + 1, 0);
+    C.uoff_pot.assign(K + 1, 0);
+    C.max_ntiles = 0;
+    C.seg_off.assign(K + 1, 0);
+    C.seg_k.clear();
+    C.seg_lo.clear();
+    C.seg_hi.clear();
+    for (int32_t k = 0; k < K; ++k) {
+        const int64_t nt = (C.nk[k] + TILE - 1) / TILE;
+        C.ntiles[k] = (int32_t)nt;
+        if (nt > C.max_ntiles) C.max_ntiles = nt;
+        C.uoff[k + 1] = C.uoff[k] + ((C.nk[k] + ipb - 1) / ipb) * nt;
+        C.uoff_pot[k + 1] = C.uoff_pot[k] + nt * nt;
+        for (int64_t lo = C.noff[k]; lo < C.noff[k + 1]; lo += SEG_BODIES) {
+            C.seg_k.push_back(k);
+            C.seg_lo.push_back(lo);
+            C.seg_hi.push_back(lo + SEG_BODIES < C.noff[k + 1] ? lo + SEG_BODIES : C.noff[k + 1]);
+        }
+        C.seg_off[k + 1] = (int32_t)C.seg_k.size();
+    }
+    const int64_t S = (int64_t)C.seg_k.size();
+    if (S > C.scap) return set_error(NB_EINVAL, "too many reduction segments");
+    // device layout (must match set_create's size computation)
+    const size_t k8 = (size_t)C.kcap * 8, k81 = (size_t)(C.kcap + 1) * 8;
+    char *p = C.dmem;
+    auto take = [&](size_t bytes) {
+        char *q = p;
+        p += al(bytes);
+        return q;
+    };
+    int64_t *d_boff = (int64_t *)take(k8);
+    int64_t *d_nk = (int64_t *)take(k8);
+    int64_t *d_noff = (int64_t *)take(k81);
+    int64_t *d_uoff = (int64_t *)take(k81);
+    int64_t *d_uoffp = (int64_t *)take(k81);
+    int32_t *d_ntiles = (int32_t *)take((size_t)C.kcap * 4);
+    float *d_eps2f = (float *)take((size_t)C.kcap * 4);
+    double *d_eps2d = (double *)take(k8);
+    double *d_dts = (double *)take(k8);
+    int32_t *d_segk = (int32_t *)take((size_t)C.scap * 4);
+    int64_t *d_seglo = (int64_t *)take((size_t)C.scap * 8);
+    int64_t *d_seghi = (int64_t *)take((size_t)C.scap * 8);
+    int32_t *d_segoff = (int32_t *)take((size_t)(C.kcap + 1) * 4);
+    C.frame = (Frame *)take((size_t)C.kcap * sizeof(Frame));
+    C.diag = (double *)take((size_t)C.kcap * DIAG_STRIDE * 8);
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st)
+                     : cudaSuccess;
+    };
+    NB_TRY(up(d_boff, C.boff.data(), K * 8));
+    NB_TRY(up(d_nk, C.nk.data(), K * 8));
+    NB_TRY(up(d_noff, C.noff.data(), (K + 1) * 8));
+    NB_TRY(up(d_uoff, C.uoff.data(), (K + 1) * 8));
+    NB_TRY(up(d_uoffp, C.uoff_pot.data(), (K + 1) * 8));
+    NB_TRY(up(d_ntiles, C.ntiles.data(), K * 4));
+    NB_TRY(up(d_eps2f, C.eps2f.data(), K * 4));
+    NB_TRY(up(d_eps2d, C.eps2d.data(), K * 8));
+    NB_TRY(up(d_dts, C.dts.data(), K * 8));
+    NB_TRY(up(d_segk, C.seg_k.data(), S * 4));
+    NB_TRY(up(d_seglo, C.seg_lo.data(), S * 8));
+    NB_TRY(up(d_seghi, C.seg_hi.data(), S * 8));
+    NB_TRY(up(d_segoff, C.seg_off.data(), (K + 1) * 4));
+    // pageable copies are staged before returning; make the tables visible
+    // to kernels launched on other streams too
+    NB_TRY(cudaStreamSynchronize(st));
+    Clusters &c = C.cl;
+    c.K = K;
+    c.boff = d_boff;
+    c.nk = d_nk;
+    c.noff = d_noff;
+    c.uoff = d_uoff;
+    c.ntiles = d_ntiles;
+    c.eps2f = d_eps2f;
+    c.eps2d = d_eps2d;
+    c.dts = d_dts;
+    c.frame = C.frame;
+    c.S = (int32_t)S;
+    c.seg_k = d_segk;
+    c.seg_lo = d_seglo;
+    c.seg_hi = d_seghi;
+    c.seg_off = d_segoff;
+    C.cl_pot = c;
+    C.cl_pot.uoff = d_uoffp;
+    return NB_OK;
+}
+
+// ---- plans -------------------------------------------------------------------
+
+int mode_of(int precision)
+{
+    switch (precision) {
+    case NB_FP64: return PM_FP64;
+    case NB_FP32: return PM_FP32;
+    case NB_DS_FULL: return PM_DS_FULL;
+    default: return PM_DS_NEAR;
+    }
+}
+
+bool float_planes(int precision) { return precision != NB_FP64; }
+
+int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan &out)
+{
+    Plan pl;
+    pl.precision = precision;
+    pl.pl.mode = mode_of(precision);
+    const int64_t mean = C.n / (C.K > 0 ? C.K : 1);
+    int I;
+    if (pl.pl.mode == PM_FP64)
+        I = 1;
+    else if (mean < 16384)
+        I = 2;
+    else
+        // measured at N = 65536: mixed is fastest at 4 bodies per thread,
+        // pure float (fewer live registers) at 8
+        I = pl.pl.mode == PM_FP32 ? 8 : 4;
+    if (const char *env = getenv("NBSYM_PAIR_I")) {
+        // tuning override: bodies per thread of the pair kernel
+        const int v = atoi(env);
+        if (pair_variant_exists(pl.pl.mode, v)) I = v;
+    }
+    pl.pl.I = I;
+    int rc = set_layout(C, TILE * I, st);
+    if (rc) return rc;
+    pl.pl.blocks_per_sm = pair_occupancy(pl.pl.mode, I);
+    if (pl.pl.blocks_per_sm < 1) pl.pl.blocks_per_sm = 1;
+    const int64_t W = C.uoff[C.K];
+    int64_t G = (int64_t)P.num_sms * pl.pl.blocks_per_sm;
+    if (W / 2 < G) G = W / 2 > 0 ? W / 2 : 1;   // at least two units per block
+    pl.pl.d = make_decomp(W, C.max_ntiles, TILE * I, G, P.s.part_slots);
+    int occ = pair_occupancy(PM_FP64, 1);
+    if (occ < 1) occ = 1;
+    const int64_t Wp = C.uoff_pot[C.K];
+    int64_t Gp = (int64_t)P.num_sms * occ;
+    if (Wp / 2 < Gp) Gp = Wp / 2 > 0 ? Wp / 2 : 1;
+    pl.pot = make_decomp(Wp, C.max_ntiles, TILE, Gp, P.s.part_slots);
+    out = pl;
+    return NB_OK;
+}
+
+DevState view(const Pool &P, const ClusterSet &C, int precision)
+{
+    DevState s = P.s;
+    s.cl = C.cl;
+    s.n = C.n;
+    s.diag = C.diag;
+    s.red = C.red;
+    s.red_len = C.scap * 16;
+    if (precision != NB_DS) s.corr = nullptr;
+    return s;
+}
+
+// ---- enqueue -----------------------------------------------------------------
+
+namespace {
+void count(int64_t *k, int64_t v)
+{
+    if (k) *k += v;
+}
+constexpr int64_t NEAR_KERNELS = 7;   // launch_near_correct (memsets not counted)
+}  // namespace
+
+int enq_split(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph,
+              cudaStream_t st, int64_t *kernels)
+{
+    if (!float_planes(pl.precision)) return NB_OK;
+    const DevState s = view(P, C, pl.precision);
+    NB_TRY(launch_frame(s, ph.near_frac, st));
+    NB_TRY(launch_split(s, st));
+    count(kernels, 3);
+    return NB_OK;
+}
+
+int enq_force(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph,
+              cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1, int64_t *kernels)
+{
+    const DevState s = view(P, C, pl.precision);
+    // inside a stream capture an event record must be an external node to
+    // time anything; outside it is a plain record
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    NB_TRY(cudaStreamIsCapturing(st, &cs));
+    const unsigned evf =
+        cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (ev0) NB_TRY(cudaEventRecordWithFlags(ev0, st, evf));
+    NB_TRY(launch_pair(s, pl.pl, ph.G, st));
+    if (ev1) NB_TRY(cudaEventRecordWithFlags(ev1, st, evf));
+    count(kernels, 1);
+    if (pl.precision == NB_DS) {
+        NB_TRY(launch_near_correct(s, ph.G, st));
+        count(kernels, NEAR_KERNELS);
+    }
+    return NB_OK;
+}
+
+int enq_step(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph, int order,
+             double h, cudaStream_t st, const std::vector<cudaEvent_t> *evs, int64_t *kernels)
+{
+    const bool sp = float_planes(pl.precision);
+    const DevState s = view(P, C, pl.precision);
+    double wk[7];
+    int K;
+    if (order == 2) {
+        K = 1;
+        wk[0] = 1.0;
+    } else {
+        K = 7;
+        const double w0 = 1.0 - 2.0 * (SI6_W1 + SI6_W2 + SI6_W3);
+        const double seq[7] = {SI6_W3, SI6_W2, SI6_W1, w0, SI6_W1, SI6_W2, SI6_W3};
+        for (int k = 0; k < 7; ++k) wk[k] = seq[k];
+    }
+    if (sp) {
+        NB_TRY(launch_frame(s, ph.near_frac, st));
+        count(kernels, 2);
+    }
+    // drift of the first leapfrog's half step (and the split it feeds)
+    NB_TRY(launch_kick_drift(s, pl.pl.d, 0.0, 0.5 * wk[0] * h, 0, sp ? 1 : 0, ph.ext, st));
+    count(kernels, 1);
+    for (int k = 0; k < K; ++k) {
+        // adjacent half drifts of consecutive leapfrogs merge
+        const double hd = 0.5 * (wk[k] + (k + 1 < K ? wk[k + 1] : 0.0)) * h;
+        const bool last = (k + 1 == K);
+        cudaEvent_t e0 = evs ? (*evs)[2 * k] : nullptr, e1 = evs ? (*evs)[2 * k + 1] : nullptr;
+        int rc = enq_force(P, C, pl, ph, st, e0, e1, kernels);
+        if (rc) return rc;
+        NB_TRY(launch_kick_drift(s, pl.pl.d, wk[k] * h, hd, 1, (sp && !last) ? 1 : 0, ph.ext,
+                                 st));
+        count(kernels, 1);
+    }
+    return NB_OK;
+}
+
+int enq_accel_out(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph,
+                  double *out, cudaStream_t st, int64_t *kernels)
+{
+    const DevState s = view(P, C, pl.precision);
+    NB_TRY(launch_accel_out(s, pl.pl.d, ph.ext, out, st));
+    count(kernels, 1);
+    return NB_OK;
+}
+
+int enq_energy(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph,
+               cudaStream_t st, int64_t *kernels)
+{
+    DevState s = view(P, C, pl.precision);
+    s.cl = C.cl_pot;
+    NB_TRY(launch_potential(s, pl.pot, st));
+    NB_TRY(launch_energy_reduce(s, pl.pot, ph.ext, ph.G, st));
+    count(kernels, 3);
+    return NB_OK;
+}
+
+int enq_torque(const Pool &P, const ClusterSet &C, const Phys &ph, cudaStream_t st,
+               int64_t *kernels)
+{
+    const DevState s = view(P, C, NB_FP64);
+    NB_TRY(launch_torque(s, ph.ext, st));
+    count(kernels, 2);
+    return NB_OK;
+}
+
+}  // namespace nb

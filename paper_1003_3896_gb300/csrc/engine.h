@@ -1,0 +1,111 @@
+// engine.h -- host-side engine behind the C ABI: a device state pool, the
+// tables of a cluster set living in it, launch plans, and the functions that
+// enqueue force evaluations, integration steps and diagnostics.  Used by the
+// context API (nbsym.cu) and the serving loop (server.cu).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "nb_internal.cuh"
+#include "../../include/nbsym.h"
+
+namespace nb {
+
+// Thread-local error message shared by every entry point.
+int set_error(int code, const char *fmt, ...);
+const char *last_error();
+
+#define NB_TRY(call)                                                                       \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return ::nb::set_error(NB_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// Device arrays for up to cap bodies (pool slots); DevState::cl and n are
+// filled per cluster set by view().
+struct Pool {
+    int device = 0;
+    int num_sms = 0;
+    int64_t cap = 0;
+    DevState s;
+    double *stage = nullptr;   // (7 cap) staging for interleaved host transfers
+};
+int pool_create(Pool &P, int device, int64_t cap);
+void pool_destroy(Pool &P);
+
+// Tables of one cluster set in a pool (host copy + device copy).
+struct ClusterSet {
+    int32_t K = 0, kcap = 0;
+    int64_t scap = 0;
+    int64_t n = 0;             // bodies, noff[K]
+    int64_t max_ntiles = 0;
+    int ipb = 0;               // i-block width the pair units are counted with
+    std::vector<int64_t> boff, nk, noff, uoff, uoff_pot, seg_lo, seg_hi;
+    std::vector<int32_t> ntiles, seg_k, seg_off;
+    std::vector<float> eps2f;
+    std::vector<double> eps, eps2d, dts;
+    char *dmem = nullptr;      // device copy of the tables
+    double *red = nullptr;     // reduction partials [scap][16]
+    Frame *frame = nullptr;    // [kcap]
+    double *diag = nullptr;    // [kcap][DIAG_STRIDE]
+    Clusters cl, cl_pot;       // device views (pair units / potential units)
+};
+int set_create(ClusterSet &C, int32_t kcap, int64_t body_cap);
+void set_destroy(ClusterSet &C);
+// Clusters k = 0..K-1 at pool slots [boff[k], boff[k] + nk[k]), softening
+// eps[k] and step scale dts[k] (NULL: 1).  Host only; set_layout uploads.
+int set_define(ClusterSet &C, int32_t K, const int64_t *boff, const int64_t *nk,
+               const double *eps, const double *dts);
+// Count pair units for i-blocks of ipb bodies, build reduction segments and
+// upload every table (stream-ordered).
+int set_layout(ClusterSet &C, int ipb, cudaStream_t st);
+
+struct Plan {
+    int precision = -1;
+    PairLaunch pl{};
+    Decomp pot{};
+};
+// Choose the pair kernel variant and decompositions for a cluster set and
+// lay the set out for it.
+int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan &out);
+
+struct Phys {
+    double G = 1.0;
+    double near_frac = 0.4;
+    ExtField ext{};
+};
+
+// Kernel-facing state of a cluster set: the pool arrays with the set's tables.
+DevState view(const Pool &P, const ClusterSet &C, int precision);
+int mode_of(int precision);
+bool float_planes(int precision);
+
+// Enqueue-only operations (no synchronisation).  *kernels, when given, is
+// increased by the number of kernels enqueued.
+int enq_split(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph,
+              cudaStream_t st, int64_t *kernels);
+// Pair forces (+ near-pair correction in the mixed mode) into partial slots;
+// ev0/ev1 (optional) bracket the pair kernel with external event records.
+int enq_force(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph,
+              cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1, int64_t *kernels);
+// One step of length dt (times each cluster's scale) of order 2 or 6.
+// evs (optional) has 2 events per force evaluation for the pair kernels.
+int enq_step(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph, int order,
+             double dt, cudaStream_t st, const std::vector<cudaEvent_t> *evs, int64_t *kernels);
+int enq_accel_out(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph,
+                  double *out, cudaStream_t st, int64_t *kernels);
+// Energy / momentum per cluster into C.diag.
+int enq_energy(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph,
+               cudaStream_t st, int64_t *kernels);
+int enq_torque(const Pool &P, const ClusterSet &C, const Phys &ph, cudaStream_t st,
+               int64_t *kernels);
+
+// SI6A weights (Kinoshita, Yoshida & Nakai 1991, Table 1 first column =
+// Yoshida's 1990 solution A); w0 = 1 - 2 (w1 + w2 + w3).
+constexpr double SI6_W1 = -1.17767998417887;
+constexpr double SI6_W2 = 0.235573213359357;
+constexpr double SI6_W3 = 0.784513610477560;
+
+}  // namespace nb

@@ -1,19 +1,37 @@
-// integrate.cu -- O(N) kernels: state layout conversion, the float frame and
-// split, the fused kick(+external field)/drift substep of the symplectic
-// schemes (Sect. 3.1), and deterministic reductions for the diagnostics of
-// Sect. 4.1.  All state arithmetic is double precision (Sect. 3.2: the time
-// advance is the round-off sensitive part).
+// integrate.cu -- O(N) kernels over a set of clusters: state layout
+// conversion, the per-cluster float frame and split, the fused kick(+external
+// field)/drift substep of the symplectic schemes (Sect. 3.1), and
+// deterministic per-cluster reductions for the diagnostics of Sect. 4.1.
+// All state arithmetic is double precision (Sect. 3.2: the time advance is
+// the round-off sensitive part).
+//
+// Per-body kernels run over linear body indices t (cluster after cluster);
+// find_cluster maps t to its cluster k and pool slot boff[k] + t - noff[k].
+// Reductions run per segment (a run of one cluster's bodies), then one block
+// per cluster adds its segments in a fixed tree order.
 #include "nb_internal.cuh"
 
 namespace nb {
 
-constexpr int RB = 256;        // reduction blocks (fixed: results independent of timing)
-constexpr int RT = 256;        // threads per reduction block
-constexpr int OT = 256;        // threads per block of the per-particle kernels
-
-int reduce_blocks() { return RB; }
+constexpr int RT = 256;   // threads per reduction block
+constexpr int OT = 256;   // threads per block of the per-body kernels
 
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+struct BodyRef {
+    int32_t k;     // cluster
+    int64_t li;    // index inside the cluster
+    int64_t gi;    // pool slot
+};
+
+__device__ __forceinline__ BodyRef body_at(const Clusters &c, int64_t t)
+{
+    BodyRef r;
+    r.k = find_cluster(c.noff, c.K, t);
+    r.li = t - c.noff[r.k];
+    r.gi = c.boff[r.k] + r.li;
+    return r;
+}
 
 // Acceleration of the smooth field of eq. 3, a = -grad Phi, for the
 // Miyamoto-Nagai disk plus Plummer bulge potential
@@ -49,6 +67,7 @@ template <int NV>
 __device__ void block_sum(double (&v)[NV], double *sh)
 {
     const int t = threadIdx.x;
+    __syncthreads();
     for (int k = 0; k < NV; ++k) sh[k * RT + t] = v[k];
     __syncthreads();
     for (int w = RT / 2; w > 0; w >>= 1) {
@@ -59,36 +78,49 @@ __device__ void block_sum(double (&v)[NV], double *sh)
     for (int k = 0; k < NV; ++k) v[k] = sh[k * RT];
 }
 
+// Sum of the NV segment partials of cluster blockIdx.x (fixed order).
+template <int NV>
+__device__ void cluster_sum(const DevState &s, double (&v)[NV], double *sh)
+{
+    const int k = blockIdx.x;
+    for (int q = 0; q < NV; ++q) v[q] = 0.0;
+    for (int sg = s.cl.seg_off[k] + threadIdx.x; sg < s.cl.seg_off[k + 1]; sg += RT)
+        for (int q = 0; q < NV; ++q) v[q] += s.red[(int64_t)sg * 16 + q];
+    block_sum<NV>(v, sh);
+}
+
 // ---- layout ------------------------------------------------------------------
 
 __global__ void unpack_kernel(DevState s, const double *__restrict__ pos,
                               const double *__restrict__ vel, const double *__restrict__ mass)
 {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= s.n) return;
-    s.x[i] = pos[3 * i];
-    s.y[i] = pos[3 * i + 1];
-    s.z[i] = pos[3 * i + 2];
-    s.vx[i] = vel[3 * i];
-    s.vy[i] = vel[3 * i + 1];
-    s.vz[i] = vel[3 * i + 2];
-    s.m[i] = mass[i];
-    s.mf[i] = __double2float_rn(mass[i]);   // masses never change after load
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= s.n) return;
+    const int64_t i = body_at(s.cl, t).gi;
+    s.x[i] = pos[3 * t];
+    s.y[i] = pos[3 * t + 1];
+    s.z[i] = pos[3 * t + 2];
+    s.vx[i] = vel[3 * t];
+    s.vy[i] = vel[3 * t + 1];
+    s.vz[i] = vel[3 * t + 2];
+    s.m[i] = mass[t];
+    s.mf[i] = __double2float_rn(mass[t]);   // masses never change after load
 }
 
 __global__ void pack_kernel(DevState s, double *__restrict__ pos, double *__restrict__ vel)
 {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= s.n) return;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= s.n) return;
+    const int64_t i = body_at(s.cl, t).gi;
     if (pos) {
-        pos[3 * i] = s.x[i];
-        pos[3 * i + 1] = s.y[i];
-        pos[3 * i + 2] = s.z[i];
+        pos[3 * t] = s.x[i];
+        pos[3 * t + 1] = s.y[i];
+        pos[3 * t + 2] = s.z[i];
     }
     if (vel) {
-        vel[3 * i] = s.vx[i];
-        vel[3 * i + 1] = s.vy[i];
-        vel[3 * i + 2] = s.vz[i];
+        vel[3 * t] = s.vx[i];
+        vel[3 * t + 1] = s.vy[i];
+        vel[3 * t + 2] = s.vz[i];
     }
 }
 
@@ -110,8 +142,12 @@ cudaError_t launch_pack(const DevState &s, double *pos, double *vel, cudaStream_
 __global__ void frame_partial_kernel(DevState s)
 {
     __shared__ double sh[5 * RT];
+    const int sg = blockIdx.x;
+    const int32_t k = s.cl.seg_k[sg];
+    const int64_t base = s.cl.boff[k] - s.cl.noff[k];
     double v[5] = {0, 0, 0, 0, 0};
-    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < s.n; i += (int64_t)RB * RT) {
+    for (int64_t t = s.cl.seg_lo[sg] + threadIdx.x; t < s.cl.seg_hi[sg]; t += RT) {
+        const int64_t i = base + t;
         const double m = s.m[i], x = s.x[i], y = s.y[i], z = s.z[i];
         v[0] += m;
         v[1] += m * x;
@@ -121,43 +157,43 @@ __global__ void frame_partial_kernel(DevState s)
     }
     block_sum<5>(v, sh);
     if (threadIdx.x == 0)
-        for (int k = 0; k < 5; ++k) s.red[blockIdx.x * 5 + k] = v[k];
+        for (int q = 0; q < 5; ++q) s.red[(int64_t)sg * 16 + q] = v[q];
 }
 
-__global__ void frame_final_kernel(DevState s, double near_frac, double eps)
+__global__ void frame_final_kernel(DevState s, double near_frac)
 {
     __shared__ double sh[5 * RT];
-    double v[5] = {0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < RB; b += RT)
-        for (int k = 0; k < 5; ++k) v[k] += s.red[b * 5 + k];
-    block_sum<5>(v, sh);
+    double v[5];
+    cluster_sum<5>(s, v, sh);
     if (threadIdx.x == 0) {
+        const int k = blockIdx.x;
         Frame f;
         const double M = v[0];
         f.cx = M > 0 ? v[1] / M : 0.0;
         f.cy = M > 0 ? v[2] / M : 0.0;
         f.cz = M > 0 ? v[3] / M : 0.0;
-        double r2 = M > 0 ? v[4] / M - (f.cx * f.cx + f.cy * f.cy + f.cz * f.cz) : 0.0;
+        const double r2 = M > 0 ? v[4] / M - (f.cx * f.cx + f.cy * f.cy + f.cz * f.cz) : 0.0;
         f.r2rms = r2 > 0 ? r2 : 0.0;
         // near-pair radius: near_frac times the rms radius over N^{1/3}, a
         // mean-spacing scale like the paper's softening rule (Sect. 2), so
         // the expected number of near neighbours per body is independent of N
-        const double spacing2 = f.r2rms / cbrt((double)s.n * (double)s.n);
-        f.th2 = (float)(near_frac * near_frac * spacing2 + eps * eps);
+        const double nk = (double)s.cl.nk[k];
+        const double spacing2 = f.r2rms / cbrt(nk * nk);
+        f.th2 = (float)(near_frac * near_frac * spacing2 + s.cl.eps2d[k]);
         f.dth = (float)(near_frac * sqrt(spacing2));
-        *s.frame = f;
+        s.cl.frame[k] = f;
     }
 }
 
-cudaError_t launch_frame(const DevState &s, double near_frac, double eps, cudaStream_t st)
+cudaError_t launch_frame(const DevState &s, double near_frac, cudaStream_t st)
 {
-    frame_partial_kernel<<<RB, RT, 0, st>>>(s);
-    frame_final_kernel<<<1, RT, 0, st>>>(s, near_frac, eps);
+    frame_partial_kernel<<<s.cl.S, RT, 0, st>>>(s);
+    frame_final_kernel<<<s.cl.K, RT, 0, st>>>(s, near_frac);
     return cudaGetLastError();
 }
 
 // hi = fl32(x - c), lo = fl32((x - c) - hi): the double-single representation
-// of Sect. 4.2, taken relative to the frame origin.
+// of Sect. 4.2, taken relative to the cluster's frame origin.
 __device__ __forceinline__ void split_one(const DevState &s, const Frame &f, int64_t i,
                                           double x, double y, double z)
 {
@@ -182,11 +218,12 @@ __device__ __forceinline__ void split_one(const DevState &s, const Frame &f, int
 
 __global__ void split_kernel(DevState s)
 {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= s.n) return;
-    const Frame f = *s.frame;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= s.n) return;
+    const BodyRef r = body_at(s.cl, t);
+    const int64_t i = r.gi;
     s.mf[i] = __double2float_rn(s.m[i]);
-    split_one(s, f, i, s.x[i], s.y[i], s.z[i]);
+    split_one(s, s.cl.frame[r.k], i, s.x[i], s.y[i], s.z[i]);
 }
 
 cudaError_t launch_split(const DevState &s, cudaStream_t st)
@@ -197,35 +234,39 @@ cudaError_t launch_split(const DevState &s, cudaStream_t st)
 
 // ---- substep -----------------------------------------------------------------
 
-__device__ __forceinline__ void sum_slots(const DevState &s, const Decomp &d, int64_t i,
+__device__ __forceinline__ void sum_slots(const DevState &s, const Decomp &d, const BodyRef &r,
                                           double &ax, double &ay, double &az)
 {
-    const int64_t b = i / d.ipb;
-    const int64_t ns = d.nslots(b);
+    int64_t first, count;
+    iblock_slots(d, s.cl, r.k, r.li, first, count);
+    (void)first;
     ax = ay = az = 0.0;
-    for (int64_t k = 0; k < ns; ++k) {
-        const double *p = s.part + (k * 3) * s.cap + i;
+    for (int64_t k = 0; k < count; ++k) {
+        const double *p = s.part + (k * 3) * s.cap + r.gi;
         ax += p[0];
         ay += p[s.cap];
         az += p[2 * s.cap];
     }
     if (s.corr) {
-        ax += s.corr[i];
-        ay += s.corr[s.cap + i];
-        az += s.corr[2 * s.cap + i];
+        ax += s.corr[r.gi];
+        ay += s.corr[s.cap + r.gi];
+        az += s.corr[2 * s.cap + r.gi];
     }
 }
 
-__global__ void kick_drift_kernel(DevState s, Decomp d, double hk, double hd, int do_kick,
+__global__ void kick_drift_kernel(DevState s, Decomp d, double wk, double wd, int do_kick,
                                   int do_split, ExtField ext)
 {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= s.n) return;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= s.n) return;
+    const BodyRef r = body_at(s.cl, t);
+    const int64_t i = r.gi;
+    const double dt = s.cl.dts[r.k];
     double x = s.x[i], y = s.y[i], z = s.z[i];
     double vx = s.vx[i], vy = s.vy[i], vz = s.vz[i];
     if (do_kick) {
         double ax, ay, az;
-        sum_slots(s, d, i, ax, ay, az);
+        sum_slots(s, d, r, ax, ay, az);
         if (ext.on) {
             double ex, ey, ez;
             field_accel(ext, x, y, z, ex, ey, ez);
@@ -233,6 +274,7 @@ __global__ void kick_drift_kernel(DevState s, Decomp d, double hk, double hd, in
             ay += ey;
             az += ez;
         }
+        const double hk = wk * dt;
         vx += hk * ax;
         vy += hk * ay;
         vz += hk * az;
@@ -240,64 +282,72 @@ __global__ void kick_drift_kernel(DevState s, Decomp d, double hk, double hd, in
         s.vy[i] = vy;
         s.vz[i] = vz;
     }
+    const double hd = wd * dt;
     x += hd * vx;
     y += hd * vy;
     z += hd * vz;
     s.x[i] = x;
     s.y[i] = y;
     s.z[i] = z;
-    if (do_split) split_one(s, *s.frame, i, x, y, z);
+    if (do_split) split_one(s, s.cl.frame[r.k], i, x, y, z);
 }
 
-cudaError_t launch_kick_drift(const DevState &s, const Decomp &d, double hk, double hd,
-                              int do_kick, int do_split, const ExtField &ext, double G,
-                              cudaStream_t st)
+cudaError_t launch_kick_drift(const DevState &s, const Decomp &d, double wk, double wd,
+                              int do_kick, int do_split, const ExtField &ext, cudaStream_t st)
 {
-    (void)G;
-    kick_drift_kernel<<<blocks_for(s.n, OT), OT, 0, st>>>(s, d, hk, hd, do_kick, do_split, ext);
+    kick_drift_kernel<<<blocks_for(s.n, OT), OT, 0, st>>>(s, d, wk, wd, do_kick, do_split, ext);
     return cudaGetLastError();
 }
 
 __global__ void accel_out_kernel(DevState s, Decomp d, ExtField ext, double *__restrict__ out)
 {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= s.n) return;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= s.n) return;
+    const BodyRef r = body_at(s.cl, t);
     double ax, ay, az;
-    sum_slots(s, d, i, ax, ay, az);
+    sum_slots(s, d, r, ax, ay, az);
     if (ext.on) {
         double ex, ey, ez;
-        field_accel(ext, s.x[i], s.y[i], s.z[i], ex, ey, ez);
+        field_accel(ext, s.x[r.gi], s.y[r.gi], s.z[r.gi], ex, ey, ez);
         ax += ex;
         ay += ey;
         az += ez;
     }
-    out[3 * i] = ax;
-    out[3 * i + 1] = ay;
-    out[3 * i + 2] = az;
+    out[3 * t] = ax;
+    out[3 * t + 1] = ay;
+    out[3 * t + 2] = az;
     if (!isfinite(ax) || !isfinite(ay) || !isfinite(az)) atomicOr(s.flag, 1);
 }
 
 cudaError_t launch_accel_out(const DevState &s, const Decomp &d, const ExtField &ext,
-                             double G, double *out_aos, cudaStream_t st)
+                             double *out_aos, cudaStream_t st)
 {
-    (void)G;
     accel_out_kernel<<<blocks_for(s.n, OT), OT, 0, st>>>(s, d, ext, out_aos);
     return cudaGetLastError();
 }
 
 // ---- diagnostics -------------------------------------------------------------
 
-// Per block: K, sum m_i phi_i, W_ext, P, L (10 values).
+// Per segment: K, sum m_i phi_i, W_ext, P, L, non-finite count (10 values).
+// d is the potential kernel's decomposition (s.cl.uoff must be its units).
 __global__ void energy_partial_kernel(DevState s, Decomp d, ExtField ext)
 {
     __shared__ double sh[10 * RT];
+    const int sg = blockIdx.x;
+    const int32_t k = s.cl.seg_k[sg];
     double v[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < s.n; i += (int64_t)RB * RT) {
+    for (int64_t t = s.cl.seg_lo[sg] + threadIdx.x; t < s.cl.seg_hi[sg]; t += RT) {
+        BodyRef r;
+        r.k = k;
+        r.li = t - s.cl.noff[k];
+        r.gi = s.cl.boff[k] + r.li;
+        const int64_t i = r.gi;
         const double m = s.m[i], x = s.x[i], y = s.y[i], z = s.z[i];
         const double vx = s.vx[i], vy = s.vy[i], vz = s.vz[i];
-        const int64_t ns = d.nslots(i / d.ipb);
+        int64_t first, count;
+        iblock_slots(d, s.cl, k, r.li, first, count);
         double phi = 0.0;
-        for (int64_t k = 0; k < ns; ++k) phi += s.part[(k * 3) * s.cap + i];
+        for (int64_t q = 0; q < count; ++q) phi += s.part[(q * 3) * s.cap + i];
         v[0] += 0.5 * m * (vx * vx + vy * vy + vz * vz);
         v[1] += m * phi;
         if (ext.on) v[2] += m * field_phi(ext, x, y, z);
@@ -313,41 +363,44 @@ __global__ void energy_partial_kernel(DevState s, Decomp d, ExtField ext)
     }
     block_sum<10>(v, sh);
     if (threadIdx.x == 0)
-        for (int k = 0; k < 10; ++k) s.red[blockIdx.x * 10 + k] = v[k];
+        for (int q = 0; q < 10; ++q) s.red[(int64_t)sg * 16 + q] = v[q];
 }
 
 __global__ void energy_final_kernel(DevState s, double G)
 {
     __shared__ double sh[10 * RT];
-    double v[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < RB; b += RT)
-        for (int k = 0; k < 10; ++k) v[k] += s.red[b * 10 + k];
-    block_sum<10>(v, sh);
+    double v[10];
+    cluster_sum<10>(s, v, sh);
     if (threadIdx.x == 0) {
+        double *o = s.diag + (int64_t)blockIdx.x * DIAG_STRIDE;
         const double W = -0.5 * G * v[1];
-        s.diag[0] = v[0];
-        s.diag[1] = W;
-        s.diag[2] = v[2];
-        s.diag[3] = v[0] + W + v[2];
-        for (int k = 0; k < 6; ++k) s.diag[4 + k] = v[3 + k];
-        if (v[9] != 0.0 || !isfinite(s.diag[3])) atomicOr(s.flag, 1);
+        o[0] = v[0];
+        o[1] = W;
+        o[2] = v[2];
+        o[3] = v[0] + W + v[2];
+        for (int q = 0; q < 6; ++q) o[4 + q] = v[3 + q];
+        if (v[9] != 0.0 || !isfinite(o[3])) atomicOr(s.flag, 1);
     }
 }
 
 cudaError_t launch_energy_reduce(const DevState &s, const Decomp &d, const ExtField &ext,
                                  double G, cudaStream_t st)
 {
-    energy_partial_kernel<<<RB, RT, 0, st>>>(s, d, ext);
-    energy_final_kernel<<<1, RT, 0, st>>>(s, G);
+    energy_partial_kernel<<<s.cl.S, RT, 0, st>>>(s, d, ext);
+    energy_final_kernel<<<s.cl.K, RT, 0, st>>>(s, G);
     return cudaGetLastError();
 }
 
-// External torque of eq. 8: sum m_i r_i x a_ext(r_i).
+// External torque of eq. 8: sum m_i r_i x a_ext(r_i), per cluster.
 __global__ void torque_partial_kernel(DevState s, ExtField ext)
 {
     __shared__ double sh[3 * RT];
+    const int sg = blockIdx.x;
+    const int32_t k = s.cl.seg_k[sg];
+    const int64_t base = s.cl.boff[k] - s.cl.noff[k];
     double v[3] = {0, 0, 0};
-    for (int64_t i = blockIdx.x * (int64_t)RT + threadIdx.x; i < s.n; i += (int64_t)RB * RT) {
+    for (int64_t t = s.cl.seg_lo[sg] + threadIdx.x; t < s.cl.seg_hi[sg]; t += RT) {
+        const int64_t i = base + t;
         const double m = s.m[i], x = s.x[i], y = s.y[i], z = s.z[i];
         double ax, ay, az;
         field_accel(ext, x, y, z, ax, ay, az);
@@ -357,24 +410,22 @@ __global__ void torque_partial_kernel(DevState s, ExtField ext)
     }
     block_sum<3>(v, sh);
     if (threadIdx.x == 0)
-        for (int k = 0; k < 3; ++k) s.red[blockIdx.x * 3 + k] = v[k];
+        for (int q = 0; q < 3; ++q) s.red[(int64_t)sg * 16 + q] = v[q];
 }
 
 __global__ void torque_final_kernel(DevState s)
 {
     __shared__ double sh[3 * RT];
-    double v[3] = {0, 0, 0};
-    for (int b = threadIdx.x; b < RB; b += RT)
-        for (int k = 0; k < 3; ++k) v[k] += s.red[b * 3 + k];
-    block_sum<3>(v, sh);
+    double v[3];
+    cluster_sum<3>(s, v, sh);
     if (threadIdx.x == 0)
-        for (int k = 0; k < 3; ++k) s.diag[10 + k] = v[k];
+        for (int q = 0; q < 3; ++q) s.diag[(int64_t)blockIdx.x * DIAG_STRIDE + 10 + q] = v[q];
 }
 
 cudaError_t launch_torque(const DevState &s, const ExtField &ext, cudaStream_t st)
 {
-    torque_partial_kernel<<<RB, RT, 0, st>>>(s, ext);
-    torque_final_kernel<<<1, RT, 0, st>>>(s);
+    torque_partial_kernel<<<s.cl.S, RT, 0, st>>>(s, ext);
+    torque_final_kernel<<<s.cl.K, RT, 0, st>>>(s);
     return cudaGetLastError();
 }
 

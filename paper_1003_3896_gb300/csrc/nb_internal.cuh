@@ -7,20 +7,18 @@
 
 namespace nb {
 
-// Tile width of the pair kernels: one j per thread per plane when a tile is
-// staged in shared memory, and the i-block is TILE * I particles wide.
+// Tile width of the pair kernels: a unit of pair work is TILE j bodies
+// against one i-block of TILE * I bodies.
 constexpr int TILE = 128;
 
 // Position of padding j slots: far enough that its mass-0 contribution is an
-// exact 0 and it never passes the near-pair test, small enough that its
-// squared distance stays finite in float.
+// exact 0, small enough that its squared distance stays finite in float.
 constexpr float FAR_F = 1.0e18f;
 constexpr double FAR_D = 1.0e150;
 
-// Reference frame of the single-precision coordinates (Sect. 4.2's
+// Reference frame of one cluster's single-precision coordinates (Sect. 4.2's
 // "delicate evaluation of coordinate difference"): positions are stored as
-// float hi = fl(x - c) and lo = fl((x - c) - hi).  th2 is the squared
-// near-pair radius plus eps^2, compared with the float r^2 + eps^2.
+// float hi = fl(x - c) and lo = fl((x - c) - hi).
 struct Frame {
     double cx, cy, cz;   // reference point (mass-weighted centre)
     double r2rms;        // mass-weighted mean |x - c|^2
@@ -28,10 +26,47 @@ struct Frame {
     float dth;           // near-pair radius d_th (th2 = d_th^2 + eps^2)
 };
 
-// Device state of one particle system.  FP64 structure-of-arrays planes are
-// the state; float planes are derived copies for the single-precision paths.
+// A set of K independent clusters living in one state pool.  Cluster k owns
+// pool slots [boff[k], boff[k] + nk[k]); bodies are also numbered linearly,
+// cluster after cluster, through the prefix sums noff.  A single system is
+// K = 1; a batched ensemble or a serving batch is K > 1.  Device pointers.
+struct Clusters {
+    int32_t K = 0;
+    const int64_t *boff = nullptr;   // [K]   first pool slot of cluster k
+    const int64_t *nk = nullptr;     // [K]   bodies of cluster k
+    const int64_t *noff = nullptr;   // [K+1] prefix sums of nk (linear body index)
+    const int64_t *uoff = nullptr;   // [K+1] prefix sums of pair units
+    const int32_t *ntiles = nullptr; // [K]   j tiles of cluster k = ceil(nk / TILE)
+    const float *eps2f = nullptr;    // [K]   eps^2 (float)
+    const double *eps2d = nullptr;   // [K]   eps^2 (double)
+    const double *dts = nullptr;     // [K]   step-length scale of cluster k
+    Frame *frame = nullptr;          // [K]
+    // reduction segments: each covers a run of one cluster's linear bodies
+    int32_t S = 0;
+    const int32_t *seg_k = nullptr;  // [S]
+    const int64_t *seg_lo = nullptr; // [S]   linear body range [lo, hi)
+    const int64_t *seg_hi = nullptr;
+    const int32_t *seg_off = nullptr;// [K+1] segments of cluster k: [seg_off[k], seg_off[k+1])
+};
+
+// largest k in [0, K) with off[k] <= t (off[0] = 0 <= t < off[K])
+__host__ __device__ __forceinline__ int32_t find_cluster(const int64_t *off, int32_t K, int64_t t)
+{
+    int32_t lo = 0, hi = K;
+    while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (off[mid] <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Device state pool.  FP64 structure-of-arrays planes are the state; float
+// planes are derived copies for the single-precision paths.  All indexed by
+// pool slot.
 struct DevState {
-    int64_t n = 0, cap = 0;
+    int64_t cap = 0;       // pool slots
+    int64_t n = 0;         // bodies in the current cluster set (noff[K])
+    Clusters cl;
     double *x = nullptr, *y = nullptr, *z = nullptr;
     double *vx = nullptr, *vy = nullptr, *vz = nullptr, *m = nullptr;
     float *xh = nullptr, *yh = nullptr, *zh = nullptr, *mf = nullptr;
@@ -44,47 +79,47 @@ struct DevState {
     int64_t part_slots = 0;
     // near-pair correction of the mixed mode (nullptr corr: not applied)
     double *corr = nullptr;     // [3][cap]
-    uint64_t *ng_key = nullptr; // cell key per body
-    int *ng_bucket = nullptr, *ng_entry = nullptr;   // per body
+    uint64_t *ng_key = nullptr; // cell key per linear body
+    int *ng_bucket = nullptr, *ng_entry = nullptr;   // per linear body
     int *ng_count = nullptr, *ng_start = nullptr;    // per bucket (start: H + 1)
     int *ng_bsum = nullptr;                          // scan block totals
     int64_t ng_hcap = 0;                             // buckets allocated
-    double *red = nullptr;      // block partials of reductions
+    double *red = nullptr;      // reduction partials [segment][16]
     int64_t red_len = 0;
-    double *aos = nullptr;      // (cap, 3) staging for interleaved I/O
-    Frame *frame = nullptr;
-    double *diag = nullptr;     // [16] reduction results (energy, torque)
+    double *diag = nullptr;     // [K][16] reduction results (energy, torque)
     int *flag = nullptr;        // non-finite flag
 };
 
-// Persistent ("stream-K") decomposition of the N x N pair work.  Unit u is
-// (i-block b, j-tile t) with u = b * ntiles + t; persistent block g owns the
-// contiguous units [U(g), U(g+1)), U(g) = floor(g W / G).  Each (b, g)
-// segment writes its own partial slot k = g - gfirst(b); consumers add the
-// slots of an i-block in slot order, so results do not depend on timing.
+// Persistent ("stream-K") decomposition of the pair work of a cluster set.
+// A unit is (cluster k, i-block b, j-tile t); units are numbered cluster by
+// cluster, u = uoff[k] + b * ntiles[k] + t, W units in all.  Persistent block
+// g owns the contiguous units [U(g), U(g+1)), U(g) = floor(g W / G); every
+// unit is TILE x TILE*I pairs, so blocks get equal work whatever the cluster
+// sizes.  Each (cluster, i-block, block g) segment writes its own partial
+// slot g - gfirst; consumers add an i-block's slots in slot order, so results
+// do not depend on timing.
 struct Decomp {
-    int64_t n;
-    int32_t ipb;      // particles per i-block = TILE * I
-    int32_t ntiles;   // ceil(n / TILE)
-    int64_t iblocks;  // ceil(n / ipb)
-    int64_t W;        // iblocks * ntiles
-    int64_t G;        // persistent blocks (grid size), 1 <= G <= W
+    int32_t ipb = TILE;   // bodies per i-block = TILE * I
+    int64_t W = 0;        // total units
+    int64_t G = 1;        // persistent blocks (grid size), 1 <= G <= W
+    int64_t slots = 1;    // max partial slots any i-block needs
 
     __host__ __device__ int64_t U(int64_t g) const { return (g * W) / G; }
     // largest g with U(g) <= u
-    __host__ __device__ int64_t owner(int64_t u) const {
-        return ((u + 1) * G + W - 1) / W - 1;
-    }
-    __host__ __device__ int64_t gfirst(int64_t b) const { return owner(b * ntiles); }
-    __host__ __device__ int64_t nslots(int64_t b) const {
-        return owner(b * ntiles + ntiles - 1) - gfirst(b) + 1;
-    }
-    __host__ __device__ int64_t max_slots() const {
-        return (G + iblocks - 1) / iblocks + 1;
-    }
+    __host__ __device__ int64_t owner(int64_t u) const { return ((u + 1) * G + W - 1) / W - 1; }
 };
 
-Decomp make_decomp(int64_t n, int ipb, int64_t G);
+// Partial slots of the i-block holding linear body t of cluster k, and the
+// first owner block (the slot of block g is g - first).
+__device__ __forceinline__ void iblock_slots(const Decomp &d, const Clusters &c, int32_t k,
+                                             int64_t li, int64_t &first, int64_t &count)
+{
+    const int64_t b = li / d.ipb;
+    const int64_t nt = c.ntiles[k];
+    const int64_t u0 = c.uoff[k] + b * nt;
+    first = d.owner(u0);
+    count = d.owner(u0 + nt - 1) - first + 1;
+}
 
 struct ExtField {
     int on;
@@ -92,13 +127,14 @@ struct ExtField {
 };
 
 // ---- launchers (pair.cu) ---------------------------------------------------
-// mode: 0 = mixed with near-pair double-single fix-up, 1 = mixed with
-// double-single difference on every pair, 2 = pure float, 3 = double.
+// mode: 0 = mixed (float pairs, double-single sums; near pairs corrected by
+// near.cu), 1 = mixed with double-single difference on every pair,
+// 2 = pure float, 3 = double.
 enum PairMode { PM_DS_NEAR = 0, PM_DS_FULL = 1, PM_FP32 = 2, PM_FP64 = 3 };
 
 struct PairLaunch {
     int mode;
-    int I;           // i-particles per thread
+    int I;           // i-bodies per thread
     int blocks_per_sm;
     Decomp d;
 };
@@ -106,37 +142,40 @@ struct PairLaunch {
 // Resident blocks per SM of a pair-kernel variant (occupancy query).
 int pair_occupancy(int mode, int I);
 bool pair_variant_exists(int mode, int I);
-cudaError_t launch_pair(const DevState &s, const PairLaunch &pl, double G, double eps,
-                        cudaStream_t st);
-// Potential sum phi_i = sum_{j != i} m_j / sqrt(r^2 + eps^2) (FP64) into
-// slot planes of s.part (component 0).
-cudaError_t launch_potential(const DevState &s, const Decomp &d, double eps, cudaStream_t st);
+// Decomposition of the pair work of clusters with host-side sizes nk and
+// tiles, given units per cluster (host arrays), i-block width, target grid.
+Decomp make_decomp(int64_t W, int64_t max_ntiles, int ipb, int64_t G, int64_t slot_cap);
+cudaError_t launch_pair(const DevState &s, const PairLaunch &pl, double G, cudaStream_t st);
+// Potential sums phi_i = sum_{j != i} m_j / sqrt(r^2 + eps^2) (FP64) into
+// slot planes of s.part (component 0); decomposition with ipb = TILE.
+cudaError_t launch_potential(const DevState &s, const Decomp &d, cudaStream_t st);
 
 // ---- near-pair correction (near.cu) ----------------------------------------
 // Hash-table buckets used for n bodies (power of two >= 2n).
 int64_t near_table_size(int64_t n);
-// corr_i = G sum over pairs closer than the frame's near radius of the
+// corr_i = G sum over pairs closer than the cluster's near radius of the
 // double-single minus the float contribution (written to s.corr).
-cudaError_t launch_near_correct(const DevState &s, double eps, double G, cudaStream_t st);
+cudaError_t launch_near_correct(const DevState &s, double G, cudaStream_t st);
 
 // ---- launchers (integrate.cu) ----------------------------------------------
+// Interleaved (linear body, 3) arrays <-> pool planes.
 cudaError_t launch_unpack(const DevState &s, const double *pos, const double *vel,
                           const double *mass, cudaStream_t st);
 cudaError_t launch_pack(const DevState &s, double *pos, double *vel, cudaStream_t st);
-cudaError_t launch_frame(const DevState &s, double near_frac, double eps, cudaStream_t st);
+cudaError_t launch_frame(const DevState &s, double near_frac, cudaStream_t st);
 cudaError_t launch_split(const DevState &s, cudaStream_t st);
-// One fused substep: optional kick v += hk (a_int + a_ext) from the partial
-// slots of decomposition d, then drift x += hd v, then (optionally) refresh
-// the float planes.
-cudaError_t launch_kick_drift(const DevState &s, const Decomp &d, double hk, double hd,
-                              int do_kick, int do_split, const ExtField &ext, double G,
-                              cudaStream_t st);
+// One fused substep: optional kick v += wk dt_k (a_int + a_ext) from the
+// partial slots of decomposition d, then drift x += wd dt_k v, then
+// (optionally) refresh the float planes.
+cudaError_t launch_kick_drift(const DevState &s, const Decomp &d, double wk, double wd,
+                              int do_kick, int do_split, const ExtField &ext, cudaStream_t st);
 cudaError_t launch_accel_out(const DevState &s, const Decomp &d, const ExtField &ext,
-                             double G, double *out_aos, cudaStream_t st);
+                             double *out_aos, cudaStream_t st);
 cudaError_t launch_energy_reduce(const DevState &s, const Decomp &d, const ExtField &ext,
                                  double G, cudaStream_t st);
 cudaError_t launch_torque(const DevState &s, const ExtField &ext, cudaStream_t st);
 
-int reduce_blocks();   // number of block partials the reductions use
+constexpr int SEG_BODIES = 2048;   // bodies per reduction segment
+constexpr int DIAG_STRIDE = 16;    // doubles per cluster in diag
 
 }  // namespace nb

@@ -5,11 +5,11 @@
 // loops that must never pay the implicit device synchronisation of
 // cudaMalloc/cudaFree, and plug-in environments whose policy forbids device
 // allocation after start-up.  Every piece of working memory the evaluation
-// needs (double and float planes, the packed j-stream, the reference frame,
-// reduction partials and the pair kernels' partial-sum slots) lives in one
-// file-scope __device__ array of fixed size, NA_BYTES below, sized for at most
-// NA_MAX_N bodies.  Every GPU that loads this library holds that array until
-// the process exits.
+// needs (double and float planes, the packed j-stream, the cluster tables and
+// reference frame, reduction partials, the pair kernels' partial-sum slots
+// and the near-pair grid) lives in one file-scope __device__ array of fixed
+// size, NA_BYTES below, sized for at most NA_MAX_N bodies.  Every GPU that
+// loads this library holds that array until the process exits.
 //
 // Host code cannot use the array's name as a device address (on the host it
 // names a stand-in object), so the first call on each device, with that
@@ -17,10 +17,10 @@
 // it.  That first call should therefore come before any stream capture.
 //
 // Every call shares the one array and leaves its contents behind; each call
-// writes every scratch element it later reads (and clears the non-finite
-// flag it uses), so nothing leaks from one call into the next.  Calls whose
-// work overlaps on the GPU (different streams, or several host threads) race
-// on the array: serialise them.
+// writes every scratch element it later reads (its tables are rebuilt on the
+// device, the non-finite flag is cleared), so nothing leaks from one call into
+// the next.  Calls whose work overlaps on the GPU (different streams, or
+// several host threads) race on the array: serialise them.
 #include <mutex>
 
 #include "nb_internal.cuh"
@@ -31,21 +31,26 @@ namespace {
 
 constexpr int64_t NA_MAX_N = 16384;   // bodies per call, at most
 constexpr int64_t NA_SLOTS = 8;       // partial-sum slots per body
-constexpr int64_t NA_RED = 16 * 256;  // reduction partials (16 x reduce_blocks())
+constexpr int64_t NA_SEGS = (NA_MAX_N + SEG_BODIES - 1) / SEG_BODIES;
+constexpr int64_t NA_H = 32768;       // near_table_size(NA_MAX_N)
 
 constexpr int64_t align256(int64_t b) { return (b + 255) / 256 * 256; }
 constexpr int64_t OFF_D = 0;                                                // x y z m
 constexpr int64_t OFF_F = OFF_D + align256(4 * NA_MAX_N * 8);               // 7 float planes
 constexpr int64_t OFF_J = OFF_F + align256(7 * NA_MAX_N * 4);               // jd, jl
 constexpr int64_t OFF_P = OFF_J + align256(4 * NA_MAX_N * 16);              // partial slots
-constexpr int64_t OFF_R = OFF_P + align256(NA_SLOTS * 3 * NA_MAX_N * 8);    // reductions
-constexpr int64_t OFF_G = OFF_R + align256(NA_RED * 8);                     // diag, frame, flag
-constexpr int64_t NA_H = 32768;                                             // near_table_size(NA_MAX_N)
-constexpr int64_t OFF_C = OFF_G + align256(16 * 8 + sizeof(Frame) + 16);    // near-pair correction
+constexpr int64_t OFF_C = OFF_P + align256(NA_SLOTS * 3 * NA_MAX_N * 8);    // near-pair correction
 constexpr int64_t OFF_K = OFF_C + align256(3 * NA_MAX_N * 8);               // cell keys
 constexpr int64_t OFF_I = OFF_K + align256(NA_MAX_N * 8);                   // bucket, entry
 constexpr int64_t OFF_H = OFF_I + align256(2 * NA_MAX_N * 4);               // count, start, bsum
-constexpr int64_t NA_BYTES = OFF_H + align256((2 * NA_H + 1 + NA_H / 1024 + 1) * 4);
+constexpr int64_t OFF_T = OFF_H + align256((2 * NA_H + 1 + NA_H / 1024 + 1) * 4);  // tables
+// tables of the single cluster: boff nk noff[2] uoff[2] eps2d dts (int64/double),
+// seg_lo[S] seg_hi[S], then ntiles eps2f seg_k[S] seg_off[2] flag (32-bit)
+constexpr int64_t T64 = 8 + 2 * NA_SEGS;
+constexpr int64_t T32 = 5 + NA_SEGS;
+constexpr int64_t OFF_R = OFF_T + align256(T64 * 8 + T32 * 4);              // reductions
+constexpr int64_t OFF_G = OFF_R + align256(NA_SEGS * 16 * 8);               // frame, diag
+constexpr int64_t NA_BYTES = OFF_G + align256(sizeof(Frame) + DIAG_STRIDE * 8);
 
 static __device__ __align__(256) unsigned char na_scratch[NA_BYTES];
 
@@ -65,6 +70,40 @@ int scratch_base(int dev, unsigned char **out)
     }
     *out = g_base[dev];
     return NB_OK;
+}
+
+struct TablePtrs {
+    int64_t *boff, *nk, *noff, *uoff, *seg_lo, *seg_hi;
+    double *eps2d, *dts;
+    int32_t *ntiles, *seg_k, *seg_off;
+    float *eps2f;
+    int *flag;
+};
+
+// Tables of one cluster of n bodies at pool slot 0, written on the device.
+__global__ void na_tables_kernel(TablePtrs t, int64_t n, double eps, int ipb)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int64_t nt = (n + TILE - 1) / TILE;
+    t.boff[0] = 0;
+    t.nk[0] = n;
+    t.noff[0] = 0;
+    t.noff[1] = n;
+    t.uoff[0] = 0;
+    t.uoff[1] = ((n + ipb - 1) / ipb) * nt;
+    t.ntiles[0] = (int32_t)nt;
+    t.eps2d[0] = eps * eps;
+    t.eps2f[0] = (float)(eps * eps);
+    t.dts[0] = 1.0;
+    int32_t S = 0;
+    for (int64_t lo = 0; lo < n; lo += SEG_BODIES, ++S) {
+        t.seg_k[S] = 0;
+        t.seg_lo[S] = lo;
+        t.seg_hi[S] = lo + SEG_BODIES < n ? lo + SEG_BODIES : n;
+    }
+    t.seg_off[0] = 0;
+    t.seg_off[1] = S;
+    *t.flag = 0;
 }
 
 __global__ void na_unpack_kernel(DevState s, const double *__restrict__ pos,
@@ -100,44 +139,61 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
         unsigned char *b = nullptr;
         rc = scratch_base(p->device, &b);
         if (rc) break;
-        cudaStream_t st = (cudaStream_t)p->stream;
-        DevState s;
-        s.n = n;
-        s.cap = NA_MAX_N;
-        double *d = reinterpret_cast<double *>(b + OFF_D);
-        s.x = d;
-        s.y = d + NA_MAX_N;
-        s.z = d + 2 * NA_MAX_N;
-        s.m = d + 3 * NA_MAX_N;
-        float *f = reinterpret_cast<float *>(b + OFF_F);
-        s.xh = f;
-        s.yh = f + NA_MAX_N;
-        s.zh = f + 2 * NA_MAX_N;
-        s.mf = f + 3 * NA_MAX_N;
-        s.xl = f + 4 * NA_MAX_N;
-        s.yl = f + 5 * NA_MAX_N;
-        s.zl = f + 6 * NA_MAX_N;
-        s.jd = reinterpret_cast<float4 *>(b + OFF_J);
-        s.jl = s.jd + 2 * NA_MAX_N;
-        s.part = reinterpret_cast<double *>(b + OFF_P);
-        s.part_slots = NA_SLOTS;
-        s.red = reinterpret_cast<double *>(b + OFF_R);
-        s.red_len = NA_RED;
-        s.diag = reinterpret_cast<double *>(b + OFF_G);
-        s.frame = reinterpret_cast<Frame *>(b + OFF_G + 16 * 8);
-        s.flag = reinterpret_cast<int *>(b + OFF_G + 16 * 8 + sizeof(Frame));
-        s.corr = reinterpret_cast<double *>(b + OFF_C);
-        s.ng_key = reinterpret_cast<uint64_t *>(b + OFF_K);
-        s.ng_bucket = reinterpret_cast<int *>(b + OFF_I);
-        s.ng_entry = s.ng_bucket + NA_MAX_N;
-        s.ng_count = reinterpret_cast<int *>(b + OFF_H);
-        s.ng_start = s.ng_count + NA_H;
-        s.ng_bsum = s.ng_start + NA_H + 1;
-        s.ng_hcap = NA_H;
         if (near_table_size(NA_MAX_N) != NA_H) {
             rc = NB_ECUDA;
             break;
         }
+        cudaStream_t st = (cudaStream_t)p->stream;
+        const int64_t N = NA_MAX_N;
+        DevState s;
+        s.n = n;
+        s.cap = N;
+        double *d = reinterpret_cast<double *>(b + OFF_D);
+        s.x = d;
+        s.y = d + N;
+        s.z = d + 2 * N;
+        s.m = d + 3 * N;
+        float *f = reinterpret_cast<float *>(b + OFF_F);
+        s.xh = f;
+        s.yh = f + N;
+        s.zh = f + 2 * N;
+        s.mf = f + 3 * N;
+        s.xl = f + 4 * N;
+        s.yl = f + 5 * N;
+        s.zl = f + 6 * N;
+        s.jd = reinterpret_cast<float4 *>(b + OFF_J);
+        s.jl = s.jd + 2 * N;
+        s.part = reinterpret_cast<double *>(b + OFF_P);
+        s.part_slots = NA_SLOTS;
+        s.corr = reinterpret_cast<double *>(b + OFF_C);
+        s.ng_key = reinterpret_cast<uint64_t *>(b + OFF_K);
+        s.ng_bucket = reinterpret_cast<int *>(b + OFF_I);
+        s.ng_entry = s.ng_bucket + N;
+        s.ng_count = reinterpret_cast<int *>(b + OFF_H);
+        s.ng_start = s.ng_count + NA_H;
+        s.ng_bsum = s.ng_start + NA_H + 1;
+        s.ng_hcap = NA_H;
+        TablePtrs t;
+        int64_t *t64 = reinterpret_cast<int64_t *>(b + OFF_T);
+        t.boff = t64;
+        t.nk = t64 + 1;
+        t.noff = t64 + 2;
+        t.uoff = t64 + 4;
+        t.eps2d = reinterpret_cast<double *>(t64 + 6);
+        t.dts = reinterpret_cast<double *>(t64 + 7);
+        t.seg_lo = t64 + 8;
+        t.seg_hi = t64 + 8 + NA_SEGS;
+        int32_t *t32 = reinterpret_cast<int32_t *>(t64 + T64);
+        t.ntiles = t32;
+        t.eps2f = reinterpret_cast<float *>(t32 + 1);
+        t.seg_off = t32 + 2;
+        t.flag = t32 + 4;
+        t.seg_k = t32 + 5;
+        s.flag = t.flag;
+        s.red = reinterpret_cast<double *>(b + OFF_R);
+        s.red_len = NA_SEGS * 16;
+        Frame *frame = reinterpret_cast<Frame *>(b + OFF_G);
+        s.diag = reinterpret_cast<double *>(b + OFF_G + sizeof(Frame));
 
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) !=
@@ -150,13 +206,31 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
                   : p->precision == NB_FP32 ? PM_FP32
                   : p->precision == NB_DS_FULL ? PM_DS_FULL : PM_DS_NEAR;
         pl.I = pl.mode == PM_FP64 ? 1 : 2;
+        const int ipb = TILE * pl.I;
         pl.blocks_per_sm = pair_occupancy(pl.mode, pl.I);
         if (pl.blocks_per_sm < 1) pl.blocks_per_sm = 1;
-        Decomp dc = make_decomp(n, TILE * pl.I, (int64_t)sms * pl.blocks_per_sm);
-        if (dc.W / 2 < dc.G) dc = make_decomp(n, TILE * pl.I, dc.W / 2 > 0 ? dc.W / 2 : 1);
-        while (dc.max_slots() > NA_SLOTS && dc.G > 1)
-            dc = make_decomp(n, TILE * pl.I, dc.G - dc.G / 8 - 1);
-        pl.d = dc;
+        const int64_t nt = (n + TILE - 1) / TILE;
+        const int64_t W = ((n + ipb - 1) / ipb) * nt;
+        int64_t G = (int64_t)sms * pl.blocks_per_sm;
+        if (W / 2 < G) G = W / 2 > 0 ? W / 2 : 1;
+        pl.d = make_decomp(W, nt, ipb, G, NA_SLOTS);
+
+        Clusters &c = s.cl;
+        c.K = 1;
+        c.boff = t.boff;
+        c.nk = t.nk;
+        c.noff = t.noff;
+        c.uoff = t.uoff;
+        c.ntiles = t.ntiles;
+        c.eps2f = t.eps2f;
+        c.eps2d = t.eps2d;
+        c.dts = t.dts;
+        c.frame = frame;
+        c.S = (int32_t)((n + SEG_BODIES - 1) / SEG_BODIES);
+        c.seg_k = t.seg_k;
+        c.seg_lo = t.seg_lo;
+        c.seg_hi = t.seg_hi;
+        c.seg_off = t.seg_off;
 
         ExtField ext;
         ext.on = p->ext_on;
@@ -167,32 +241,30 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
         ext.Mb = p->Mb;
         ext.ab = p->ab;
 
+        na_tables_kernel<<<1, 32, 0, st>>>(t, n, p->eps, ipb);
         na_unpack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, d_pos, d_mass);
         if (cudaGetLastError() != cudaSuccess) { rc = NB_ECUDA; break; }
         if (pl.mode != PM_FP64) {
             const double nf = p->near_frac > 0 ? p->near_frac : 0.4;
-            if (launch_frame(s, nf, p->eps, st) != cudaSuccess ||
-                launch_split(s, st) != cudaSuccess) {
+            if (launch_frame(s, nf, st) != cudaSuccess || launch_split(s, st) != cudaSuccess) {
                 rc = NB_ECUDA;
                 break;
             }
         }
-        if (cudaMemsetAsync(s.flag, 0, sizeof(int), st) != cudaSuccess ||
-            launch_pair(s, pl, p->G, p->eps, st) != cudaSuccess) {
+        if (launch_pair(s, pl, p->G, st) != cudaSuccess) {
             rc = NB_ECUDA;
             break;
         }
         // the mixed mode re-forms near pairs from the double-single difference
         if (pl.mode == PM_DS_NEAR) {
-            if (launch_near_correct(s, p->eps, p->G, st) != cudaSuccess) {
+            if (launch_near_correct(s, p->G, st) != cudaSuccess) {
                 rc = NB_ECUDA;
                 break;
             }
         } else {
             s.corr = nullptr;
         }
-        if (launch_accel_out(s, pl.d, ext, p->G, d_acc_out, st) != cudaSuccess)
-            rc = NB_ECUDA;
+        if (launch_accel_out(s, pl.d, ext, d_acc_out, st) != cudaSuccess) rc = NB_ECUDA;
     } while (0);
     if (prev != p->device) cudaSetDevice(prev);
     return rc;

@@ -1,14 +1,16 @@
 // pair.cu -- all-pairs softened gravity (eq. 5; eq. 2 when eps = 0) on sm_103a.
 //
-// Every kernel here walks the same persistent decomposition (Decomp): a grid
-// of G blocks, one contiguous run of (i-block, j-tile) units per block, so
-// every SM gets the same amount of work whatever N is.  Each thread owns I
-// i-bodies and keeps their sums in registers; every pair of the N x N array
-// is evaluated, as in the paper (Sect. 3.2), not N(N-1)/2.
+// Every kernel here walks the same persistent decomposition (Decomp) of the
+// pair work of a set of independent clusters: a grid of G blocks, one
+// contiguous run of (cluster, i-block, j-tile) units per block, so every SM
+// gets the same amount of work whatever the cluster sizes are (one cluster,
+// or an ensemble of uneven clusters in one launch).  Each thread owns I
+// i-bodies and keeps their sums in registers; every pair of each cluster's
+// N x N array is evaluated, as in the paper (Sect. 3.2), not N(N-1)/2.
 //
 // Single-precision family (one template, three modes):
-//   PM_DS_NEAR  float pair arithmetic on coordinates relative to the frame
-//               origin, per-tile float sums folded into double-single
+//   PM_DS_NEAR  float pair arithmetic on coordinates relative to the cluster's
+//               frame origin, per-tile float sums folded into double-single
 //               accumulators (Sect. 4.2's software double precision); pairs
 //               closer than the near radius are re-formed from the
 //               double-single coordinate difference (hi_j - hi_i) +
@@ -30,17 +32,20 @@
 
 namespace nb {
 
-Decomp make_decomp(int64_t n, int ipb, int64_t G)
+Decomp make_decomp(int64_t W, int64_t max_ntiles, int ipb, int64_t G, int64_t slot_cap)
 {
     Decomp d;
-    d.n = n;
     d.ipb = ipb;
-    d.ntiles = (int32_t)((n + TILE - 1) / TILE);
-    d.iblocks = (n + ipb - 1) / ipb;
-    d.W = d.iblocks * (int64_t)d.ntiles;
+    d.W = W > 0 ? W : 1;
     if (G > d.W) G = d.W;
     if (G < 1) G = 1;
-    d.G = G;
+    for (;;) {
+        d.G = G;
+        d.slots = (max_ntiles * G + d.W - 1) / d.W + 1;
+        if (d.slots <= slot_cap || G == 1) break;
+        G = G - G / 8 - 1;
+        if (G < 1) G = 1;
+    }
     return d;
 }
 
@@ -64,11 +69,39 @@ __device__ __forceinline__ void ds_add(float &hi, float &lo, float t)
     hi = h;
 }
 
+// One contiguous run of units of block g inside one cluster's i-block.
+struct Segment {
+    int32_t k;        // cluster
+    int64_t base;     // first pool slot of the cluster
+    int32_t nk;       // bodies of the cluster
+    int32_t b;        // i-block
+    int32_t t0, t1;   // j tiles [t0, t1)
+    int64_t slot;     // partial slot of this block for the i-block
+};
+
+__device__ __forceinline__ Segment segment_at(const Decomp &d, const Clusters &c, int64_t g,
+                                              int64_t u, int64_t uend)
+{
+    Segment s;
+    s.k = find_cluster(c.uoff, c.K, u);
+    const int64_t u0 = c.uoff[s.k];
+    const int32_t nt = c.ntiles[s.k];
+    const int64_t lu = u - u0;
+    s.b = (int32_t)(lu / nt);
+    s.t0 = (int32_t)(lu - (int64_t)s.b * nt);
+    const int64_t left = uend - u;
+    s.t1 = (int64_t)s.t0 + left < nt ? (int32_t)(s.t0 + left) : nt;
+    s.base = c.boff[s.k];
+    s.nk = (int32_t)c.nk[s.k];
+    s.slot = g - d.owner(u0 + (int64_t)s.b * nt);
+    return s;
+}
+
 constexpr int CH = 32;            // j bodies per warp chunk
 constexpr int WARPS = TILE / 32;  // warps per block
 
 // Thread-private i bodies, two per packed register pair: pair p holds bodies
-// k = 2p (.x) and k = 2p + 1 (.y), body k = ib0 + tid + k * TILE.
+// k = 2p (.x) and k = 2p + 1 (.y), local body k = ib0 + tid + k * TILE.
 template <int P>
 struct IPairs {
     float2 nx[P], ny[P], nz[P];     // negated hi coordinates
@@ -76,8 +109,9 @@ struct IPairs {
     float2 ax[P], ay[P], az[P];     // float sums of the current 128-j tile
 };
 
-// One chunk of CH j bodies against the thread's 2P i bodies.  MASK zeroes the
-// j == i term (eps = 0, diagonal chunks).
+// One chunk of CH j bodies (local indices j0 ...) against the thread's 2P i
+// bodies (local indices ibase + k * TILE).  MASK zeroes the j == i term
+// (eps = 0, diagonal chunks).
 template <int P, int MODE, bool MASK>
 __device__ __forceinline__ void chunk_pass(const float4 (*cb)[4], int j0, int ibase,
                                            IPairs<P> &ip, float eps2)
@@ -137,8 +171,7 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
     const float4 *__restrict__ jd, const float4 *__restrict__ jl,
     const float *__restrict__ xh, const float *__restrict__ yh, const float *__restrict__ zh,
     const float *__restrict__ xl, const float *__restrict__ yl, const float *__restrict__ zl,
-    const Frame *__restrict__ frame, Decomp d, float eps2, int mask_self, double G,
-    double *__restrict__ part, int64_t cap)
+    Clusters c, Decomp d, double G, double *__restrict__ part, int64_t cap)
 {
     constexpr int I = 2 * P;
     constexpr bool FULL = (MODE == PM_DS_FULL);
@@ -151,28 +184,29 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
     const int lane = tid & 31;
     const int w = tid >> 5;
     const float4(*cb)[4] = cbuf[w];
-    const int n = (int)d.n;
     const int64_t g = blockIdx.x;
     int64_t u = d.U(g);
     const int64_t uend = d.U(g + 1);
-    (void)frame;
     const float4 far4 = make_float4(FAR_F, FAR_F, FAR_F, FAR_F);
     const float4 farm = make_float4(FAR_F, FAR_F, 0.f, 0.f);
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
 
     while (u < uend) {
-        const int64_t b = u / d.ntiles;
-        const int t0 = (int)(u - b * d.ntiles);
-        const int t1 = (int)((int64_t)t0 + (uend - u) < d.ntiles ? t0 + (uend - u) : d.ntiles);
-        const int64_t slot = g - d.gfirst(b);
-        const int ib0 = (int)(b * d.ipb);
+        const Segment sg = segment_at(d, c, g, u, uend);
+        const int n = sg.nk;
+        const int64_t base = sg.base;
+        const float eps2 = c.eps2f[sg.k];
+        const bool mask_self = eps2 == 0.f;
+        const int ib0 = sg.b * d.ipb;
         const int ibase = ib0 + tid;
+        const float4 *jdk = jd + 2 * base;
+        const float4 *jlk = jl + 2 * base;
 
         IPairs<P> ip;
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             const int ia = ibase + 2 * p * TILE, ib = ia + TILE;
-            const int ca = ia < n ? ia : n - 1, cb2 = ib < n ? ib : n - 1;
+            const int64_t ca = base + (ia < n ? ia : n - 1), cb2 = base + (ib < n ? ib : n - 1);
             ip.nx[p] = make_float2(-xh[ca], -xh[cb2]);
             ip.ny[p] = make_float2(-yh[ca], -yh[cb2]);
             ip.nz[p] = make_float2(-zh[ca], -zh[cb2]);
@@ -186,15 +220,15 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
 #pragma unroll
         for (int r = 0; r < 6 * I; ++r) acc_sh[r][tid] = 0.f;
 
-        const int J0 = t0 * TILE, J1 = t1 * TILE;
+        const int J0 = sg.t0 * TILE, J1 = sg.t1 * TILE;
         float4 pf[4];
         {
             const int j = J0 + lane;
-            pf[0] = j < n ? jd[2 * j] : far4;
-            pf[1] = j < n ? jd[2 * j + 1] : farm;
+            pf[0] = j < n ? jdk[2 * j] : far4;
+            pf[1] = j < n ? jdk[2 * j + 1] : farm;
             if (FULL) {
-                pf[2] = j < n ? jl[2 * j] : zero4;
-                pf[3] = j < n ? jl[2 * j + 1] : zero4;
+                pf[2] = j < n ? jlk[2 * j] : zero4;
+                pf[3] = j < n ? jlk[2 * j + 1] : zero4;
             }
         }
         for (int jc = J0; jc < J1; jc += CH) {
@@ -203,11 +237,11 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
             __syncwarp();
             if (jc + CH < J1) {
                 const int j = jc + CH + lane;
-                pf[0] = j < n ? jd[2 * j] : far4;
-                pf[1] = j < n ? jd[2 * j + 1] : farm;
+                pf[0] = j < n ? jdk[2 * j] : far4;
+                pf[1] = j < n ? jdk[2 * j + 1] : farm;
                 if (FULL) {
-                    pf[2] = j < n ? jl[2 * j] : zero4;
-                    pf[3] = j < n ? jl[2 * j + 1] : zero4;
+                    pf[2] = j < n ? jlk[2 * j] : zero4;
+                    pf[3] = j < n ? jlk[2 * j + 1] : zero4;
                 }
             }
             const bool diag = mask_self && jc < ib0 + d.ipb && jc + CH > ib0;
@@ -222,21 +256,21 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
                 for (int p = 0; p < P; ++p) {
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const int k = 2 * p + h;
+                        const int kk = 2 * p + h;
                         const float t[3] = {h ? ip.ax[p].y : ip.ax[p].x,
                                             h ? ip.ay[p].y : ip.ay[p].x,
                                             h ? ip.az[p].y : ip.az[p].x};
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            float hi = acc_sh[c * I + k][tid];
+                        for (int cc = 0; cc < 3; ++cc) {
+                            float hi = acc_sh[cc * I + kk][tid];
                             if (DSACC) {
-                                float lo = acc_sh[(3 + c) * I + k][tid];
-                                ds_add(hi, lo, t[c]);
-                                acc_sh[(3 + c) * I + k][tid] = lo;
+                                float lo = acc_sh[(3 + cc) * I + kk][tid];
+                                ds_add(hi, lo, t[cc]);
+                                acc_sh[(3 + cc) * I + kk][tid] = lo;
                             } else {
-                                hi = __fadd_rn(hi, t[c]);
+                                hi = __fadd_rn(hi, t[cc]);
                             }
-                            acc_sh[c * I + k][tid] = hi;
+                            acc_sh[cc * I + kk][tid] = hi;
                         }
                     }
                     ip.ax[p] = ip.ay[p] = ip.az[p] = make_float2(0.f, 0.f);
@@ -245,17 +279,17 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
         }
 
 #pragma unroll
-        for (int k = 0; k < I; ++k) {
-            const int i = ibase + k * TILE;
+        for (int kk = 0; kk < I; ++kk) {
+            const int i = ibase + kk * TILE;
             if (i < n) {
-                double *o = part + (slot * 3) * cap + i;
+                double *o = part + (sg.slot * 3) * cap + base + i;
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    o[c * cap] = G * ((double)acc_sh[c * I + k][tid] +
-                                      (double)acc_sh[(3 + c) * I + k][tid]);
+                for (int cc = 0; cc < 3; ++cc)
+                    o[cc * cap] = G * ((double)acc_sh[cc * I + kk][tid] +
+                                       (double)acc_sh[(3 + cc) * I + kk][tid]);
             }
         }
-        u += t1 - t0;
+        u += sg.t1 - sg.t0;
     }
 }
 
@@ -267,49 +301,49 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
 template <int I, bool POT>
 __global__ void __launch_bounds__(TILE) pair_fp64_kernel(
     const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
-    const double *__restrict__ m, Decomp d, double eps2, int mask_self, double G,
-    double *__restrict__ part, int64_t cap)
+    const double *__restrict__ m, Clusters c, Decomp d, double G, double *__restrict__ part,
+    int64_t cap)
 {
     __shared__ double sx[TILE], sy[TILE], sz[TILE], sm[TILE];
     const int tid = threadIdx.x;
-    const int n = (int)d.n;
     const int64_t g = blockIdx.x;
     int64_t u = d.U(g);
     const int64_t uend = d.U(g + 1);
 
     while (u < uend) {
-        const int64_t b = u / d.ntiles;
-        const int t0 = (int)(u - b * d.ntiles);
-        const int t1 = (int)((int64_t)t0 + (uend - u) < d.ntiles ? t0 + (uend - u) : d.ntiles);
-        const int64_t slot = g - d.gfirst(b);
-        const int ib0 = (int)(b * d.ipb);
+        const Segment sg = segment_at(d, c, g, u, uend);
+        const int n = sg.nk;
+        const int64_t base = sg.base;
+        const double eps2 = c.eps2d[sg.k];
+        const bool mask_self = POT || eps2 == 0.0;
+        const int ib0 = sg.b * d.ipb;
         int idx[I];
         double xi[I], yi[I], zi[I], ax[I], ay[I], az[I];
 #pragma unroll
         for (int k = 0; k < I; ++k) {
             const int i = ib0 + tid + k * TILE;
-            const int ic = i < n ? i : n - 1;
+            const int64_t ic = base + (i < n ? i : n - 1);
             idx[k] = i;
             xi[k] = x[ic];
             yi[k] = y[ic];
             zi[k] = z[ic];
             ax[k] = ay[k] = az[k] = 0.0;
         }
-        for (int t = t0; t < t1; ++t) {
+        for (int t = sg.t0; t < sg.t1; ++t) {
             const int jglob = t * TILE;
             const int j = jglob + tid;
             __syncthreads();
             if (j < n) {
-                sx[tid] = x[j];
-                sy[tid] = y[j];
-                sz[tid] = z[j];
-                sm[tid] = m[j];
+                sx[tid] = x[base + j];
+                sy[tid] = y[base + j];
+                sz[tid] = z[base + j];
+                sm[tid] = m[base + j];
             } else {
                 sx[tid] = sy[tid] = sz[tid] = FAR_D;
                 sm[tid] = 0.0;
             }
             __syncthreads();
-            const bool diag = (POT || mask_self) && jglob < ib0 + d.ipb && jglob + TILE > ib0;
+            const bool diag = mask_self && jglob < ib0 + d.ipb && jglob + TILE > ib0;
 #pragma unroll 2
             for (int jj = 0; jj < TILE; ++jj) {
                 const double xj = sx[jj], yj = sy[jj], zj = sz[jj], mj = sm[jj];
@@ -321,9 +355,9 @@ __global__ void __launch_bounds__(TILE) pair_fp64_kernel(
                     r2 = fma(dz, dz, r2);
                     const double ri = rsqrt(r2);
                     if (POT) {
-                        double w = mj * ri;
-                        if (diag && jglob + jj == idx[k]) w = 0.0;
-                        ax[k] += w;
+                        double wgt = mj * ri;
+                        if (diag && jglob + jj == idx[k]) wgt = 0.0;
+                        ax[k] += wgt;
                     } else {
                         double s = (mj * ri) * (ri * ri);
                         if (diag && jglob + jj == idx[k]) s = 0.0;
@@ -338,7 +372,7 @@ __global__ void __launch_bounds__(TILE) pair_fp64_kernel(
         for (int k = 0; k < I; ++k) {
             const int i = idx[k];
             if (i < n) {
-                double *p = part + (slot * 3) * cap + i;
+                double *p = part + (sg.slot * 3) * cap + base + i;
                 if (POT) {
                     p[0] = ax[k];
                 } else {
@@ -348,7 +382,7 @@ __global__ void __launch_bounds__(TILE) pair_fp64_kernel(
                 }
             }
         }
-        u += t1 - t0;
+        u += sg.t1 - sg.t0;
     }
 }
 
@@ -356,9 +390,9 @@ __global__ void __launch_bounds__(TILE) pair_fp64_kernel(
 
 typedef void (*sp_kernel_t)(const float4 *, const float4 *, const float *, const float *,
                             const float *, const float *, const float *, const float *,
-                            const Frame *, Decomp, float, int, double, double *, int64_t);
+                            Clusters, Decomp, double, double *, int64_t);
 typedef void (*dp_kernel_t)(const double *, const double *, const double *, const double *,
-                            Decomp, double, int, double, double *, int64_t);
+                            Clusters, Decomp, double, double *, int64_t);
 
 // I (bodies per thread) = 2P for the single-precision family.
 static sp_kernel_t sp_variant(int mode, int I)
@@ -397,29 +431,26 @@ int pair_occupancy(int mode, int I)
     return nb;
 }
 
-cudaError_t launch_pair(const DevState &s, const PairLaunch &pl, double G, double eps,
-                        cudaStream_t st)
+cudaError_t launch_pair(const DevState &s, const PairLaunch &pl, double G, cudaStream_t st)
 {
-    const int mask_self = eps == 0.0 ? 1 : 0;
     const dim3 grid((unsigned)pl.d.G), block(TILE);
     if (pl.mode == PM_FP64) {
         dp_kernel_t k = dp_variant(pl.I);
         if (!k) return cudaErrorInvalidValue;
-        k<<<grid, block, 0, st>>>(s.x, s.y, s.z, s.m, pl.d, eps * eps, mask_self, G, s.part,
-                                  s.cap);
+        k<<<grid, block, 0, st>>>(s.x, s.y, s.z, s.m, s.cl, pl.d, G, s.part, s.cap);
     } else {
         sp_kernel_t k = sp_variant(pl.mode, pl.I);
         if (!k) return cudaErrorInvalidValue;
-        k<<<grid, block, 0, st>>>(s.jd, s.jl, s.xh, s.yh, s.zh, s.xl, s.yl, s.zl, s.frame,
-                                  pl.d, (float)(eps * eps), mask_self, G, s.part, s.cap);
+        k<<<grid, block, 0, st>>>(s.jd, s.jl, s.xh, s.yh, s.zh, s.xl, s.yl, s.zl, s.cl, pl.d, G,
+                                  s.part, s.cap);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_potential(const DevState &s, const Decomp &d, double eps, cudaStream_t st)
+cudaError_t launch_potential(const DevState &s, const Decomp &d, cudaStream_t st)
 {
-    pair_fp64_kernel<1, true><<<(unsigned)d.G, TILE, 0, st>>>(s.x, s.y, s.z, s.m, d, eps * eps,
-                                                               1, 1.0, s.part, s.cap);
+    pair_fp64_kernel<1, true><<<(unsigned)d.G, TILE, 0, st>>>(s.x, s.y, s.z, s.m, s.cl, d, 1.0,
+                                                               s.part, s.cap);
     return cudaGetLastError();
 }
 

@@ -81,6 +81,11 @@ nb_prof_enable = _sig("nb_prof_enable", C.c_int, _ctxp, C.c_int)
 nb_prof_read = _sig("nb_prof_read", C.c_int, _ctxp, C.POINTER(ProfT))
 nb_destroy = _sig("nb_destroy", None, _ctxp)
 nb_measure_peaks = _sig("nb_measure_peaks", C.c_int, C.c_int, C.POINTER(PeaksT))
+nb_create_batch = _sig("nb_create_batch", C.c_int, C.POINTER(Params), C.c_int64,
+                       C.POINTER(C.c_int64), C.POINTER(_ctxp))
+nb_set_cluster_params = _sig("nb_set_cluster_params", C.c_int, _ctxp, _dp, _dp)
+nb_clusters = _sig("nb_clusters", C.c_int64, _ctxp)
+nb_energy_clusters = _sig("nb_energy_clusters", C.c_int, _ctxp, C.POINTER(EnergyT))
 nb_accel_static = _sig("nb_accel_static", C.c_int, C.POINTER(Params), C.c_int64, _vp, _vp, _vp)
 
 
@@ -133,12 +138,15 @@ class Energy:
 
 
 class Context:
-    """One particle system resident on one GPU (``nb_ctx``)."""
+    """One particle system (``nb_create``) or an ensemble of independent
+    clusters of fixed sizes (``sizes=...``, ``nb_create_batch``) resident on
+    one GPU (``nb_ctx``)."""
 
-    def __init__(self, capacity: int, G: float = 1.0, eps: float = 0.0,
+    def __init__(self, capacity: int = 0, G: float = 1.0, eps: float = 0.0,
                  precision: int | str = NB_DS, ext_on: bool = False,
                  Md: float = 100.0, ad: float = 6.5, bd: float = 0.26, Mb: float = 15.0,
-                 ab: float = 0.7, device: int = 0, stream=None, near_frac: float = 0.0):
+                 ab: float = 0.7, device: int = 0, stream=None, near_frac: float = 0.0,
+                 sizes=None):
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
         p = Params()
@@ -149,9 +157,31 @@ class Context:
         p.stream = _addr(stream) if stream is not None else None
         p.near_frac = near_frac
         h = _ctxp()
-        check(nb_create(C.byref(p), int(capacity), C.byref(h)))
+        if sizes is None:
+            check(nb_create(C.byref(p), int(capacity), C.byref(h)))
+            self.capacity = int(capacity)
+        else:
+            sz = np.ascontiguousarray(sizes, dtype=np.int64)
+            check(nb_create_batch(C.byref(p), sz.size,
+                                  sz.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(h)))
+            self.capacity = int(sz.sum())
         self._h = h
-        self.capacity = int(capacity)
+
+    @property
+    def clusters(self) -> int:
+        return int(check(nb_clusters(self._h)))
+
+    def set_cluster_params(self, eps=None, dt_scale=None):
+        e = None if eps is None else np.ascontiguousarray(eps, dtype=np.float64)
+        d = None if dt_scale is None else np.ascontiguousarray(dt_scale, dtype=np.float64)
+        check(nb_set_cluster_params(self._h, None if e is None else _p(e),
+                                    None if d is None else _p(d)))
+
+    def energy_clusters(self) -> list:
+        k = self.clusters
+        arr = (EnergyT * k)()
+        check(nb_energy_clusters(self._h, arr))
+        return [Energy(e.K, e.W, e.W_ext, e.E, np.array(e.P[:]), np.array(e.L[:])) for e in arr]
 
     # -- lifecycle
     def close(self):

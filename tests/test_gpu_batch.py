@@ -1,0 +1,125 @@
+"""Batched ensemble: many independent clusters of uneven size integrated by
+one persistent launch per force evaluation.  Each cluster's result must equal
+the same cluster run alone (its own context), within the parity tolerances,
+and match the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1003_3896_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [300, 1000, 129, 2048, 777, 4100, 256, 1]
+
+
+@pytest.fixture(scope="module")
+def nbs():
+    from paper_1003_3896_gb300 import build
+    build.build()
+    from paper_1003_3896_gb300 import nbsym
+    return nbsym
+
+
+def rel_rms(a, ref):
+    den = (ref ** 2).sum()
+    return math.sqrt(((a - ref) ** 2).sum() / den) if den > 0 else float(np.abs(a - ref).max())
+
+
+def clusters(sizes, base_seed=100):
+    out = []
+    for k, n in enumerate(sizes):
+        pos, vel, m = ics.henon_plummer(n, base_seed + k)
+        out.append((pos, vel, m, ics.paper_softening(n)))
+    return out
+
+
+def concat(cl):
+    return (np.concatenate([c[0] for c in cl]), np.concatenate([c[1] for c in cl]),
+            np.concatenate([c[2] for c in cl]))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "ds", "fp32"])
+def test_batch_accel_matches_oracle_and_alone(nbs, orc, prec):
+    cl = clusters(SIZES)
+    pos, vel, m = concat(cl)
+    eps = [c[3] for c in cl]
+    with nbs.Context(sizes=SIZES, precision=prec) as b:
+        assert b.clusters == len(SIZES)
+        b.set_cluster_params(eps=eps)
+        b.load(pos, vel, m)
+        a = b.accel()
+    tol = {"fp64": 1e-12, "ds": 1e-6, "fp32": 1e-4}[prec]
+    off = 0
+    for (p, v, mm, e), n in zip(cl, SIZES):
+        ref = orc.accel_int(p, mm, 1.0, e)
+        got = a[off:off + n]
+        if n > 1:
+            assert rel_rms(got, ref) <= tol, (n, rel_rms(got, ref))
+        else:
+            assert np.all(got == 0)
+        with nbs.Context(n, eps=e, precision=prec) as c:
+            c.load(p, v, mm)
+            alone = c.accel()
+        # same arithmetic, different grouping of partial sums
+        assert rel_rms(got, alone) <= (1e-14 if prec == "fp64" else 1e-6)
+        off += n
+
+
+@pytest.mark.parametrize("prec", ["fp64", "ds"])
+def test_batch_steps_equal_alone_runs(nbs, orc, prec):
+    """Four SI6A steps of the whole ensemble with per-cluster softening and
+    per-cluster step scale against each cluster stepped alone."""
+    cl = clusters(SIZES, base_seed=200)
+    pos, vel, m = concat(cl)
+    eps = [c[3] for c in cl]
+    scale = [1.0 + 0.25 * (k % 3) for k in range(len(SIZES))]
+    dt = 1.0 / 512
+    with nbs.Context(sizes=SIZES, precision=prec) as b:
+        b.set_cluster_params(eps=eps, dt_scale=scale)
+        b.load(pos, vel, m)
+        e_cl = b.energy_clusters()
+        b.step(6, dt, 4)
+        x, v = b.get_state()
+    off = 0
+    tol = 1e-12 if prec == "fp64" else 1e-8
+    for k, ((p, vv, mm, e), n) in enumerate(zip(cl, SIZES)):
+        with nbs.Context(n, eps=e, precision=prec) as c:
+            c.load(p, vv, mm)
+            e_alone = c.energy()
+            c.step(6, dt * scale[k], 4)
+            xa, va = c.get_state()
+        assert np.abs(x[off:off + n] - xa).max() <= tol
+        assert np.abs(v[off:off + n] - va).max() <= tol * 10
+        assert abs(e_cl[k].E - e_alone.E) <= 1e-13 * abs(e_alone.E) + 1e-300
+        if k == 3:
+            rx, rv = orc.run(p, vv, mm, orc.Params(eps=e), 6, dt * scale[k], 4)
+            assert np.abs(x[off:off + n] - rx).max() <= (1e-10 if prec == "fp64" else 1e-6)
+        off += n
+
+
+def test_batch_energy_totals(nbs, orc):
+    cl = clusters(SIZES[:5], base_seed=300)
+    pos, vel, m = concat(cl)
+    with nbs.Context(sizes=SIZES[:5], precision="ds", eps=0.01) as b:
+        b.load(pos, vel, m)
+        per = b.energy_clusters()
+        tot = b.energy()
+    assert abs(sum(e.E for e in per) - tot.E) <= 1e-14 * abs(tot.E)
+    for (p, v, mm, _), e in zip(cl, per):
+        r = orc.energy(p, v, mm, orc.Params(eps=0.01))
+        assert abs(e.E - r.E) <= 1e-12 * abs(r.E)
+        np.testing.assert_allclose(e.L, r.L, rtol=0, atol=1e-13)
+
+
+def test_batch_rejects_bad_shapes(nbs):
+    with pytest.raises(nbs.NBError):
+        nbs.Context(sizes=[10, 0, 5])
+    with nbs.Context(sizes=[10, 5]) as b:
+        p, v, m = ics.henon_plummer(14, 0)
+        with pytest.raises(nbs.NBError) as e:
+            b.load(p, v, m)
+        assert e.value.code == nbs.NB_EINVAL
+        with pytest.raises(nbs.NBError):
+            b.set_cluster_params(eps=[0.1, -1.0])
