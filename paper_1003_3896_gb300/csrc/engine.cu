@@ -291,6 +291,8 @@ int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan
     int64_t G = (int64_t)P.num_sms * pl.pl.blocks_per_sm;
     if (W / 2 < G) G = W / 2 > 0 ? W / 2 : 1;   // at least two units per block
     pl.pl.d = make_decomp(W, C.max_ntiles, TILE * I, G, P.s.part_slots);
+    for (int32_t k = 0; k < C.K; ++k)
+        if (C.eps2d[k] == 0.0) pl.pl.d.mask_self = 1;
     int occ = pair_occupancy(PM_FP64, 1);
     if (occ < 1) occ = 1;
     const int64_t Wp = C.uoff_pot[C.K];

@@ -103,6 +103,10 @@ struct Decomp {
     int64_t W = 0;        // total units
     int64_t G = 1;        // persistent blocks (grid size), 1 <= G <= W
     int64_t slots = 1;    // max partial slots any i-block needs
+    // 1 when some cluster has eps = 0: the j == i term is then masked in every
+    // cluster (for eps > 0 it is exactly zero anyway), which keeps the
+    // decision a launch-wide constant
+    int32_t mask_self = 0;
 
     __host__ __device__ int64_t U(int64_t g) const { return (g * W) / G; }
     // largest g with U(g) <= u

@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
         const int n = sg.nk;
         const int64_t base = sg.base;
         const float eps2 = c.eps2f[sg.k];
-        const bool mask_self = eps2 == 0.f;
+        const bool mask_self = d.mask_self != 0;
         const int ib0 = sg.b * d.ipb;
         const int ibase = ib0 + tid;
         const float4 *jdk = jd + 2 * base;
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(TILE) pair_fp64_kernel(
         const int n = sg.nk;
         const int64_t base = sg.base;
         const double eps2 = c.eps2d[sg.k];
-        const bool mask_self = POT || eps2 == 0.0;
+        const bool mask_self = POT || d.mask_self != 0;
         const int ib0 = sg.b * d.ipb;
         int idx[I];
         double xi[I], yi[I], zi[I], ax[I], ay[I], az[I];
