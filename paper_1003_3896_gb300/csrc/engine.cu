@@ -347,7 +347,14 @@ int enq_force(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph
     const unsigned evf =
         cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (ev0) NB_TRY(cudaEventRecordWithFlags(ev0, st, evf));
-    NB_TRY(launch_pair(s, pl.pl, ph.G, st));
+    HostTab ht;
+    ht.K = C.K;
+    ht.uoff = C.uoff.data();
+    ht.boff = C.boff.data();
+    ht.nk = C.nk.data();
+    ht.ntiles = C.ntiles.data();
+    ht.eps2f = C.eps2f.data();
+    NB_TRY(launch_pair(s, pl.pl, ht, ph.G, st));
     if (ev1) NB_TRY(cudaEventRecordWithFlags(ev1, st, evf));
     count(kernels, 1);
     if (pl.precision == NB_DS) {

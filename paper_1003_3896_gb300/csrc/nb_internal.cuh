@@ -143,13 +143,27 @@ struct PairLaunch {
     Decomp d;
 };
 
+// Host copy of the per-cluster values the pair kernels need per segment.  Up
+// to PARAM_CLUSTERS clusters travel by value as a kernel parameter, where the
+// compiler knows them to be uniform across the block (loop bounds and
+// addresses then live in uniform registers); larger sets read the device
+// tables of Clusters.
+constexpr int PARAM_CLUSTERS = 512;
+struct HostTab {
+    int32_t K = 0;
+    const int64_t *uoff = nullptr, *boff = nullptr, *nk = nullptr;
+    const int32_t *ntiles = nullptr;
+    const float *eps2f = nullptr;
+};
+
 // Resident blocks per SM of a pair-kernel variant (occupancy query).
 int pair_occupancy(int mode, int I);
 bool pair_variant_exists(int mode, int I);
 // Decomposition of the pair work of clusters with host-side sizes nk and
 // tiles, given units per cluster (host arrays), i-block width, target grid.
 Decomp make_decomp(int64_t W, int64_t max_ntiles, int ipb, int64_t G, int64_t slot_cap);
-cudaError_t launch_pair(const DevState &s, const PairLaunch &pl, double G, cudaStream_t st);
+cudaError_t launch_pair(const DevState &s, const PairLaunch &pl, const HostTab &ht, double G,
+                        cudaStream_t st);
 // Potential sums phi_i = sum_{j != i} m_j / sqrt(r^2 + eps^2) (FP64) into
 // slot planes of s.part (component 0); decomposition with ipb = TILE.
 cudaError_t launch_potential(const DevState &s, const Decomp &d, cudaStream_t st);

@@ -252,7 +252,17 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
                 break;
             }
         }
-        if (launch_pair(s, pl, p->G, st) != cudaSuccess) {
+        const int64_t h_uoff[2] = {0, W}, h_boff[1] = {0}, h_nk[1] = {n};
+        const int32_t h_nt[1] = {(int32_t)nt};
+        const float h_e2[1] = {(float)(p->eps * p->eps)};
+        HostTab ht;
+        ht.K = 1;
+        ht.uoff = h_uoff;
+        ht.boff = h_boff;
+        ht.nk = h_nk;
+        ht.ntiles = h_nt;
+        ht.eps2f = h_e2;
+        if (launch_pair(s, pl, ht, p->G, st) != cudaSuccess) {
             rc = NB_ECUDA;
             break;
         }

@@ -28,6 +28,8 @@
 // rsqrt runs on the MUFU pipe (rsqrt.approx).  Arithmetic uses explicit
 // round-to-nearest intrinsics so the near-pair correction reproduces this
 // loop's float contribution bit for bit.
+#include <cstring>
+
 #include "nb_internal.cuh"
 
 namespace nb {
@@ -78,6 +80,48 @@ struct Segment {
     int32_t t0, t1;   // j tiles [t0, t1)
     int64_t slot;     // partial slot of this block for the i-block
 };
+
+// Per-cluster values by value (kernel parameter): uniform across the block.
+template <int KC>
+struct ParamTab {
+    int32_t K;
+    int64_t uoff[KC + 1];
+    int64_t boff[KC];
+    int32_t nk[KC];
+    int32_t ntiles[KC];
+    float eps2f[KC];
+};
+
+// largest k in [0, K) with off[k] <= t
+template <typename T>
+__device__ __forceinline__ int32_t find_in(const T *off, int32_t K, int64_t t)
+{
+    int32_t lo = 0, hi = K;
+    while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (off[mid] <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <int KC>
+__device__ __forceinline__ Segment segment_at(const Decomp &d, const ParamTab<KC> &t, int64_t g,
+                                              int64_t u, int64_t uend)
+{
+    Segment s;
+    s.k = KC == 1 ? 0 : find_in(t.uoff, t.K, u);
+    const int64_t u0 = t.uoff[s.k];
+    const int32_t nt = t.ntiles[s.k];
+    const int64_t lu = u - u0;
+    s.b = (int32_t)(lu / nt);
+    s.t0 = (int32_t)(lu - (int64_t)s.b * nt);
+    const int64_t left = uend - u;
+    s.t1 = (int64_t)s.t0 + left < nt ? (int32_t)(s.t0 + left) : nt;
+    s.base = t.boff[s.k];
+    s.nk = t.nk[s.k];
+    s.slot = g - d.owner(u0 + (int64_t)s.b * nt);
+    return s;
+}
 
 __device__ __forceinline__ Segment segment_at(const Decomp &d, const Clusters &c, int64_t g,
                                               int64_t u, int64_t uend)
@@ -166,12 +210,18 @@ __device__ __forceinline__ void chunk_pass(const float4 (*cb)[4], int j0, int ib
 // thread trade registers against shared-memory broadcasts per pair.
 __host__ __device__ constexpr int sp_min_blocks(int P) { return P == 1 ? 8 : (P == 2 ? 6 : 3); }
 
-template <int P, int MODE>
+// KC > 0: the cluster values come from the by-value table tab (K <= KC);
+// KC == 0: from the device tables of c.
+template <int KC>
+using TabOf = ParamTab<KC == 0 ? 1 : KC>;
+
+template <int P, int MODE, int KC>
 __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
     const float4 *__restrict__ jd, const float4 *__restrict__ jl,
     const float *__restrict__ xh, const float *__restrict__ yh, const float *__restrict__ zh,
     const float *__restrict__ xl, const float *__restrict__ yl, const float *__restrict__ zl,
-    Clusters c, Decomp d, double G, double *__restrict__ part, int64_t cap)
+    Clusters c, const __grid_constant__ TabOf<KC> tab, Decomp d, double G,
+    double *__restrict__ part, int64_t cap)
 {
     constexpr int I = 2 * P;
     constexpr bool FULL = (MODE == PM_DS_FULL);
@@ -192,10 +242,10 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
 
     while (u < uend) {
-        const Segment sg = segment_at(d, c, g, u, uend);
+        const Segment sg = KC > 0 ? segment_at(d, tab, g, u, uend) : segment_at(d, c, g, u, uend);
         const int n = sg.nk;
         const int64_t base = sg.base;
-        const float eps2 = c.eps2f[sg.k];
+        const float eps2 = KC > 0 ? tab.eps2f[sg.k] : c.eps2f[sg.k];
         const bool mask_self = d.mask_self != 0;
         const int ib0 = sg.b * d.ipb;
         const int ibase = ib0 + tid;
@@ -388,22 +438,52 @@ __global__ void __launch_bounds__(TILE) pair_fp64_kernel(
 
 // ---- variant table -----------------------------------------------------------
 
-typedef void (*sp_kernel_t)(const float4 *, const float4 *, const float *, const float *,
-                            const float *, const float *, const float *, const float *,
-                            Clusters, Decomp, double, double *, int64_t);
+template <int KC>
+using sp_kernel_t = void (*)(const float4 *, const float4 *, const float *, const float *,
+                             const float *, const float *, const float *, const float *,
+                             Clusters, TabOf<KC>, Decomp, double, double *, int64_t);
 typedef void (*dp_kernel_t)(const double *, const double *, const double *, const double *,
                             Clusters, Decomp, double, double *, int64_t);
 
 // I (bodies per thread) = 2P for the single-precision family.
-static sp_kernel_t sp_variant(int mode, int I)
+template <int KC>
+static sp_kernel_t<KC> sp_variant(int mode, int I)
 {
 #define NB_SP(M, II) \
-    if (mode == M && I == II) return pair_sp_kernel<II / 2, M>;
+    if (mode == M && I == II) return pair_sp_kernel<II / 2, M, KC>;
     NB_SP(PM_DS_NEAR, 2) NB_SP(PM_DS_NEAR, 4) NB_SP(PM_DS_NEAR, 8)
     NB_SP(PM_DS_FULL, 2) NB_SP(PM_DS_FULL, 4)
     NB_SP(PM_FP32, 2) NB_SP(PM_FP32, 4) NB_SP(PM_FP32, 8)
 #undef NB_SP
     return nullptr;
+}
+
+// The parameter-table width used for a set of K clusters.
+static int kc_for(int32_t K) { return K == 1 ? 1 : (K <= PARAM_CLUSTERS ? PARAM_CLUSTERS : 0); }
+
+template <int KC>
+static cudaError_t launch_sp(const DevState &s, const PairLaunch &pl, const HostTab &ht,
+                             double G, cudaStream_t st)
+{
+    sp_kernel_t<KC> k = sp_variant<KC>(pl.mode, pl.I);
+    if (!k) return cudaErrorInvalidValue;
+    TabOf<KC> t;
+    std::memset(&t, 0, sizeof t);
+    if (KC > 0) {
+        if (ht.K > KC) return cudaErrorInvalidValue;
+        t.K = ht.K;
+        for (int32_t q = 0; q < ht.K; ++q) {
+            t.uoff[q] = ht.uoff[q];
+            t.boff[q] = ht.boff[q];
+            t.nk[q] = (int32_t)ht.nk[q];
+            t.ntiles[q] = ht.ntiles[q];
+            t.eps2f[q] = ht.eps2f[q];
+        }
+        t.uoff[ht.K] = ht.uoff[ht.K];
+    }
+    k<<<(unsigned)pl.d.G, TILE, 0, st>>>(s.jd, s.jl, s.xh, s.yh, s.zh, s.xl, s.yl, s.zl, s.cl, t,
+                                         pl.d, G, s.part, s.cap);
+    return cudaGetLastError();
 }
 
 static dp_kernel_t dp_variant(int I)
@@ -416,35 +496,45 @@ static dp_kernel_t dp_variant(int I)
 bool pair_variant_exists(int mode, int I)
 {
     if (mode == PM_FP64) return dp_variant(I) != nullptr;
-    return sp_variant(mode, I) != nullptr;
+    return sp_variant<1>(mode, I) != nullptr;
 }
 
 int pair_occupancy(int mode, int I)
 {
     int nb = 0;
     cudaError_t e;
-    if (mode == PM_FP64)
+    if (mode == PM_FP64) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, dp_variant(I), TILE, 0);
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sp_variant(mode, I), TILE, 0);
+    } else {
+        // the narrowest over the parameter-table widths
+        int a = 0, b = 0, c = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, sp_variant<1>(mode, I), TILE, 0);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &b, sp_variant<PARAM_CLUSTERS>(mode, I), TILE, 0);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, sp_variant<0>(mode, I), TILE, 0);
+        nb = a < b ? a : b;
+        nb = nb < c ? nb : c;
+    }
     if (e != cudaSuccess) return 0;
     return nb;
 }
 
-cudaError_t launch_pair(const DevState &s, const PairLaunch &pl, double G, cudaStream_t st)
+cudaError_t launch_pair(const DevState &s, const PairLaunch &pl, const HostTab &ht, double G,
+                        cudaStream_t st)
 {
-    const dim3 grid((unsigned)pl.d.G), block(TILE);
     if (pl.mode == PM_FP64) {
         dp_kernel_t k = dp_variant(pl.I);
         if (!k) return cudaErrorInvalidValue;
-        k<<<grid, block, 0, st>>>(s.x, s.y, s.z, s.m, s.cl, pl.d, G, s.part, s.cap);
-    } else {
-        sp_kernel_t k = sp_variant(pl.mode, pl.I);
-        if (!k) return cudaErrorInvalidValue;
-        k<<<grid, block, 0, st>>>(s.jd, s.jl, s.xh, s.yh, s.zh, s.xl, s.yl, s.zl, s.cl, pl.d, G,
-                                  s.part, s.cap);
+        k<<<(unsigned)pl.d.G, TILE, 0, st>>>(s.x, s.y, s.z, s.m, s.cl, pl.d, G, s.part, s.cap);
+        return cudaGetLastError();
     }
-    return cudaGetLastError();
+    switch (kc_for(ht.K)) {
+    case 1: return launch_sp<1>(s, pl, ht, G, st);
+    case PARAM_CLUSTERS: return launch_sp<PARAM_CLUSTERS>(s, pl, ht, G, st);
+    default: return launch_sp<0>(s, pl, ht, G, st);
+    }
 }
 
 cudaError_t launch_potential(const DevState &s, const Decomp &d, cudaStream_t st)
