@@ -258,6 +258,98 @@ int nb_accel_static(const nb_params *p, int64_t n, const double *d_pos,
 /* Release the context and all its device memory.  NULL-safe. */
 void nb_destroy(nb_ctx *ctx);
 
+/* ---- Serving loop ----------------------------------------------------------
+ * Integration jobs of different N, order and precision share one GPU.  The
+ * paper runs one simulation per program; this is a request loop around the
+ * same step (Sect. 3.1).  A scheduler thread admits queued jobs in arrival
+ * order when a resident-job slot is free and the state pool (sized from the
+ * HBM budget) has a contiguous range for the job's bodies.  Resident jobs are
+ * grouped by (precision, order); each group advances one step at a time with
+ * one persistent launch per force evaluation covering all its jobs, on its
+ * own stream, so groups overlap on the device.  Jobs join and leave a group
+ * between two of its steps (continuous batching).  Each job is an independent
+ * system (eq. 3) with its own softening and step; the field parameters are
+ * the server's.  All calls are thread-safe. */
+typedef struct nb_server nb_server;
+
+typedef struct {
+    int device;
+    double hbm_budget_bytes;  /* device memory for resident state (> 0);
+                                 about 460 bytes per body slot */
+    int max_jobs;             /* resident jobs at most, 1..65536 */
+    double G;                 /* as nb_params */
+    int ext_on;
+    double Md, ad, bd, Mb, ab;
+    double near_frac;         /* as nb_params (NB_DS jobs) */
+} nb_server_params;
+
+typedef struct {
+    int64_t n;        /* bodies, 1 <= n <= pool capacity */
+    int order;        /* 2 or 6 */
+    int precision;    /* NB_FP64 or NB_DS */
+    double dt;        /* step length > 0 */
+    int64_t nsteps;   /* >= 1 */
+    double eps;       /* softening >= 0 */
+} nb_job_desc;
+
+enum nb_job_state { NB_JOB_QUEUED = 0, NB_JOB_RUNNING = 1, NB_JOB_DONE = 2,
+                    NB_JOB_FAILED = 3, NB_JOB_CANCELLED = 4 };
+
+typedef struct {
+    int state;            /* enum nb_job_state */
+    int64_t steps_done;
+    double t_submit;      /* server clock, seconds since nb_server_create */
+    double t_admit;       /* 0 while queued */
+    double t_done;        /* 0 until finished; latency = t_done - t_submit */
+} nb_job_status;
+
+typedef struct {
+    int64_t submitted, admitted, completed, failed, cancelled, queued, running;
+    double interactions;      /* pair interactions evaluated (N^2 per evaluation) */
+    int64_t kernel_launches;  /* kernels the scheduler enqueued */
+    int64_t capacity_bodies;  /* pool capacity from the budget */
+    double clock_s;           /* server clock now */
+} nb_server_stats_t;
+
+/* Defaults: device 0, 4 GB budget, 64 jobs, G = 1, field off with the disk +
+ * bulge constants of nb_params_default.  NULL-safe. */
+void nb_server_params_default(nb_server_params *p);
+
+/* Allocate the pool and start the scheduler thread.  Errors: NB_EINVAL,
+ * NB_ENOMEM, NB_ECUDA. */
+int nb_server_create(const nb_server_params *p, nb_server **out);
+
+/* Queue a job; host arrays (n rows of positions and velocities, n masses) are
+ * copied before the call returns.  *job_id receives the job's id.  Errors:
+ * NB_EINVAL (bad descriptor or NULL), NB_ECUDA (server stopped). */
+int nb_server_submit(nb_server *s, const nb_job_desc *d, const double *pos,
+                     const double *vel, const double *mass, int64_t *job_id);
+
+/* Current status of a job.  Errors: NB_EINVAL (unknown id). */
+int nb_server_poll(nb_server *s, int64_t job_id, nb_job_status *st);
+
+/* Block until the job is done, failed or cancelled, or timeout_s elapses
+ * (NB_ETIMEOUT; *st then holds the current status). */
+int nb_server_wait(nb_server *s, int64_t job_id, double timeout_s, nb_job_status *st);
+
+/* Final positions and velocities of a done job (n rows each; either pointer
+ * may be NULL).  Errors: NB_ESTATE (not done), NB_ENONFINITE (job failed),
+ * NB_EINVAL. */
+int nb_server_result(nb_server *s, int64_t job_id, double *pos, double *vel);
+
+/* Cancel a queued job, or a running one at its group's next step boundary. */
+int nb_server_cancel(nb_server *s, int64_t job_id);
+
+/* Drop a finished job's record and result.  Errors: NB_ESTATE if running. */
+int nb_server_forget(nb_server *s, int64_t job_id);
+
+/* Counters since creation. */
+int nb_server_stats(nb_server *s, nb_server_stats_t *out);
+
+/* Stop the scheduler (queued and running jobs are abandoned) and free
+ * everything.  NULL-safe. */
+void nb_server_destroy(nb_server *s);
+
 #ifdef __cplusplus
 }
 #endif

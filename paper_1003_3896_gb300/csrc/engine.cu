@@ -44,7 +44,6 @@ int pool_create(Pool &P, int device, int64_t cap)
     int64_t slots = 2 + (gmax * 512 + cap - 1) / cap;
     if (slots > 24) slots = 24;
     s.part_slots = slots;
-    s.ng_hcap = near_table_size(cap);
     s.red_len = 0;
     bool ok = true;
     auto A = [&](void **q, size_t bytes) {
@@ -62,13 +61,6 @@ int pool_create(Pool &P, int device, int64_t cap)
     A((void **)&s.jl, 2 * (size_t)cap * sizeof(float4));
     A((void **)&s.part, (size_t)s.part_slots * 3 * c8);
     A((void **)&s.corr, 3 * c8);
-    A((void **)&s.ng_key, c8);
-    A((void **)&s.ng_bucket, c4);
-    A((void **)&s.ng_entry, c4);
-    A((void **)&s.ng_count, (size_t)s.ng_hcap * 4);
-    A((void **)&s.ng_start, (size_t)(s.ng_hcap + 1) * 4);
-    A((void **)&s.ng_bsum, (size_t)(s.ng_hcap / 1024 + 1) * 4);
-    A((void **)&s.flag, sizeof(int));
     A((void **)&P.stage, 7 * c8);
     if (!ok) {
         cudaGetLastError();
@@ -82,9 +74,8 @@ int pool_create(Pool &P, int device, int64_t cap)
 void pool_destroy(Pool &P)
 {
     DevState &s = P.s;
-    void *ptrs[] = {s.x, s.y, s.z, s.vx, s.vy, s.vz, s.m, s.xh, s.yh, s.zh, s.mf, s.xl,
-                    s.yl, s.zl, s.jd, s.jl, s.part, s.corr, s.ng_key, s.ng_bucket,
-                    s.ng_entry, s.ng_count, s.ng_start, s.ng_bsum, s.flag, P.stage};
+    void *ptrs[] = {s.x,  s.y,  s.z,  s.vx, s.vy, s.vz, s.m,    s.xh,    s.yh,
+                    s.zh, s.mf, s.xl, s.yl, s.zl, s.jd, s.jl, s.part, s.corr, P.stage};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     s = DevState();
@@ -112,10 +103,27 @@ int set_create(ClusterSet &C, int32_t kcap, int64_t body_cap)
         C.dmem = nullptr;
         return set_error(NB_ENOMEM, "cluster tables: device allocation failed");
     }
-    // reduction partials: one row of 16 doubles per segment
-    if (cudaMalloc(&C.red, (size_t)C.scap * 16 * 8) != cudaSuccess) {
+    // reduction partials (one row of 16 doubles per segment), the near-pair
+    // hash grid and the non-finite flag
+    C.body_cap = body_cap;
+    C.ng_hcap = near_table_size(body_cap);
+    bool ok = true;
+    auto A = [&](void **q, size_t b) {
+        if (ok && cudaMalloc(q, b) != cudaSuccess) {
+            *q = nullptr;
+            ok = false;
+        }
+    };
+    A((void **)&C.red, (size_t)C.scap * 16 * 8);
+    A((void **)&C.ng_key, (size_t)body_cap * 8);
+    A((void **)&C.ng_bucket, (size_t)body_cap * 4);
+    A((void **)&C.ng_entry, (size_t)body_cap * 4);
+    A((void **)&C.ng_count, (size_t)C.ng_hcap * 4);
+    A((void **)&C.ng_start, (size_t)(C.ng_hcap + 1) * 4);
+    A((void **)&C.ng_bsum, (size_t)(C.ng_hcap / 1024 + 1) * 4);
+    A((void **)&C.flag, sizeof(int));
+    if (!ok) {
         cudaGetLastError();
-        C.red = nullptr;
         set_destroy(C);
         return set_error(NB_ENOMEM, "cluster tables: device allocation failed");
     }
@@ -125,8 +133,10 @@ int set_create(ClusterSet &C, int32_t kcap, int64_t body_cap)
 
 void set_destroy(ClusterSet &C)
 {
-    if (C.dmem) cudaFree(C.dmem);
-    if (C.red) cudaFree(C.red);
+    void *ptrs[] = {C.dmem,      C.red,      C.ng_key,   C.ng_bucket, C.ng_entry,
+                    C.ng_count,  C.ng_start, C.ng_bsum,  C.flag};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
     C = ClusterSet();
 }
 
@@ -311,6 +321,14 @@ DevState view(const Pool &P, const ClusterSet &C, int precision)
     s.diag = C.diag;
     s.red = C.red;
     s.red_len = C.scap * 16;
+    s.ng_key = C.ng_key;
+    s.ng_bucket = C.ng_bucket;
+    s.ng_entry = C.ng_entry;
+    s.ng_count = C.ng_count;
+    s.ng_start = C.ng_start;
+    s.ng_bsum = C.ng_bsum;
+    s.ng_hcap = C.ng_hcap;
+    s.flag = C.flag;
     if (precision != NB_DS) s.corr = nullptr;
     return s;
 }

@@ -48,6 +48,12 @@ struct ClusterSet {
     std::vector<double> eps, eps2d, dts;
     char *dmem = nullptr;      // device copy of the tables
     double *red = nullptr;     // reduction partials [scap][16]
+    // per-set scratch, so sets in one pool can run concurrently on different
+    // streams: near-pair hash grid over the set's linear bodies and the flag
+    int64_t body_cap = 0, ng_hcap = 0;
+    uint64_t *ng_key = nullptr;
+    int *ng_bucket = nullptr, *ng_entry = nullptr, *ng_count = nullptr, *ng_start = nullptr,
+        *ng_bsum = nullptr, *flag = nullptr;
     Frame *frame = nullptr;    // [kcap]
     double *diag = nullptr;    // [kcap][DIAG_STRIDE]
     Clusters cl, cl_pot;       // device views (pair units / potential units)

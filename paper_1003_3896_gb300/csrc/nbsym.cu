@@ -197,7 +197,7 @@ int get_graph(nb_ctx *c, int order, double h, StepGraph **out)
 int check_flag(nb_ctx *c, const char *what)
 {
     int h = 0;
-    NB_TRY(cudaMemcpyAsync(&h, c->pool.s.flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    NB_TRY(cudaMemcpyAsync(&h, c->set.flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     NB_TRY(cudaStreamSynchronize(c->stream));
     if (h) return set_error(NB_ENONFINITE, "%s: non-finite values (coincident bodies with eps = 0?)", what);
     return NB_OK;
@@ -386,7 +386,7 @@ static int accel_common(nb_ctx *c, double *out, bool host)
     rc = enq_force(c->pool, c->set, c->plan, c->phys, c->stream, nullptr,
                    c->prof_on ? c->pe1 : nullptr, &k);
     if (rc) return rc;
-    NB_TRY(cudaMemsetAsync(c->pool.s.flag, 0, sizeof(int), c->stream));
+    NB_TRY(cudaMemsetAsync(c->set.flag, 0, sizeof(int), c->stream));
     double *dst = host ? c->pool.stage : out;
     rc = enq_accel_out(c->pool, c->set, c->plan, c->phys, dst, c->stream, &k);
     if (rc) return rc;
@@ -446,7 +446,7 @@ static int energy_common(nb_ctx *c, std::vector<double> &d)
 {
     if (c->n == 0) return set_error(NB_ESTATE, "nb_energy before nb_load");
     DeviceGuard dg(c->p.device);
-    NB_TRY(cudaMemsetAsync(c->pool.s.flag, 0, sizeof(int), c->stream));
+    NB_TRY(cudaMemsetAsync(c->set.flag, 0, sizeof(int), c->stream));
     int64_t k = 0;
     int rc = enq_energy(c->pool, c->set, c->plan, c->phys, c->stream, &k);
     if (rc) return rc;

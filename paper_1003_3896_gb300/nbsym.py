@@ -262,3 +262,125 @@ class Context:
         check(nb_prof_read(self._h, C.byref(p)))
         return {"pair_launches": p.pair_launches, "pair_ms": p.pair_ms,
                 "interactions": p.interactions, "kernel_launches": p.kernel_launches}
+
+
+# ---- serving loop --------------------------------------------------------------
+
+class ServerParams(C.Structure):
+    _fields_ = [("device", C.c_int), ("hbm_budget_bytes", C.c_double), ("max_jobs", C.c_int),
+                ("G", C.c_double), ("ext_on", C.c_int), ("Md", C.c_double), ("ad", C.c_double),
+                ("bd", C.c_double), ("Mb", C.c_double), ("ab", C.c_double),
+                ("near_frac", C.c_double)]
+
+
+class JobDesc(C.Structure):
+    _fields_ = [("n", C.c_int64), ("order", C.c_int), ("precision", C.c_int),
+                ("dt", C.c_double), ("nsteps", C.c_int64), ("eps", C.c_double)]
+
+
+class JobStatus(C.Structure):
+    _fields_ = [("state", C.c_int), ("steps_done", C.c_int64), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_done", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("failed", C.c_int64), ("cancelled", C.c_int64), ("queued", C.c_int64),
+                ("running", C.c_int64), ("interactions", C.c_double),
+                ("kernel_launches", C.c_int64), ("capacity_bodies", C.c_int64),
+                ("clock_s", C.c_double)]
+
+
+JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED, JOB_CANCELLED = 0, 1, 2, 3, 4
+_srvp = C.c_void_p
+nb_server_params_default = _sig("nb_server_params_default", None, C.POINTER(ServerParams))
+nb_server_create = _sig("nb_server_create", C.c_int, C.POINTER(ServerParams), C.POINTER(_srvp))
+nb_server_submit = _sig("nb_server_submit", C.c_int, _srvp, C.POINTER(JobDesc), _dp, _dp, _dp,
+                        C.POINTER(C.c_int64))
+nb_server_poll = _sig("nb_server_poll", C.c_int, _srvp, C.c_int64, C.POINTER(JobStatus))
+nb_server_wait = _sig("nb_server_wait", C.c_int, _srvp, C.c_int64, C.c_double,
+                      C.POINTER(JobStatus))
+nb_server_result = _sig("nb_server_result", C.c_int, _srvp, C.c_int64, _dp, _dp)
+nb_server_cancel = _sig("nb_server_cancel", C.c_int, _srvp, C.c_int64)
+nb_server_forget = _sig("nb_server_forget", C.c_int, _srvp, C.c_int64)
+nb_server_stats = _sig("nb_server_stats", C.c_int, _srvp, C.POINTER(ServerStats))
+nb_server_destroy = _sig("nb_server_destroy", None, _srvp)
+
+
+def _status(st: JobStatus) -> dict:
+    return {"state": st.state, "steps_done": st.steps_done, "t_submit": st.t_submit,
+            "t_admit": st.t_admit, "t_done": st.t_done}
+
+
+class Server:
+    """Continuous-batching request loop (``nb_server``)."""
+
+    def __init__(self, hbm_budget_bytes: float = 4e9, max_jobs: int = 64, device: int = 0,
+                 G: float = 1.0, ext_on: bool = False, near_frac: float = 0.0, **field):
+        p = ServerParams()
+        nb_server_params_default(C.byref(p))
+        p.device, p.hbm_budget_bytes, p.max_jobs = device, hbm_budget_bytes, max_jobs
+        p.G, p.ext_on, p.near_frac = G, int(bool(ext_on)), near_frac
+        for k, v in field.items():
+            setattr(p, k, v)
+        h = _srvp()
+        check(nb_server_create(C.byref(p), C.byref(h)))
+        self._h = h
+        self._n = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            nb_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, pos, vel, mass, order: int, dt: float, nsteps: int,
+               precision: int | str = NB_DS, eps: float = 0.0) -> int:
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        mass = np.ascontiguousarray(mass, dtype=np.float64).ravel()
+        n = mass.size
+        pos = _host3(pos, n)
+        vel = _host3(vel, n)
+        d = JobDesc(n, int(order), int(precision), float(dt), int(nsteps), float(eps))
+        jid = C.c_int64()
+        check(nb_server_submit(self._h, C.byref(d), _p(pos), _p(vel), _p(mass), C.byref(jid)))
+        self._n[jid.value] = n
+        return jid.value
+
+    def poll(self, job_id: int) -> dict:
+        st = JobStatus()
+        check(nb_server_poll(self._h, int(job_id), C.byref(st)))
+        return _status(st)
+
+    def wait(self, job_id: int, timeout_s: float = 600.0) -> dict:
+        st = JobStatus()
+        check(nb_server_wait(self._h, int(job_id), float(timeout_s), C.byref(st)))
+        return _status(st)
+
+    def result(self, job_id: int):
+        n = self._n[job_id]
+        pos = np.empty((n, 3))
+        vel = np.empty((n, 3))
+        check(nb_server_result(self._h, int(job_id), _p(pos), _p(vel)))
+        return pos, vel
+
+    def cancel(self, job_id: int):
+        check(nb_server_cancel(self._h, int(job_id)))
+
+    def forget(self, job_id: int):
+        check(nb_server_forget(self._h, int(job_id)))
+        self._n.pop(job_id, None)
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        check(nb_server_stats(self._h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}

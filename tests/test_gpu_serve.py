@@ -1,0 +1,132 @@
+"""Serving loop: jobs of different size, order and precision admitted by
+budget and slots, batched while others run, each result the same alone and
+in the mix (within the parity tolerances), failures isolated to their job."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1003_3896_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nbs():
+    from paper_1003_3896_gb300 import build
+    build.build()
+    from paper_1003_3896_gb300 import nbsym
+    return nbsym
+
+
+JOBS = [  # n, order, precision, dt, nsteps
+    (1500, 6, "ds", 1 / 512, 5),
+    (3000, 2, "fp64", 1 / 1024, 9),
+    (700, 2, "ds", 1 / 256, 12),
+    (2200, 6, "fp64", 1 / 512, 3),
+    (5000, 6, "ds", 1 / 512, 4),
+    (400, 6, "ds", 1 / 128, 7),
+]
+
+
+def ic(n, seed):
+    pos, vel, m = ics.henon_plummer(n, seed)
+    return pos, vel, m, ics.paper_softening(n)
+
+
+def test_each_result_same_alone_and_in_mix(nbs):
+    with nbs.Server(hbm_budget_bytes=2e9, max_jobs=16) as srv:
+        ids = []
+        for k, (n, order, prec, dt, steps) in enumerate(JOBS):
+            pos, vel, m, eps = ic(n, 500 + k)
+            ids.append(srv.submit(pos, vel, m, order, dt, steps, precision=prec, eps=eps))
+        st = [srv.wait(j, 300) for j in ids]
+        assert all(s["state"] == nbs.JOB_DONE for s in st), st
+        # work overlapped: some job was admitted before another finished
+        overlap = any(a["t_admit"] < b["t_done"] and b["t_admit"] < a["t_done"]
+                      for i, a in enumerate(st) for b in st[i + 1:])
+        assert overlap
+        stats = srv.stats()
+        assert stats["completed"] == len(JOBS) and stats["interactions"] > 0
+        results = [srv.result(j) for j in ids]
+    for k, ((n, order, prec, dt, steps), (x, v)) in enumerate(zip(JOBS, results)):
+        pos, vel, m, eps = ic(n, 500 + k)
+        with nbs.Context(n, eps=eps, precision=prec) as c:
+            c.load(pos, vel, m)
+            c.step(order, dt, steps)
+            xa, va = c.get_state()
+        tol = 1e-12 if prec == "fp64" else 1e-8
+        assert np.abs(x - xa).max() <= tol, (k, np.abs(x - xa).max())
+        assert np.abs(v - va).max() <= 10 * tol
+
+
+def test_admission_respects_budget_and_slots(nbs):
+    """A budget for about two 1000-body jobs: never more than two resident,
+    every job still completes in arrival order of admission."""
+    with nbs.Server(hbm_budget_bytes=2200 * 460.0, max_jobs=8) as srv:
+        cap = srv.stats()["capacity_bodies"]
+        assert 2000 <= cap < 3000
+        ids = []
+        for k in range(5):
+            pos, vel, m, eps = ic(1000, 600 + k)
+            ids.append(srv.submit(pos, vel, m, 6, 1 / 512, 6, precision="ds", eps=eps))
+        st = [srv.wait(j, 300) for j in ids]
+    assert all(s["state"] == nbs.JOB_DONE for s in st)
+    events = sorted([(s["t_admit"], +1) for s in st] + [(s["t_done"], -1) for s in st])
+    live = peak = 0
+    for _, d in events:
+        live += d
+        peak = max(peak, live)
+    assert peak <= 2
+    admits = [s["t_admit"] for s in st]
+    assert admits == sorted(admits)
+
+
+def test_slot_limit_and_cancel(nbs):
+    with nbs.Server(hbm_budget_bytes=1e9, max_jobs=1) as srv:
+        pos, vel, m, eps = ic(4000, 700)
+        long_job = srv.submit(pos, vel, m, 6, 1 / 512, 400, precision="fp64", eps=eps)
+        p2, v2, m2, e2 = ic(500, 701)
+        queued = srv.submit(p2, v2, m2, 2, 1 / 512, 5, precision="ds", eps=e2)
+        time.sleep(0.05)
+        assert srv.poll(queued)["state"] == nbs.JOB_QUEUED
+        srv.cancel(queued)
+        srv.cancel(long_job)
+        assert srv.wait(queued, 60)["state"] == nbs.JOB_CANCELLED
+        assert srv.wait(long_job, 120)["state"] == nbs.JOB_CANCELLED
+        with pytest.raises(nbs.NBError) as e:
+            srv.result(long_job)
+        assert e.value.code == nbs.NB_ESTATE
+        srv.forget(queued)
+
+
+def test_failure_is_isolated(nbs):
+    """A job with coincident bodies and eps = 0 goes non-finite and fails; a
+    job in the same group finishes normally."""
+    with nbs.Server(hbm_budget_bytes=1e9, max_jobs=8) as srv:
+        bad = np.zeros((3, 3))
+        bad[2, 0] = 1.0
+        jb = srv.submit(bad, np.zeros((3, 3)), np.ones(3), 2, 1 / 64, 3, precision="ds", eps=0.0)
+        pos, vel, m, eps = ic(900, 800)
+        jg = srv.submit(pos, vel, m, 2, 1 / 512, 3, precision="ds", eps=eps)
+        assert srv.wait(jb, 60)["state"] == nbs.JOB_FAILED
+        assert srv.wait(jg, 60)["state"] == nbs.JOB_DONE
+        with pytest.raises(nbs.NBError) as e:
+            srv.result(jb)
+        assert e.value.code == nbs.NB_ENONFINITE
+        x, _ = srv.result(jg)
+        assert np.isfinite(x).all()
+
+
+def test_bad_jobs_rejected(nbs):
+    with nbs.Server(hbm_budget_bytes=100 * 460.0, max_jobs=2) as srv:
+        pos, vel, m, eps = ic(50, 900)
+        for kw in [dict(order=3), dict(dt=0.0), dict(nsteps=0), dict(precision="fp32")]:
+            args = dict(order=2, dt=0.01, nsteps=1, precision="ds", eps=eps)
+            args.update(kw)
+            with pytest.raises(nbs.NBError) as e:
+                srv.submit(pos, vel, m, **args)
+            assert e.value.code == nbs.NB_EINVAL
+        p2, v2, m2, _ = ic(500, 901)
+        with pytest.raises(nbs.NBError):
+            srv.submit(p2, v2, m2, 2, 0.01, 1)
