@@ -183,7 +183,15 @@ def main():
     ap.add_argument("--near-frac", type=float, default=0.0,
                     help="mixed mode near-pair radius in units of R_rms / N^(1/3) (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5"],
+                    help="c2 (default): the headline line; the others print their own "
+                         "labelled lines (see bench_workloads.py)")
+    ap.add_argument("--jobs", type=int, default=48, help="c5: jobs in the bounded trace")
+    ap.add_argument("--steps-cap", type=int, default=20, help="c5: cap on steps per job")
     args = ap.parse_args()
+    if args.workload != "c2":
+        import bench_workloads
+        return bench_workloads.run(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
