@@ -122,6 +122,7 @@ int set_create(ClusterSet &C, int32_t kcap, int64_t body_cap)
     A((void **)&C.ng_start, (size_t)(C.ng_hcap + 1) * 4);
     A((void **)&C.ng_bsum, (size_t)(C.ng_hcap / 1024 + 1) * 4);
     A((void **)&C.flag, sizeof(int));
+    A((void **)&C.cid, (size_t)body_cap * 4);
     if (!ok) {
         cudaGetLastError();
         set_destroy(C);
@@ -133,8 +134,8 @@ int set_create(ClusterSet &C, int32_t kcap, int64_t body_cap)
 
 void set_destroy(ClusterSet &C)
 {
-    void *ptrs[] = {C.dmem,      C.red,      C.ng_key,   C.ng_bucket, C.ng_entry,
-                    C.ng_count,  C.ng_start, C.ng_bsum,  C.flag};
+    void *ptrs[] = {C.dmem,     C.red,      C.ng_key,  C.ng_bucket, C.ng_entry,
+                    C.ng_count, C.ng_start, C.ng_bsum, C.flag,      C.cid};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     C = ClusterSet();
@@ -234,9 +235,6 @@ int set_layout(ClusterSet &C, int ipb, cudaStream_t st)
     NB_TRY(up(d_seglo, C.seg_lo.data(), S * 8));
     NB_TRY(up(d_seghi, C.seg_hi.data(), S * 8));
     NB_TRY(up(d_segoff, C.seg_off.data(), (K + 1) * 4));
-    // pageable copies are staged before returning; make the tables visible
-    // to kernels launched on other streams too
-    NB_TRY(cudaStreamSynchronize(st));
     Clusters &c = C.cl;
     c.K = K;
     c.boff = d_boff;
@@ -253,6 +251,11 @@ int set_layout(ClusterSet &C, int ipb, cudaStream_t st)
     c.seg_lo = d_seglo;
     c.seg_hi = d_seghi;
     c.seg_off = d_segoff;
+    c.cid = C.cid;
+    if (K > 1) NB_TRY(launch_cluster_map(c, C.cid, C.n, st));
+    // pageable copies are staged before returning; make the tables visible
+    // to kernels launched on other streams too
+    NB_TRY(cudaStreamSynchronize(st));
     C.cl_pot = c;
     C.cl_pot.uoff = d_uoffp;
     return NB_OK;

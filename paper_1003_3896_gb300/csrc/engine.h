@@ -54,6 +54,7 @@ struct ClusterSet {
     uint64_t *ng_key = nullptr;
     int *ng_bucket = nullptr, *ng_entry = nullptr, *ng_count = nullptr, *ng_start = nullptr,
         *ng_bsum = nullptr, *flag = nullptr;
+    int32_t *cid = nullptr;    // linear body -> cluster map
     Frame *frame = nullptr;    // [kcap]
     double *diag = nullptr;    // [kcap][DIAG_STRIDE]
     Clusters cl, cl_pot;       // device views (pair units / potential units)

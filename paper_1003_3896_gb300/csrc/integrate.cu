@@ -6,7 +6,8 @@
 // the round-off sensitive part).
 //
 // Per-body kernels run over linear body indices t (cluster after cluster);
-// find_cluster maps t to its cluster k and pool slot boff[k] + t - noff[k].
+// the set's body -> cluster map gives t's cluster k, and its pool slot is
+// boff[k] + t - noff[k].
 // Reductions run per segment (a run of one cluster's bodies), then one block
 // per cluster adds its segments in a fixed tree order.
 #include "nb_internal.cuh"
@@ -27,7 +28,7 @@ struct BodyRef {
 __device__ __forceinline__ BodyRef body_at(const Clusters &c, int64_t t)
 {
     BodyRef r;
-    r.k = find_cluster(c.noff, c.K, t);
+    r.k = cluster_of(c, t);
     r.li = t - c.noff[r.k];
     r.gi = c.boff[r.k] + r.li;
     return r;
@@ -122,6 +123,20 @@ __global__ void pack_kernel(DevState s, double *__restrict__ pos, double *__rest
         vel[3 * t + 1] = s.vy[i];
         vel[3 * t + 2] = s.vz[i];
     }
+}
+
+// cid[t] = cluster of linear body t (binary search once per layout).
+__global__ void cluster_map_kernel(Clusters c, int32_t *cid, int64_t n)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n) cid[t] = find_cluster(c.noff, c.K, t);
+}
+
+cudaError_t launch_cluster_map(const Clusters &c, int32_t *cid, int64_t n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    cluster_map_kernel<<<blocks_for(n, OT), OT, 0, st>>>(c, cid, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_unpack(const DevState &s, const double *pos, const double *vel,

@@ -47,7 +47,14 @@ struct Clusters {
     const int64_t *seg_lo = nullptr; // [S]   linear body range [lo, hi)
     const int64_t *seg_hi = nullptr;
     const int32_t *seg_off = nullptr;// [K+1] segments of cluster k: [seg_off[k], seg_off[k+1])
+    const int32_t *cid = nullptr;    // [noff[K]] cluster of each linear body (K > 1)
 };
+
+// Cluster of linear body t: one load from the precomputed map (K = 1: 0).
+__device__ __forceinline__ int32_t cluster_of(const Clusters &c, int64_t t)
+{
+    return c.K == 1 ? 0 : c.cid[t];
+}
 
 // largest k in [0, K) with off[k] <= t (off[0] = 0 <= t < off[K])
 __host__ __device__ __forceinline__ int32_t find_cluster(const int64_t *off, int32_t K, int64_t t)
@@ -176,6 +183,8 @@ int64_t near_table_size(int64_t n);
 cudaError_t launch_near_correct(const DevState &s, double G, cudaStream_t st);
 
 // ---- launchers (integrate.cu) ----------------------------------------------
+// Fill the body -> cluster map cid[0, n) of a cluster set.
+cudaError_t launch_cluster_map(const Clusters &c, int32_t *cid, int64_t n, cudaStream_t st);
 // Interleaved (linear body, 3) arrays <-> pool planes.
 cudaError_t launch_unpack(const DevState &s, const double *pos, const double *vel,
                           const double *mass, cudaStream_t st);

@@ -65,7 +65,7 @@ __global__ void near_cell_kernel(DevState s, uint32_t mask)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= s.n) return;
-    const int32_t k = find_cluster(s.cl.noff, s.cl.K, t);
+    const int32_t k = cluster_of(s.cl, t);
     const int64_t i = s.cl.boff[k] + t - s.cl.noff[k];
     const float ih = inv_cell(s.cl.frame[k]);
     const int cx = cell_coord(s.xh[i], ih), cy = cell_coord(s.yh[i], ih),
@@ -170,7 +170,7 @@ __global__ void near_correct_kernel(DevState s, uint32_t mask, double G)
     const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (t >= s.n) return;   // whole warps exit together
-    const int32_t k = find_cluster(s.cl.noff, s.cl.K, t);
+    const int32_t k = cluster_of(s.cl, t);
     const int64_t base = s.cl.boff[k] - s.cl.noff[k];
     const int64_t i = base + t;
     const Frame f = s.cl.frame[k];
