@@ -67,6 +67,13 @@ __host__ __device__ __forceinline__ int32_t find_cluster(const int64_t *off, int
     return lo;
 }
 
+// Slot of the near-pair cell table: cell key (all ones: empty) and the
+// cell's range [start, end) in the cell-ordered body copies.
+struct __align__(16) NgSlot {
+    unsigned long long key;
+    int start, end;
+};
+
 // Device state pool.  FP64 structure-of-arrays planes are the state; float
 // planes are derived copies for the single-precision paths.  All indexed by
 // pool slot.
@@ -87,10 +94,16 @@ struct DevState {
     // near-pair correction of the mixed mode (nullptr corr: not applied)
     double *corr = nullptr;     // [3][cap]
     uint64_t *ng_key = nullptr; // cell key per linear body
-    int *ng_bucket = nullptr, *ng_entry = nullptr;   // per linear body
-    int *ng_count = nullptr, *ng_start = nullptr;    // per bucket (start: H + 1)
+    // per linear body: table slot of its cell, arrival rank in the cell, and
+    // (per cell-ordered position) the body index before ordering
+    int *ng_bucket = nullptr, *ng_rank = nullptr, *ng_entry = nullptr;
+    // compact copies per linear body (hi x, y, z, m) and (lo x, y, z, side
+    // bits), and the same in cell order (lo.w = linear index)
+    float4 *ng_pos = nullptr, *ng_lo = nullptr, *ng_spos = nullptr, *ng_slo = nullptr;
+    NgSlot *ng_slot = nullptr;                       // cell table [H]
+    int *ng_count = nullptr, *ng_start = nullptr;    // per slot (start: H + 1)
     int *ng_bsum = nullptr;                          // scan block totals
-    int64_t ng_hcap = 0;                             // buckets allocated
+    int64_t ng_hcap = 0;                             // slots allocated
     double *red = nullptr;      // reduction partials [segment][16]
     int64_t red_len = 0;
     double *diag = nullptr;     // [K][16] reduction results (energy, torque)
@@ -176,7 +189,7 @@ cudaError_t launch_pair(const DevState &s, const PairLaunch &pl, const HostTab &
 cudaError_t launch_potential(const DevState &s, const Decomp &d, cudaStream_t st);
 
 // ---- near-pair correction (near.cu) ----------------------------------------
-// Hash-table buckets used for n bodies (power of two >= 2n).
+// Cell-table slots used for n bodies (power of two >= 2n).
 int64_t near_table_size(int64_t n);
 // corr_i = G sum over pairs closer than the cluster's near radius of the
 // double-single minus the float contribution (written to s.corr).

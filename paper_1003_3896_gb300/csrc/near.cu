@@ -4,8 +4,8 @@
 // relative to the cluster's frame origin c (hi = fl(x - c)).  For pairs
 // closer than the near radius d_th the rounding of hi dominates the error of
 // the coordinate difference (Sect. 4.2's "delicate evaluation of coordinate
-// difference"), so this pass finds them with a spatial hash grid of cell size
-// d_th and adds, per body i,
+// difference"), so this pass finds them with a spatial grid and adds, per
+// body i,
 //     corr_i = G sum_{j near i, j != i} [ f(d_ij^ds) - f(d_ij^float) ]
 // where d^ds = (hi_j - hi_i) + (lo_j - lo_i) is the double-single difference
 // and f(d^float) is recomputed with exactly the operations of the pair
@@ -13,10 +13,21 @@
 // rounding of its running sum.  Cells carry the cluster index, so bodies of
 // different clusters never pair.
 //
-// Deterministic: bodies are counting-sorted into hash buckets, each bucket is
-// then sorted by linear body index, and every body visits its 27 neighbour
-// cells in a fixed lane order with a fixed shuffle-tree sum, so the FP64
-// correction sums do not depend on timing.
+// Grid: cubic cells of side h = CELL_SCALE d_th.  Since h > 2 d_th, the
+// d_th-ball around a body reaches, along each axis, only its own cell and the
+// neighbour on the side of the cell half the body sits in, so each body looks
+// at 2 x 2 x 2 cells.  The 10% margin in CELL_SCALE absorbs the float rounding
+// of x / h for every cell coordinate the key can hold.  Occupied cells live
+// in an open-addressing table (linear probing, at most one cell per two
+// slots) whose slot records carry the cell's range in a cell-ordered copy of
+// the bodies, so a probe costs one 16-byte load and never walks another
+// cell's bodies.  Near pairs are rare (a few tenths per body in a Plummer
+// sphere), so the pass is dominated by these probes.
+//
+// Deterministic: within a cell the bodies are ordered by linear index, and
+// every body visits its 8 cells in a fixed order, so the FP64 correction sums
+// do not depend on timing (which slot a cell lands in may vary; the sums do
+// not depend on it).
 #include "nb_internal.cuh"
 
 namespace nb {
@@ -30,13 +41,10 @@ __device__ __forceinline__ float near_rsqrt(float x)
 
 constexpr int CELL_BITS = 15;                 // per coordinate
 constexpr int CELL_OFF = 1 << (CELL_BITS - 1);
-
-__device__ __forceinline__ int cell_coord(float v, float inv_h)
-{
-    float c = floorf(v * inv_h);
-    c = fminf(fmaxf(c, -(float)(CELL_OFF - 2)), (float)(CELL_OFF - 2));
-    return (int)c;
-}
+constexpr int CELL_MAX = CELL_OFF - 2;        // |cell| <= CELL_MAX, neighbours <= CELL_OFF - 1
+constexpr float CELL_SCALE = 2.2f;            // h / d_th
+constexpr unsigned long long NG_EMPTY = ~0ull;
+constexpr int NO_GRID = 8;                    // side bits: body not in the grid (d_th = 0)
 
 __device__ __forceinline__ uint64_t cell_key(int32_t k, int cx, int cy, int cz)
 {
@@ -45,35 +53,56 @@ __device__ __forceinline__ uint64_t cell_key(int32_t k, int cx, int cy, int cz)
            ((uint64_t)(cy + CELL_OFF) << CELL_BITS) | (uint64_t)(cz + CELL_OFF);
 }
 
-__device__ __forceinline__ uint32_t cell_bucket(int32_t k, int cx, int cy, int cz,
-                                                uint32_t mask)
+// Multiplicative (Fibonacci) hash of the key: the middle bits of key * 2^64/phi.
+__device__ __forceinline__ uint32_t slot_of(uint64_t key, uint32_t mask)
 {
-    const uint32_t h = ((uint32_t)cx * 73856093u) ^ ((uint32_t)cy * 19349663u) ^
-                       ((uint32_t)cz * 83492791u) ^ ((uint32_t)k * 2654435761u);
-    return h & mask;
+    return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 32) & mask;
 }
 
-// Inverse cell size: cells 0.1% wider than the near radius, so two bodies
-// whose float separation is below d_th never land two cells apart after the
-// rounding of x / h.
-__device__ __forceinline__ float inv_cell(const Frame &f)
+// Cell coordinate of v (clamped to the key's range) and the side, -1 or +1,
+// of the neighbour its d_th-interval can reach.
+__device__ __forceinline__ int cell_coord(float v, float inv_h, int &side)
 {
-    return f.dth > 0.f ? 1.0f / (1.001f * f.dth) : 0.f;
+    const float q = v * inv_h;
+    const float f = floorf(q);
+    side = q - f < 0.5f ? -1 : 1;
+    return (int)fminf(fmaxf(f, -(float)CELL_MAX), (float)CELL_MAX);
 }
 
-__global__ void near_cell_kernel(DevState s, uint32_t mask)
+// Per body: compact float copies, the cell key, insertion of the cell into
+// the slot table and the body's rank among its cell's arrivals.
+__global__ void near_cell_kernel(DevState s, uint32_t mask, int64_t H)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= s.n) return;
     const int32_t k = cluster_of(s.cl, t);
     const int64_t i = s.cl.boff[k] + t - s.cl.noff[k];
-    const float ih = inv_cell(s.cl.frame[k]);
-    const int cx = cell_coord(s.xh[i], ih), cy = cell_coord(s.yh[i], ih),
-              cz = cell_coord(s.zh[i], ih);
-    s.ng_key[t] = cell_key(k, cx, cy, cz);
-    const uint32_t b = cell_bucket(k, cx, cy, cz, mask);
+    const float dth = s.cl.frame[k].dth;
+    const float x = s.xh[i], y = s.yh[i], z = s.zh[i];
+    s.ng_pos[t] = make_float4(x, y, z, s.mf[i]);
+    if (!(dth > 0.f)) {   // no pair can pass the test r^2 + eps^2 < eps^2
+        s.ng_key[t] = cell_key(k, 0, 0, 0);
+        s.ng_lo[t] = make_float4(s.xl[i], s.yl[i], s.zl[i], __int_as_float(NO_GRID));
+        s.ng_bucket[t] = -1;
+        return;
+    }
+    const float ih = 1.0f / (CELL_SCALE * dth);
+    int sx, sy, sz;
+    const int cx = cell_coord(x, ih, sx), cy = cell_coord(y, ih, sy), cz = cell_coord(z, ih, sz);
+    const int bits = (sx > 0 ? 1 : 0) | (sy > 0 ? 2 : 0) | (sz > 0 ? 4 : 0);
+    s.ng_lo[t] = make_float4(s.xl[i], s.yl[i], s.zl[i], __int_as_float(bits));
+    const uint64_t key = cell_key(k, cx, cy, cz);
+    s.ng_key[t] = key;
+    // the table has at least twice as many slots as bodies, so a free or
+    // matching slot always exists; the bound only caps the loop
+    uint32_t b = slot_of(key, mask);
+    for (int64_t p = 0; p < H; ++p) {
+        const unsigned long long prev = atomicCAS(&s.ng_slot[b].key, NG_EMPTY, key);
+        if (prev == NG_EMPTY || prev == key) break;
+        b = (b + 1) & mask;
+    }
     s.ng_bucket[t] = (int)b;
-    atomicAdd(&s.ng_count[b], 1);
+    s.ng_rank[t] = atomicAdd(&s.ng_count[b], 1);
 }
 
 // Exclusive scan of ng_count[0, H) into ng_start: per-block scan of 1024
@@ -137,94 +166,114 @@ __global__ void scan_add_kernel(int *out, const int *bsum, int64_t H, int64_t n)
     if (i == 0) out[H] = (int)n;
 }
 
+// Bodies into their cell's range, in arrival order.
 __global__ void near_scatter_kernel(DevState s)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= s.n) return;
     const int b = s.ng_bucket[t];
-    const int pos = s.ng_start[b] + atomicAdd(&s.ng_count[b], 1);
-    s.ng_entry[pos] = (int)t;
+    if (b < 0) return;
+    s.ng_entry[s.ng_start[b] + s.ng_rank[t]] = (int)t;
 }
 
-// Bodies of each bucket in ascending linear index (buckets hold ~1 body).
-__global__ void near_sort_kernel(DevState s, int64_t H)
+// Final place of each body in its cell = number of cell members with a
+// smaller linear index; writes the cell-ordered copies (lo.w = t) and, from
+// the cell's first body, the slot's range.
+__global__ void near_rank_kernel(DevState s)
 {
-    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (b >= H) return;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= s.n) return;
+    const int b = s.ng_bucket[t];
+    if (b < 0) return;
     const int lo = s.ng_start[b], hi = s.ng_start[b + 1];
-    for (int a = lo + 1; a < hi; ++a) {
-        const int v = s.ng_entry[a];
-        int k = a - 1;
-        while (k >= lo && s.ng_entry[k] > v) {
-            s.ng_entry[k + 1] = s.ng_entry[k];
-            --k;
-        }
-        s.ng_entry[k + 1] = v;
+    int r = 0;
+    for (int e = lo; e < hi; ++e) r += s.ng_entry[e] < (int)t ? 1 : 0;
+    s.ng_spos[lo + r] = s.ng_pos[t];
+    float4 l = s.ng_lo[t];
+    l.w = __int_as_float((int)t);
+    s.ng_slo[lo + r] = l;
+    if (r == 0) {
+        s.ng_slot[b].start = lo;
+        s.ng_slot[b].end = hi;
     }
 }
 
-// One warp per body t; lane l < 27 visits neighbour cell (l % 3 - 1,
-// l / 3 % 3 - 1, l / 9 - 1); the lane sums are combined by a fixed shuffle tree.
-__global__ void near_correct_kernel(DevState s, uint32_t mask, double G)
+// One thread per body t: probe its 8 cells (first loads issued together),
+// then visit their bodies in cell order.
+__global__ void __launch_bounds__(256) near_correct_kernel(DevState s, uint32_t mask, int64_t H,
+                                                           double G)
 {
-    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (t >= s.n) return;   // whole warps exit together
-    const int32_t k = cluster_of(s.cl, t);
-    const int64_t base = s.cl.boff[k] - s.cl.noff[k];
-    const int64_t i = base + t;
-    const Frame f = s.cl.frame[k];
-    const float eps2 = s.cl.eps2f[k];
-    const float th2 = f.th2;
-    const float ih = inv_cell(f);
-    const float xi = s.xh[i], yi = s.yh[i], zi = s.zh[i];
-    const float lxi = s.xl[i], lyi = s.yl[i], lzi = s.zl[i];
-    const int cx = cell_coord(xi, ih), cy = cell_coord(yi, ih), cz = cell_coord(zi, ih);
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= s.n) return;
+    const uint64_t kt = s.ng_key[t];
+    const float4 P = s.ng_pos[t];
+    const float4 Lo = s.ng_lo[t];
+    const int32_t k = (int32_t)(kt >> (3 * CELL_BITS));
+    const int bits = __float_as_int(Lo.w);
     double ax = 0.0, ay = 0.0, az = 0.0;
-    if (lane < 27) {
-        const int dx = lane % 3 - 1, dy = lane / 3 % 3 - 1, dz = lane / 9 - 1;
-        const uint64_t key = cell_key(k, cx + dx, cy + dy, cz + dz);
-        const uint32_t b = cell_bucket(k, cx + dx, cy + dy, cz + dz, mask);
-        const int lo = s.ng_start[b], hi = s.ng_start[b + 1];
-        for (int e = lo; e < hi; ++e) {
-            const int tj = s.ng_entry[e];
-            if (tj == t || s.ng_key[tj] != key) continue;
-            const int64_t j = base + tj;
-            // the pair kernel's float contribution, operation for operation
-            const float mj = s.mf[j];
-            const float ddx = __fadd_rn(s.xh[j], -xi);
-            const float ddy = __fadd_rn(s.yh[j], -yi);
-            const float ddz = __fadd_rn(s.zh[j], -zi);
-            float r2 = __fmaf_rn(ddx, ddx, eps2);
-            r2 = __fmaf_rn(ddy, ddy, r2);
-            r2 = __fmaf_rn(ddz, ddz, r2);
-            if (!(r2 < th2)) continue;
-            const float ri = near_rsqrt(r2);
-            const float sf = __fmul_rn(__fmul_rn(mj, ri), __fmul_rn(ri, ri));
-            // the same pair with the double-single coordinate difference
-            const float ex = __fadd_rn(ddx, __fsub_rn(s.xl[j], lxi));
-            const float ey = __fadd_rn(ddy, __fsub_rn(s.yl[j], lyi));
-            const float ez = __fadd_rn(ddz, __fsub_rn(s.zl[j], lzi));
-            float e2 = __fmaf_rn(ex, ex, eps2);
-            e2 = __fmaf_rn(ey, ey, e2);
-            e2 = __fmaf_rn(ez, ez, e2);
-            const float re = near_rsqrt(e2);
-            const float se = __fmul_rn(__fmul_rn(mj, re), __fmul_rn(re, re));
-            ax += (double)__fmul_rn(ex, se) - (double)__fmul_rn(ddx, sf);
-            ay += (double)__fmul_rn(ey, se) - (double)__fmul_rn(ddy, sf);
-            az += (double)__fmul_rn(ez, se) - (double)__fmul_rn(ddz, sf);
+    if (!(bits & NO_GRID)) {
+        const int cmask = (1 << CELL_BITS) - 1;
+        const int cx = (int)((kt >> (2 * CELL_BITS)) & cmask) - CELL_OFF;
+        const int cy = (int)((kt >> CELL_BITS) & cmask) - CELL_OFF;
+        const int cz = (int)(kt & cmask) - CELL_OFF;
+        const int sx = bits & 1 ? 1 : -1, sy = bits & 2 ? 1 : -1, sz = bits & 4 ? 1 : -1;
+        uint64_t key[8];
+        uint32_t slot[8];
+        NgSlot v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            key[q] = cell_key(k, cx + (q & 1 ? sx : 0), cy + (q & 2 ? sy : 0),
+                              cz + (q & 4 ? sz : 0));
+            slot[q] = slot_of(key[q], mask);
+            v[q] = s.ng_slot[slot[q]];
+        }
+        const float eps2 = s.cl.eps2f[k];
+        const float th2 = s.cl.frame[k].th2;
+        const float xi = P.x, yi = P.y, zi = P.z;
+        const float lxi = Lo.x, lyi = Lo.y, lzi = Lo.z;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            NgSlot c = v[q];
+            uint32_t b = slot[q];
+            for (int64_t p = 1; p < H && c.key != key[q] && c.key != NG_EMPTY; ++p) {
+                b = (b + 1) & mask;
+                c = s.ng_slot[b];
+            }
+            if (c.key != key[q]) continue;   // empty cell
+            for (int e = c.start; e < c.end; ++e) {
+                const float4 Pj = s.ng_spos[e];
+                const float4 Lj = s.ng_slo[e];
+                if (__float_as_int(Lj.w) == (int)t) continue;
+                // the pair kernel's float contribution, operation for operation
+                const float mj = Pj.w;
+                const float ddx = __fadd_rn(Pj.x, -xi);
+                const float ddy = __fadd_rn(Pj.y, -yi);
+                const float ddz = __fadd_rn(Pj.z, -zi);
+                float r2 = __fmaf_rn(ddx, ddx, eps2);
+                r2 = __fmaf_rn(ddy, ddy, r2);
+                r2 = __fmaf_rn(ddz, ddz, r2);
+                if (!(r2 < th2)) continue;
+                const float ri = near_rsqrt(r2);
+                const float sf = __fmul_rn(__fmul_rn(mj, ri), __fmul_rn(ri, ri));
+                // the same pair with the double-single coordinate difference
+                const float ex = __fadd_rn(ddx, __fsub_rn(Lj.x, lxi));
+                const float ey = __fadd_rn(ddy, __fsub_rn(Lj.y, lyi));
+                const float ez = __fadd_rn(ddz, __fsub_rn(Lj.z, lzi));
+                float e2 = __fmaf_rn(ex, ex, eps2);
+                e2 = __fmaf_rn(ey, ey, e2);
+                e2 = __fmaf_rn(ez, ez, e2);
+                const float re = near_rsqrt(e2);
+                const float se = __fmul_rn(__fmul_rn(mj, re), __fmul_rn(re, re));
+                ax += (double)__fmul_rn(ex, se) - (double)__fmul_rn(ddx, sf);
+                ay += (double)__fmul_rn(ey, se) - (double)__fmul_rn(ddy, sf);
+                az += (double)__fmul_rn(ez, se) - (double)__fmul_rn(ddz, sf);
+            }
         }
     }
-    for (int w = 16; w > 0; w >>= 1) {
-        ax += __shfl_down_sync(0xffffffffu, ax, w);
-        ay += __shfl_down_sync(0xffffffffu, ay, w);
-        az += __shfl_down_sync(0xffffffffu, az, w);
-    }
-    if (lane == 0) {
-        s.corr[i] = G * ax;
-        s.corr[s.cap + i] = G * ay;
-        s.corr[2 * s.cap + i] = G * az;
-    }
+    const int64_t i = s.cl.boff[k] + t - s.cl.noff[k];
+    s.corr[i] = G * ax;
+    s.corr[s.cap + i] = G * ay;
+    s.corr[2 * s.cap + i] = G * az;
 }
 
 int64_t near_table_size(int64_t n)
@@ -242,17 +291,17 @@ cudaError_t launch_near_correct(const DevState &s, double G, cudaStream_t st)
     const unsigned nbn = (unsigned)((s.n + 255) / 256);
     const unsigned nbh = (unsigned)((H + 255) / 256);
     const int nscan = (int)((H + SCAN_B - 1) / SCAN_B);
-    cudaError_t e = cudaMemsetAsync(s.ng_count, 0, (size_t)H * sizeof(int), st);
+    cudaError_t e = cudaMemsetAsync(s.ng_slot, 0xff, (size_t)H * sizeof(NgSlot), st);
     if (e != cudaSuccess) return e;
-    near_cell_kernel<<<nbn, 256, 0, st>>>(s, mask);
+    e = cudaMemsetAsync(s.ng_count, 0, (size_t)H * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    near_cell_kernel<<<nbn, 256, 0, st>>>(s, mask, H);
     scan_block_kernel<<<nscan, SCAN_T, 0, st>>>(s.ng_count, s.ng_start, s.ng_bsum, H);
     scan_top_kernel<<<1, SCAN_T, 0, st>>>(s.ng_bsum, nscan);
     scan_add_kernel<<<nbh, 256, 0, st>>>(s.ng_start, s.ng_bsum, H, s.n);
-    e = cudaMemsetAsync(s.ng_count, 0, (size_t)H * sizeof(int), st);
-    if (e != cudaSuccess) return e;
     near_scatter_kernel<<<nbn, 256, 0, st>>>(s);
-    near_sort_kernel<<<nbh, 256, 0, st>>>(s, H);
-    near_correct_kernel<<<(unsigned)((s.n * 32 + 255) / 256), 256, 0, st>>>(s, mask, G);
+    near_rank_kernel<<<nbn, 256, 0, st>>>(s);
+    near_correct_kernel<<<nbn, 256, 0, st>>>(s, mask, H, G);
     return cudaGetLastError();
 }
 

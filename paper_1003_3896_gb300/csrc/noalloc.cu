@@ -41,8 +41,10 @@ constexpr int64_t OFF_J = OFF_F + align256(7 * NA_MAX_N * 4);               // j
 constexpr int64_t OFF_P = OFF_J + align256(4 * NA_MAX_N * 16);              // partial slots
 constexpr int64_t OFF_C = OFF_P + align256(NA_SLOTS * 3 * NA_MAX_N * 8);    // near-pair correction
 constexpr int64_t OFF_K = OFF_C + align256(3 * NA_MAX_N * 8);               // cell keys
-constexpr int64_t OFF_I = OFF_K + align256(NA_MAX_N * 8);                   // bucket, entry
-constexpr int64_t OFF_H = OFF_I + align256(2 * NA_MAX_N * 4);               // count, start, bsum
+constexpr int64_t OFF_I = OFF_K + align256(NA_MAX_N * 8);                   // bucket, rank, entry
+constexpr int64_t OFF_Q = OFF_I + align256(3 * NA_MAX_N * 4);               // pos lo spos slo
+constexpr int64_t OFF_S = OFF_Q + align256(4 * NA_MAX_N * 16);              // cell table
+constexpr int64_t OFF_H = OFF_S + align256(NA_H * (int64_t)sizeof(NgSlot));  // count, start, bsum
 constexpr int64_t OFF_T = OFF_H + align256((2 * NA_H + 1 + NA_H / 1024 + 1) * 4);  // tables
 // tables of the single cluster: boff nk noff[2] uoff[2] eps2d dts (int64/double),
 // seg_lo[S] seg_hi[S], then ntiles eps2f seg_k[S] seg_off[2] flag (32-bit)
@@ -168,7 +170,13 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
         s.corr = reinterpret_cast<double *>(b + OFF_C);
         s.ng_key = reinterpret_cast<uint64_t *>(b + OFF_K);
         s.ng_bucket = reinterpret_cast<int *>(b + OFF_I);
-        s.ng_entry = s.ng_bucket + N;
+        s.ng_rank = s.ng_bucket + N;
+        s.ng_entry = s.ng_bucket + 2 * N;
+        s.ng_pos = reinterpret_cast<float4 *>(b + OFF_Q);
+        s.ng_lo = s.ng_pos + N;
+        s.ng_spos = s.ng_pos + 2 * N;
+        s.ng_slo = s.ng_pos + 3 * N;
+        s.ng_slot = reinterpret_cast<NgSlot *>(b + OFF_S);
         s.ng_count = reinterpret_cast<int *>(b + OFF_H);
         s.ng_start = s.ng_count + NA_H;
         s.ng_bsum = s.ng_start + NA_H + 1;
