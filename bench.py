@@ -109,6 +109,28 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+# DRAM bytes (read + write) per launch of the mixed pair kernel on this
+# workload, from one `ncu --set full` capture (profiles/ has the summary and the
+# command).  Reported only while pair.cu is byte-identical to the captured
+# source (first 16 hex digits of its SHA-256); any change to the kernel makes
+# the figure stale and the bench then reports null.
+PAIR_TRAFFIC = {"source_sha256": "c8d323ce115f4d62", "n": 65536, "precision": "ds",
+                "bytes_per_launch": 2936576.0}
+
+
+def pair_traffic(n: int, precision: str):
+    import hashlib
+    path = os.path.join(ROOT, "paper_1003_3896_gb300", "csrc", "pair.cu")
+    try:
+        digest = hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    t = PAIR_TRAFFIC
+    if digest != t["source_sha256"] or n != t["n"] or precision != t["precision"]:
+        return None
+    return t["bytes_per_launch"]
+
+
 def fp32_peak_tflops(sms: int, mhz: float) -> float:
     """FP32 FMA peak from unit counts: 128 FP32 lanes per SM, 2 flops per FMA."""
     return sms * 128 * 2 * mhz * 1e6 / 1e12
@@ -296,7 +318,8 @@ def main():
                   "fp32": "f32", "fp64": "f64"}[args.precision],
         "data": "synthetic", "config": config_dict(args, world),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": pair_traffic(n, args.precision),
+                     "traffic_unit": "bytes per launch (dram read + write)",
                      "kernel": f"pair_sp_kernel ({args.precision})",
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max clock)",
                      "frac_at_sampled_clock": achieved / fp32_peak_tflops(sms, sustained_mhz),
