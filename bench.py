@@ -111,14 +111,15 @@ class ClockSampler:
 
 # DRAM bytes (read + write) per launch of the mixed pair kernel on this
 # workload, from one `ncu --set full` capture (profiles/ has the summary and the
-# command).  Reported only while pair.cu is byte-identical to the captured
-# source (first 16 hex digits of its SHA-256); any change to the kernel makes
-# the figure stale and the bench then reports null.
+# command).  Reported only for the captured launch shape and while pair.cu is
+# byte-identical to the captured source (first 16 hex digits of its SHA-256);
+# any change to the kernel or its shape makes the figure stale and the bench
+# then reports null.
 PAIR_TRAFFIC = {"source_sha256": "c8d323ce115f4d62", "n": 65536, "precision": "ds",
-                "bytes_per_launch": 2936576.0}
+                "bodies_per_thread": 4, "blocks_per_sm": 6, "bytes_per_launch": 2936576.0}
 
 
-def pair_traffic(n: int, precision: str):
+def pair_traffic(n: int, precision: str, shape: dict):
     import hashlib
     path = os.path.join(ROOT, "paper_1003_3896_gb300", "csrc", "pair.cu")
     try:
@@ -126,7 +127,9 @@ def pair_traffic(n: int, precision: str):
     except OSError:
         return None
     t = PAIR_TRAFFIC
-    if digest != t["source_sha256"] or n != t["n"] or precision != t["precision"]:
+    if (digest != t["source_sha256"] or n != t["n"] or precision != t["precision"]
+            or shape.get("bodies_per_thread") != t["bodies_per_thread"]
+            or shape.get("blocks_per_sm") != t["blocks_per_sm"]):
         return None
     return t["bytes_per_launch"]
 
@@ -205,6 +208,8 @@ def main():
     ap.add_argument("--near-frac", type=float, default=0.0,
                     help="mixed mode near-pair radius in units of R_rms / N^(1/3) (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the pair-kernel shape autotuner (nb_tune) before timing")
     ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5"],
                     help="c2 (default): the headline line; the others print their own "
                          "labelled lines (see bench_workloads.py)")
@@ -243,6 +248,7 @@ def main():
     ctx = nbsym.Context(n, eps=eps, precision=args.precision, ext_on=True, device=local,
                         stream=stream.cuda_stream, near_frac=args.near_frac)
     ctx.load(pos, vel, m)
+    tuning = None if args.no_tune else ctx.tune(reps=3)
     for _ in range(args.warmup):
         ctx.step(6, dt, 1)
 
@@ -264,6 +270,7 @@ def main():
         torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     prof = ctx.prof_read()
+    shape = ctx.pair_shape()
     ctx.prof_enable(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     t_ms = sum(step_ms)
@@ -298,6 +305,7 @@ def main():
 
     # plain FP64 kernel on the same state and configuration
     ctx.set_precision("fp64")
+    tuning64 = None if args.no_tune else ctx.tune(reps=1)
     ctx.prof_enable(True)
     for _ in range(2):
         ctx.accel()
@@ -318,7 +326,7 @@ def main():
                   "fp32": "f32", "fp64": "f64"}[args.precision],
         "data": "synthetic", "config": config_dict(args, world),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": pair_traffic(n, args.precision),
+                     "frac": achieved / peak, "traffic": pair_traffic(n, args.precision, shape),
                      "traffic_unit": "bytes per launch (dram read + write)",
                      "kernel": f"pair_sp_kernel ({args.precision})",
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max clock)",
@@ -328,7 +336,8 @@ def main():
                      "measured_peaks": peaks,
                      "pair_kernel_ms_mean": prof["pair_ms"] / max(1, prof["pair_launches"]),
                      "pair_launches": prof["pair_launches"]},
-        "fp64_kernel": {"value": fp64_rate, "unit": UNIT},
+        "pair_shape": {"timed": shape, "tuning": tuning},
+        "fp64_kernel": {"value": fp64_rate, "unit": UNIT, "tuned": tuning64},
         "vs_fp64_kernel": value / fp64_rate if fp64_rate > 0 else None,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 7 * 8,
                 "d2h_bytes_per_step": n * 6 * 8, "steps": e2e_steps},

@@ -54,6 +54,7 @@ def c1(args, nbsym, torch):
     for prec in ("fp64", "ds"):
         with _ctx(nbsym, n, eps=eps, precision=prec) as c:
             c.load(pos, vel, m)
+            tuning = None if args.no_tune else c.tune(reps=5)
             c.step(2, dt, 3)             # warm-up (graph capture)
             c.load(pos, vel, m)
             torch.cuda.synchronize()
@@ -65,7 +66,8 @@ def c1(args, nbsym, torch):
         out[prec] = {"us_per_step": 1e6 * wall / nsteps,
                      "value": nsteps * n * n / wall / 1e9,
                      "dE_over_E": de, "dE_over_E_oracle": de_ref,
-                     "max_pos_err_vs_oracle": float(np.abs(x - rx).max())}
+                     "max_pos_err_vs_oracle": float(np.abs(x - rx).max()),
+                     "tuning": tuning}
     return {"metric": "leapfrog step latency, N=1024", "workload":
             "plummer_N1024_henon_eps1e-3_dkd_dt1/1024_64steps", "unit": "us/step",
             "value": out["fp64"]["us_per_step"], "higher_is_better": False,
@@ -81,8 +83,12 @@ def c3(args, nbsym, torch):
     sweep = {}
     with _ctx(nbsym, n, eps=eps, precision="ds") as c:
         c.load(pos, vel, m)
+        tunings = {}
         for prec in ("fp64", "ds", "fp32"):
             c.set_precision(prec)
+            # the FP64 kernel takes seconds per launch here: tuned only by request
+            if not args.no_tune and prec != "fp64":
+                tunings[prec] = c.tune(reps=2)
             c.accel()
             c.prof_enable(True)
             a = c.accel()
@@ -100,7 +106,8 @@ def c3(args, nbsym, torch):
     return {"metric": "accuracy sweep and leapfrog throughput, N=262144 Salpeter",
             "workload": "plummer_salpeter_N262144_eps1e-4", "unit": UNIT,
             "value": 20 * n * n / wall / 1e9, "higher_is_better": True,
-            "sweep": sweep, "tolerance": {"fp64": 1e-12, "ds": 1e-6, "fp32": 1e-5}}
+            "sweep": sweep, "tolerance": {"fp64": 1e-12, "ds": 1e-6, "fp32": 1e-5},
+            "tuning": tunings}
 
 
 def c4(args, nbsym, torch):
@@ -118,6 +125,7 @@ def c4(args, nbsym, torch):
     with nbsym.Context(sizes=sizes, precision="ds") as b:
         b.set_cluster_params(eps=eps)
         b.load(pos, vel, mass)
+        tuning = None if args.no_tune else b.tune(reps=2)
         b.step(6, dt, max(1, args.warmup))
         steps = args.steps
         torch.cuda.synchronize()
@@ -135,7 +143,7 @@ def c4(args, nbsym, torch):
             "sum_N2_per_eval": pairs, "steps": steps, "ms_per_step": 1e3 * wall / steps,
             "pair_kernel_tflops": achieved, "pair_launches": pr["pair_launches"],
             "pair_kernel_ms_mean": pr["pair_ms"] / max(1, pr["pair_launches"]),
-            "gpu_launches": pr["kernel_launches"]}
+            "gpu_launches": pr["kernel_launches"], "tuning": tuning}
 
 
 def c5(args, nbsym, torch):

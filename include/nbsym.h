@@ -255,6 +255,57 @@ int nb_measure_peaks(int device, nb_peaks_t *out);
 int nb_accel_static(const nb_params *p, int64_t n, const double *d_pos,
                     const double *d_mass, double *d_acc_out);
 
+/* ---- autotuner (no counterpart in the paper: the paper fixes one block
+ * shape for its GPU, Sect. 3.2) ---------------------------------------------
+ * The launch shape of the pair kernel is (bodies per thread I, resident
+ * blocks per SM b): I sets the width 128 * I of the i-block that one work
+ * unit covers against one 128-body j-tile, b sets the persistent grid
+ * (b * SMs blocks, at most half the unit count) and so how finely units are
+ * cut into per-block runs.  nb_tune times every shape this build compiled for
+ * the context's current precision on its loaded state (reps launches each,
+ * CUDA events on the context's stream), switches the context to the fastest
+ * and records it in a process-wide table keyed by the workload's shape (SM
+ * count, precision, cluster count, bodies, widest cluster), which every later
+ * context or serving group of the same shape uses.  Two shapes can split the
+ * j-sums differently, so results may differ at the rounding level between
+ * shapes; with one shape they are bit-reproducible. */
+typedef struct {
+    int precision;           /* enum nb_precision tuned */
+    int bodies_per_thread;   /* chosen I */
+    int blocks_per_sm;       /* chosen b */
+    int candidates;          /* shapes timed */
+    int64_t grid;            /* persistent blocks of the chosen shape */
+    double pair_ms;          /* mean pair-launch time of the chosen shape */
+    double default_ms;       /* the same for the shape chosen without tuning */
+} nb_tune_t;
+
+/* Tune the context (1 <= reps <= 1000; out may be NULL).  Synchronous; the
+ * state is untouched.  Errors: NB_EINVAL, NB_ESTATE (nothing loaded),
+ * NB_ECUDA. */
+int nb_tune(nb_ctx *ctx, int reps, nb_tune_t *out);
+
+/* Write the process-wide table to a text file (one line per shape: SM count,
+ * precision, clusters, bodies, widest cluster in tiles, I, b).  Errors:
+ * NB_EINVAL (NULL path, file not writable). */
+int nb_tune_save(const char *path);
+
+/* Merge the entries of a file written by nb_tune_save into the table.
+ * Returns the number of entries read (>= 0), or NB_EINVAL (NULL path,
+ * unreadable or malformed file, or a shape this build lacks; nothing is
+ * merged then).  Contexts planned afterwards use the entries. */
+int64_t nb_tune_load(const char *path);
+
+/* The pair-kernel shape of the context's current plan: bodies per thread,
+ * resident blocks per SM, persistent grid (any out pointer may be NULL).
+ * Errors: NB_EINVAL (NULL ctx), NB_ESTATE (nothing loaded yet). */
+int nb_pair_shape(nb_ctx *ctx, int *bodies_per_thread, int *blocks_per_sm, int64_t *grid);
+
+/* Number of entries in the table. */
+int64_t nb_tune_entries(void);
+
+/* Empty the table.  Contexts already planned keep their shape. */
+void nb_tune_clear(void);
+
 /* Release the context and all its device memory.  NULL-safe. */
 void nb_destroy(nb_ctx *ctx);
 

@@ -166,6 +166,13 @@ int set_define(ClusterSet &C, int32_t K, const int64_t *boff, const int64_t *nk,
         C.noff[k + 1] = C.noff[k] + nk[k];
     }
     C.n = C.noff[K];
+    // widest cluster in j-tiles (independent of the i-block width; part of
+    // the tuned-shape key, so known before the layout)
+    C.max_ntiles = 0;
+    for (int32_t k = 0; k < K; ++k) {
+        const int64_t nt = (C.nk[k] + TILE - 1) / TILE;
+        if (nt > C.max_ntiles) C.max_ntiles = nt;
+    }
     C.eps2d.resize(K);
     C.eps2f.resize(K);
     for (int32_t k = 0; k < K; ++k) {
@@ -283,30 +290,38 @@ int mode_of(int precision)
 
 bool float_planes(int precision) { return precision != NB_FP64; }
 
-int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan &out)
+int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan &out,
+              const PairShape *force, bool use_table)
 {
     Plan pl;
     pl.precision = precision;
     pl.pl.mode = mode_of(precision);
     const int64_t mean = C.n / (C.K > 0 ? C.K : 1);
-    int I;
-    if (pl.pl.mode == PM_FP64)
+    int I, bps = 0;
+    PairShape tuned;
+    if (force) {
+        I = force->I;
+        bps = force->blocks_per_sm;
+    } else if (use_table && tune_lookup(tune_key(P, C, precision), &tuned)) {
+        I = tuned.I;
+        bps = tuned.blocks_per_sm;
+    } else if (pl.pl.mode == PM_FP64) {
         I = 1;
-    else if (mean < 16384)
+    } else if (mean < 16384) {
         I = 2;
-    else
+    } else {
         // measured at N = 65536: mixed is fastest at 4 bodies per thread,
         // pure float (fewer live registers) at 8
         I = pl.pl.mode == PM_FP32 ? 8 : 4;
-    if (const char *env = getenv("NBSYM_PAIR_I")) {
-        // tuning override: bodies per thread of the pair kernel
-        const int v = atoi(env);
-        if (pair_variant_exists(pl.pl.mode, v)) I = v;
     }
+    if (!pair_variant_exists(pl.pl.mode, I))
+        return set_error(NB_EINVAL, "no pair kernel with %d bodies per thread for this precision",
+                         I);
     pl.pl.I = I;
     int rc = set_layout(C, TILE * I, st);
     if (rc) return rc;
-    pl.pl.blocks_per_sm = pair_occupancy(pl.pl.mode, I);
+    const int occ = pair_occupancy(pl.pl.mode, I);
+    pl.pl.blocks_per_sm = bps > 0 && bps < occ ? bps : occ;
     if (pl.pl.blocks_per_sm < 1) pl.pl.blocks_per_sm = 1;
     const int64_t W = C.uoff[C.K];
     int64_t G = (int64_t)P.num_sms * pl.pl.blocks_per_sm;
@@ -314,10 +329,10 @@ int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan
     pl.pl.d = make_decomp(W, C.max_ntiles, TILE * I, G, P.s.part_slots);
     for (int32_t k = 0; k < C.K; ++k)
         if (C.eps2d[k] == 0.0) pl.pl.d.mask_self = 1;
-    int occ = pair_occupancy(PM_FP64, 1);
-    if (occ < 1) occ = 1;
+    int occ_pot = pair_occupancy(PM_FP64, 1);
+    if (occ_pot < 1) occ_pot = 1;
     const int64_t Wp = C.uoff_pot[C.K];
-    int64_t Gp = (int64_t)P.num_sms * occ;
+    int64_t Gp = (int64_t)P.num_sms * occ_pot;
     if (Wp / 2 < Gp) Gp = Wp / 2 > 0 ? Wp / 2 : 1;
     pl.pot = make_decomp(Wp, C.max_ntiles, TILE, Gp, P.s.part_slots);
     out = pl;

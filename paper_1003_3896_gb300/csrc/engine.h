@@ -76,9 +76,45 @@ struct Plan {
     PairLaunch pl{};
     Decomp pot{};
 };
+// Launch shape of the pair kernel: I bodies per thread (i-block width
+// TILE * I) and blocks_per_sm resident blocks (grid = blocks_per_sm * SMs,
+// at most half the unit count).
+struct PairShape {
+    int I = 0;
+    int blocks_per_sm = 0;
+};
 // Choose the pair kernel variant and decompositions for a cluster set and
-// lay the set out for it.
-int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan &out);
+// lay the set out for it.  The shape is `force` when given, else the tuned
+// entry for the set's shape (when use_table), else the built-in heuristic.
+int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan &out,
+              const PairShape *force = nullptr, bool use_table = true);
+
+// ---- autotuner (tune.cu) -----------------------------------------------------
+struct TuneKey {
+    int sms = 0, precision = 0;
+    int32_t K = 0;
+    int64_t n = 0, max_ntiles = 0;
+};
+struct TuneReport {
+    int precision = 0;
+    PairShape shape;
+    int64_t grid = 0;
+    int candidates = 0;
+    double pair_ms = 0, default_ms = 0;
+};
+TuneKey tune_key(const Pool &P, const ClusterSet &C, int precision);
+bool tune_lookup(const TuneKey &k, PairShape *out);
+void tune_store(const TuneKey &k, const PairShape &s);
+void tune_clear();
+int64_t tune_entries();
+int tune_save(const char *path);
+int tune_load(const char *path, int64_t *loaded);
+struct Phys;
+// Time every compiled shape of the precision's pair kernel on the set's
+// current state (reps launches each), remember the fastest for the set's
+// shape and return the plan built with it.
+int tune_pair(const Pool &P, ClusterSet &C, int precision, const Phys &ph, cudaStream_t st,
+              int reps, TuneReport &rep, Plan &out);
 
 struct Phys {
     double G = 1.0;

@@ -566,6 +566,60 @@ int nb_set_precision(nb_ctx *c, int precision)
     return NB_OK;
 }
 
+int nb_tune(nb_ctx *c, int reps, nb_tune_t *out)
+{
+    if (!c) return set_error(NB_EINVAL, "ctx is NULL");
+    if (reps < 1 || reps > 1000) return set_error(NB_EINVAL, "reps must be in [1, 1000]");
+    if (c->n == 0) return set_error(NB_ESTATE, "nb_tune before nb_load");
+    DeviceGuard dg(c->p.device);
+    int rc = refresh_split(c);
+    if (rc) return rc;
+    TuneReport rep;
+    Plan pl;
+    rc = tune_pair(c->pool, c->set, c->p.precision, c->phys, c->stream, reps, rep, pl);
+    if (rc) return rc;
+    c->plan = pl;
+    free_graphs(c);
+    if (out) {
+        out->precision = rep.precision;
+        out->bodies_per_thread = rep.shape.I;
+        out->blocks_per_sm = rep.shape.blocks_per_sm;
+        out->candidates = rep.candidates;
+        out->grid = rep.grid;
+        out->pair_ms = rep.pair_ms;
+        out->default_ms = rep.default_ms;
+    }
+    return NB_OK;
+}
+
+int nb_pair_shape(nb_ctx *c, int *bodies_per_thread, int *blocks_per_sm, int64_t *grid)
+{
+    if (!c) return set_error(NB_EINVAL, "ctx is NULL");
+    if (c->n == 0 || !c->planned) return set_error(NB_ESTATE, "nothing loaded");
+    if (bodies_per_thread) *bodies_per_thread = c->plan.pl.I;
+    if (blocks_per_sm) *blocks_per_sm = c->plan.pl.blocks_per_sm;
+    if (grid) *grid = c->plan.pl.d.G;
+    return NB_OK;
+}
+
+int nb_tune_save(const char *path)
+{
+    if (!path) return set_error(NB_EINVAL, "path is NULL");
+    return tune_save(path);
+}
+
+int64_t nb_tune_load(const char *path)
+{
+    if (!path) return set_error(NB_EINVAL, "path is NULL");
+    int64_t n = 0;
+    const int rc = tune_load(path, &n);
+    return rc ? rc : n;
+}
+
+int64_t nb_tune_entries(void) { return tune_entries(); }
+
+void nb_tune_clear(void) { tune_clear(); }
+
 int nb_prof_enable(nb_ctx *c, int on)
 {
     if (!c) return set_error(NB_EINVAL, "ctx is NULL");

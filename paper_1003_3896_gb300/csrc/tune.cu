@@ -1,0 +1,225 @@
+// tune.cu -- autotuner of the pair kernels' launch shape.
+//
+// The shape of one pair-force launch is (I, b): I bodies per thread, which
+// sets the width TILE * I of the i-block a work unit covers (the unit is that
+// i-block against one TILE-wide j-tile), and b resident blocks per SM, which
+// sets the persistent grid G = b * SMs (at most half the unit count) and so
+// how finely the (i-block, j-tile) units are cut into per-block runs.  The
+// best shape depends on the arithmetic (registers per thread), on N (small
+// clusters need more, smaller units to fill 152 SMs) and on the cluster mix of
+// a batch, so it is measured rather than modelled: every variant the library
+// has compiled is timed on the loaded state with CUDA events and the fastest
+// is kept.
+//
+// Choices are remembered process-wide per workload shape (SM count,
+// precision, cluster count, bodies, widest cluster in tiles), so every
+// context or serving group of that shape starts from the tuned plan, and can
+// be saved to / loaded from a text file so a tuned shape replays across runs.
+// A shape changes where the j-sums are split between partial slots, so
+// results of two shapes can differ at the rounding level (within the
+// precision's tolerance); with one shape they are bit-reproducible.
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "engine.h"
+
+namespace nb {
+
+namespace {
+
+using Key = std::tuple<int, int, int32_t, int64_t, int64_t>;
+std::mutex g_mu;
+std::map<Key, PairShape> g_table;
+
+Key key_of(const TuneKey &k) { return Key(k.sms, k.precision, k.K, k.n, k.max_ntiles); }
+
+bool shape_valid(int precision, const PairShape &s)
+{
+    return s.I > 0 && s.blocks_per_sm > 0 && pair_variant_exists(mode_of(precision), s.I);
+}
+
+}  // namespace
+
+TuneKey tune_key(const Pool &P, const ClusterSet &C, int precision)
+{
+    TuneKey k;
+    k.sms = P.num_sms;
+    k.precision = precision;
+    k.K = C.K;
+    k.n = C.n;
+    k.max_ntiles = C.max_ntiles;
+    return k;
+}
+
+bool tune_lookup(const TuneKey &k, PairShape *out)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_table.find(key_of(k));
+    if (it == g_table.end()) return false;
+    *out = it->second;
+    return true;
+}
+
+void tune_store(const TuneKey &k, const PairShape &s)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_table[key_of(k)] = s;
+}
+
+void tune_clear()
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_table.clear();
+}
+
+int64_t tune_entries()
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    return (int64_t)g_table.size();
+}
+
+int tune_save(const char *path)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    FILE *f = std::fopen(path, "w");
+    if (!f) return set_error(NB_EINVAL, "cannot open %s for writing", path);
+    std::fprintf(f, "nbsym-tune 1\n");
+    for (const auto &e : g_table) {
+        const Key &k = e.first;
+        std::fprintf(f, "%d %d %d %lld %lld %d %d\n", std::get<0>(k), std::get<1>(k),
+                     (int)std::get<2>(k), (long long)std::get<3>(k), (long long)std::get<4>(k),
+                     e.second.I, e.second.blocks_per_sm);
+    }
+    const bool ok = std::fclose(f) == 0;
+    return ok ? NB_OK : set_error(NB_EINVAL, "writing %s failed", path);
+}
+
+int tune_load(const char *path, int64_t *loaded)
+{
+    FILE *f = std::fopen(path, "r");
+    if (!f) return set_error(NB_EINVAL, "cannot open %s", path);
+    int version = 0;
+    if (std::fscanf(f, "nbsym-tune %d", &version) != 1 || version != 1) {
+        std::fclose(f);
+        return set_error(NB_EINVAL, "%s is not a tuning file of version 1", path);
+    }
+    int64_t count = 0;
+    int sms, prec, K, I, b;
+    long long n, mt;
+    std::map<Key, PairShape> add;
+    for (;;) {
+        const int r = std::fscanf(f, "%d %d %d %lld %lld %d %d", &sms, &prec, &K, &n, &mt, &I, &b);
+        if (r == EOF) break;
+        if (r != 7 || sms <= 0 || prec < NB_FP64 || prec > NB_DS_FULL || K <= 0 || n <= 0 ||
+            mt <= 0) {
+            std::fclose(f);
+            return set_error(NB_EINVAL, "%s: malformed entry %lld", path, (long long)count + 1);
+        }
+        PairShape s{I, b};
+        if (!shape_valid(prec, s)) {
+            std::fclose(f);
+            return set_error(NB_EINVAL, "%s: entry %lld names a shape this build lacks", path,
+                             (long long)count + 1);
+        }
+        add[Key(sms, prec, K, n, mt)] = s;
+        ++count;
+    }
+    std::fclose(f);
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (const auto &e : add) g_table[e.first] = e.second;
+    if (loaded) *loaded = count;
+    return NB_OK;
+}
+
+// Mean time of one pair launch of the given plan, over reps launches after
+// one untimed launch.
+static int time_plan(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph,
+                     cudaStream_t st, int reps, cudaEvent_t e0, cudaEvent_t e1, double *ms)
+{
+    const DevState s = view(P, C, pl.precision);
+    HostTab ht;
+    ht.K = C.K;
+    ht.uoff = C.uoff.data();
+    ht.boff = C.boff.data();
+    ht.nk = C.nk.data();
+    ht.ntiles = C.ntiles.data();
+    ht.eps2f = C.eps2f.data();
+    NB_TRY(launch_pair(s, pl.pl, ht, ph.G, st));
+    NB_TRY(cudaEventRecord(e0, st));
+    for (int r = 0; r < reps; ++r) NB_TRY(launch_pair(s, pl.pl, ht, ph.G, st));
+    NB_TRY(cudaEventRecord(e1, st));
+    NB_TRY(cudaEventSynchronize(e1));
+    float t = 0.f;
+    NB_TRY(cudaEventElapsedTime(&t, e0, e1));
+    *ms = t / reps;
+    return NB_OK;
+}
+
+int tune_pair(const Pool &P, ClusterSet &C, int precision, const Phys &ph, cudaStream_t st,
+              int reps, TuneReport &rep, Plan &out)
+{
+    if (reps < 1) reps = 1;
+    const int mode = mode_of(precision);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    NB_TRY(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return set_error(NB_ECUDA, "cudaEventCreate failed");
+    }
+    int rc = NB_OK;
+    rep = TuneReport();
+    rep.precision = precision;
+    PairShape best{0, 0};
+    double best_ms = 0;
+    std::vector<int64_t> seen;   // (I, G) pairs already timed
+    do {
+        // the shape the planner would pick without a tuned entry
+        Plan def;
+        rc = plan_make(P, C, precision, st, def, nullptr, /*use_table=*/false);
+        if (rc) break;
+        rc = time_plan(P, C, def, ph, st, reps, e0, e1, &rep.default_ms);
+        if (rc) break;
+        const int Is[] = {1, 2, 4, 8};
+        for (int I : Is) {
+            if (!pair_variant_exists(mode, I)) continue;
+            const int occ = pair_occupancy(mode, I);
+            for (int b = occ; b >= 1 && b > occ - 4; --b) {
+                const PairShape s{I, b};
+                Plan pl;
+                rc = plan_make(P, C, precision, st, pl, &s, false);
+                if (rc) break;
+                const int64_t tag = pl.pl.d.G * 16 + I;
+                bool dup = false;
+                for (int64_t v : seen) dup = dup || v == tag;
+                if (dup) continue;
+                seen.push_back(tag);
+                double ms = 0;
+                rc = time_plan(P, C, pl, ph, st, reps, e0, e1, &ms);
+                if (rc) break;
+                ++rep.candidates;
+                if (best.I == 0 || ms < best_ms) {
+                    best = s;
+                    best_ms = ms;
+                    rep.grid = pl.pl.d.G;
+                }
+            }
+            if (rc) break;
+        }
+        if (rc) break;
+        if (best.I == 0) {
+            rc = set_error(NB_ECUDA, "no pair-kernel shape could be timed");
+            break;
+        }
+        rep.shape = best;
+        rep.pair_ms = best_ms;
+        tune_store(tune_key(P, C, precision), best);
+        rc = plan_make(P, C, precision, st, out, &best, false);
+    } while (0);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+}  // namespace nb

@@ -50,6 +50,12 @@ class PeaksT(C.Structure):
                 ("rsqrt_gops", C.c_double), ("pairmix_gpairs", C.c_double)]
 
 
+class TuneT(C.Structure):
+    _fields_ = [("precision", C.c_int), ("bodies_per_thread", C.c_int),
+                ("blocks_per_sm", C.c_int), ("candidates", C.c_int), ("grid", C.c_int64),
+                ("pair_ms", C.c_double), ("default_ms", C.c_double)]
+
+
 _dp = C.POINTER(C.c_double)
 _vp = C.c_void_p
 _ctxp = C.c_void_p
@@ -87,6 +93,31 @@ nb_set_cluster_params = _sig("nb_set_cluster_params", C.c_int, _ctxp, _dp, _dp)
 nb_clusters = _sig("nb_clusters", C.c_int64, _ctxp)
 nb_energy_clusters = _sig("nb_energy_clusters", C.c_int, _ctxp, C.POINTER(EnergyT))
 nb_accel_static = _sig("nb_accel_static", C.c_int, C.POINTER(Params), C.c_int64, _vp, _vp, _vp)
+nb_tune = _sig("nb_tune", C.c_int, _ctxp, C.c_int, C.POINTER(TuneT))
+nb_tune_save = _sig("nb_tune_save", C.c_int, C.c_char_p)
+nb_tune_load = _sig("nb_tune_load", C.c_int64, C.c_char_p)
+nb_tune_entries = _sig("nb_tune_entries", C.c_int64)
+nb_pair_shape = _sig("nb_pair_shape", C.c_int, _ctxp, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                     C.POINTER(C.c_int64))
+nb_tune_clear = _sig("nb_tune_clear", None)
+
+
+def tune_save(path: str):
+    """Write the process-wide table of tuned pair-kernel shapes."""
+    check(nb_tune_save(os.fsencode(path)))
+
+
+def tune_load(path: str) -> int:
+    """Merge a saved table; returns the number of entries read."""
+    return int(check(nb_tune_load(os.fsencode(path))))
+
+
+def tune_entries() -> int:
+    return int(nb_tune_entries())
+
+
+def tune_clear():
+    nb_tune_clear()
 
 
 def measure_peaks(device: int = 0) -> dict:
@@ -253,6 +284,19 @@ class Context:
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
         check(nb_set_precision(self._h, int(precision)))
+
+    def tune(self, reps: int = 3) -> dict:
+        """Time every compiled pair-kernel shape on the loaded state and keep
+        the fastest (``nb_tune``)."""
+        t = TuneT()
+        check(nb_tune(self._h, int(reps), C.byref(t)))
+        return {k: getattr(t, k) for k, _ in TuneT._fields_}
+
+    def pair_shape(self) -> dict:
+        """Bodies per thread, blocks per SM and grid of the current plan."""
+        i, b, g = C.c_int(), C.c_int(), C.c_int64()
+        check(nb_pair_shape(self._h, C.byref(i), C.byref(b), C.byref(g)))
+        return {"bodies_per_thread": i.value, "blocks_per_sm": b.value, "grid": g.value}
 
     def prof_enable(self, on: bool = True):
         check(nb_prof_enable(self._h, int(bool(on))))

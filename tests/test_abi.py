@@ -80,3 +80,34 @@ def test_oracle_is_not_on_the_product_path():
         if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
             assert "oracle" not in open(f).read().replace("Oracle", "").lower() or \
                 f.endswith("ics.py"), f
+
+
+def test_tuning_table_files_without_gpu(lib, tmp_path):
+    """The tuned-shape table round-trips through its text file; malformed
+    files and shapes this build lacks are rejected and merge nothing."""
+    from paper_1003_3896_gb300 import nbsym
+    nbsym.tune_clear()
+    assert nbsym.tune_entries() == 0
+    good = tmp_path / "good.txt"
+    good.write_text("nbsym-tune 1\n152 1 1 65536 512 4 6\n152 0 512 1289617 64 1 8\n")
+    assert nbsym.tune_load(str(good)) == 2
+    assert nbsym.tune_entries() == 2
+    out = tmp_path / "out.txt"
+    nbsym.tune_save(str(out))
+    lines = [ln for ln in out.read_text().splitlines() if ln]
+    assert lines[0] == "nbsym-tune 1" and len(lines) == 3
+    nbsym.tune_clear()
+    assert nbsym.tune_load(str(out)) == 2
+    nbsym.tune_clear()
+    bad = tmp_path / "bad.txt"
+    for text in ("nbsym-tune 1\n152 1 1 65536 512 3 6\n",   # no kernel with 3 bodies/thread
+                 "nbsym-tune 1\n152 1 1 65536\n",            # truncated entry
+                 "nbsym-tune 2\n",                            # unknown version
+                 "garbage\n"):
+        bad.write_text(text)
+        assert nbsym.nb_tune_load(os.fsencode(str(bad))) == nbsym.NB_EINVAL
+        assert nbsym.tune_entries() == 0
+    assert nbsym.nb_tune_load(None) == nbsym.NB_EINVAL
+    assert nbsym.nb_tune_save(None) == nbsym.NB_EINVAL
+    assert nbsym.nb_tune(None, 2, None) == nbsym.NB_EINVAL
+    assert nbsym.nb_pair_shape(None, None, None, None) == nbsym.NB_EINVAL

@@ -1,0 +1,114 @@
+"""Autotuner of the pair kernels' launch shape: the tuned plan keeps parity
+with the oracle, is recorded per workload shape and re-applied to new contexts
+of that shape (bit-identical results), for single systems and batches."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1003_3896_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nbs():
+    from paper_1003_3896_gb300 import build
+    build.build()
+    from paper_1003_3896_gb300 import nbsym
+    nbsym.tune_clear()
+    yield nbsym
+    nbsym.tune_clear()
+
+
+def rel_rms(a, ref):
+    return math.sqrt(((a - ref) ** 2).sum() / (ref ** 2).sum())
+
+
+@pytest.mark.parametrize("prec,n,tol", [("ds", 20000, 1e-6), ("fp64", 3000, 1e-12),
+                                        ("fp32", 9000, 1e-4)])
+def test_tuned_plan_keeps_parity_and_is_reused(nbs, orc, prec, n, tol):
+    pos, vel, m = ics.henon_plummer(n, 7)
+    eps = ics.paper_softening(n)
+    ref = orc.accel_int(pos, m, 1.0, eps)
+    with nbs.Context(n, eps=eps, precision=prec) as ctx:
+        ctx.load(pos, vel, m)
+        untuned = ctx.accel()
+        r = ctx.tune(reps=2)
+        assert r["candidates"] >= 2
+        assert r["pair_ms"] > 0 and r["default_ms"] > 0
+        # the planner's own shape is among the candidates
+        assert r["pair_ms"] <= 1.15 * r["default_ms"]
+        shape = ctx.pair_shape()
+        assert shape["bodies_per_thread"] == r["bodies_per_thread"]
+        assert shape["blocks_per_sm"] == r["blocks_per_sm"]
+        assert shape["grid"] == r["grid"]
+        tuned = ctx.accel()
+        assert rel_rms(tuned, ref) < tol
+        assert rel_rms(tuned, untuned) < tol
+        # steps still run on the new plan
+        ctx.step(2, 1.0 / 1024, 2)
+        p, _ = ctx.get_state()
+        assert np.isfinite(p).all()
+    with nbs.Context(n, eps=eps, precision=prec) as ctx2:
+        ctx2.load(pos, vel, m)
+        assert ctx2.pair_shape() == shape
+        assert np.array_equal(ctx2.accel(), tuned)
+
+
+def test_tuned_batch_parity(nbs, orc):
+    sizes = [300, 1000, 129, 2048, 777, 4100, 256, 1]
+    cl = []
+    for k, n in enumerate(sizes):
+        pos, vel, m = ics.henon_plummer(n, 300 + k)
+        cl.append((pos, vel, m, ics.paper_softening(n)))
+    pos = np.concatenate([c[0] for c in cl])
+    vel = np.concatenate([c[1] for c in cl])
+    m = np.concatenate([c[2] for c in cl])
+    with nbs.Context(sizes=sizes, precision="ds") as ctx:
+        ctx.set_cluster_params(eps=[c[3] for c in cl])
+        ctx.load(pos, vel, m)
+        r = ctx.tune(reps=2)
+        assert r["candidates"] >= 2
+        a = ctx.accel()
+    off = 0
+    for (p, _, mk, e), n in zip(cl, sizes):
+        ref = orc.accel_int(p, mk, 1.0, e)
+        got = a[off:off + n]
+        if n > 1:
+            assert rel_rms(got, ref) < 1e-6
+        else:
+            assert np.array_equal(got, np.zeros((1, 3)))
+        off += n
+
+
+def test_saved_table_replays(nbs, tmp_path):
+    n = 5000
+    pos, vel, m = ics.henon_plummer(n, 11)
+    eps = ics.paper_softening(n)
+    nbs.tune_clear()
+    with nbs.Context(n, eps=eps, precision="ds") as ctx:
+        ctx.load(pos, vel, m)
+        ctx.tune(reps=1)
+        shape = ctx.pair_shape()
+        a = ctx.accel()
+    path = str(tmp_path / "tune.txt")
+    nbs.tune_save(path)
+    nbs.tune_clear()
+    assert nbs.tune_entries() == 0
+    assert nbs.tune_load(path) >= 1
+    with nbs.Context(n, eps=eps, precision="ds") as ctx:
+        ctx.load(pos, vel, m)
+        assert ctx.pair_shape() == shape
+        assert np.array_equal(ctx.accel(), a)
+    nbs.tune_clear()
+
+
+def test_tune_needs_loaded_state(nbs):
+    with nbs.Context(100, eps=1e-3, precision="ds") as ctx:
+        assert nbs.nb_tune(ctx.handle, 2, None) == nbs.NB_ESTATE
+        assert nbs.nb_pair_shape(ctx.handle, None, None, None) == nbs.NB_ESTATE
+        pos, vel, m = ics.henon_plummer(100, 1)
+        ctx.load(pos, vel, m)
+        assert nbs.nb_tune(ctx.handle, 0, None) == nbs.NB_EINVAL
+        assert nbs.nb_tune(ctx.handle, 1001, None) == nbs.NB_EINVAL
