@@ -30,7 +30,7 @@
 extern "C" {
 #endif
 
-#define NB_ABI_VERSION 1
+#define NB_ABI_VERSION 2
 
 /* Opaque context: device state of one particle system plus its buffers,
  * stream, captured step graphs and launch configuration.  Library-owned. */
@@ -257,11 +257,12 @@ int nb_accel_static(const nb_params *p, int64_t n, const double *d_pos,
 
 /* ---- autotuner (no counterpart in the paper: the paper fixes one block
  * shape for its GPU, Sect. 3.2) ---------------------------------------------
- * The launch shape of the pair kernel is (bodies per thread I, resident
- * blocks per SM b): I sets the width 128 * I of the i-block that one work
- * unit covers against one 128-body j-tile, b sets the persistent grid
- * (b * SMs blocks, at most half the unit count) and so how finely units are
- * cut into per-block runs.  nb_tune times every shape this build compiled for
+ * The launch shape of the pair kernel is (bodies per thread I, j-tile width
+ * jt, resident blocks per SM b): one work unit is an i-block of 128 * I
+ * bodies against a j-range of jt bodies (128, 64 or 32: narrower ranges give
+ * small clusters enough units to fill the GPU); b sets the persistent grid
+ * (b * SMs blocks, at most the unit count) and so how finely units are cut
+ * into per-block runs.  nb_tune times every shape this build compiled for
  * the context's current precision on its loaded state (reps launches each,
  * CUDA events on the context's stream), switches the context to the fastest
  * and records it in a process-wide table keyed by the workload's shape (SM
@@ -273,6 +274,7 @@ typedef struct {
     int precision;           /* enum nb_precision tuned */
     int bodies_per_thread;   /* chosen I */
     int blocks_per_sm;       /* chosen b */
+    int j_tile;              /* chosen j bodies per unit: 128, 64 or 32 */
     int candidates;          /* shapes timed */
     int64_t grid;            /* persistent blocks of the chosen shape */
     double pair_ms;          /* mean pair-launch time of the chosen shape */
@@ -296,9 +298,10 @@ int nb_tune_save(const char *path);
 int64_t nb_tune_load(const char *path);
 
 /* The pair-kernel shape of the context's current plan: bodies per thread,
- * resident blocks per SM, persistent grid (any out pointer may be NULL).
- * Errors: NB_EINVAL (NULL ctx), NB_ESTATE (nothing loaded yet). */
-int nb_pair_shape(nb_ctx *ctx, int *bodies_per_thread, int *blocks_per_sm, int64_t *grid);
+ * resident blocks per SM, j bodies per unit, persistent grid (any out pointer
+ * may be NULL).  Errors: NB_EINVAL (NULL ctx), NB_ESTATE (nothing loaded). */
+int nb_pair_shape(nb_ctx *ctx, int *bodies_per_thread, int *blocks_per_sm, int *j_tile,
+                  int64_t *grid);
 
 /* Number of entries in the table. */
 int64_t nb_tune_entries(void);

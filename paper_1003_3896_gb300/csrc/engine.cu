@@ -183,8 +183,11 @@ int set_define(ClusterSet &C, int32_t K, const int64_t *boff, const int64_t *nk,
     return NB_OK;
 }
 
-int set_layout(ClusterSet &C, int ipb, cudaStream_t st)
+int set_layout(ClusterSet &C, int ipb, cudaStream_t st, int jt)
 {
+    if (jt < 32 || jt > TILE || TILE % jt != 0)
+        return set_error(NB_EINVAL, "j-range width %d must divide %d and be >= 32", jt, TILE);
+    const int64_t per_tile = TILE / jt;
     const int32_t K = C.K;
     C.ipb = ipb;
     C.ntiles.resize(K);
@@ -199,7 +202,7 @@ int set_layout(ClusterSet &C, int ipb, cudaStream_t st)
         const int64_t nt = (C.nk[k] + TILE - 1) / TILE;
         C.ntiles[k] = (int32_t)nt;
         if (nt > C.max_ntiles) C.max_ntiles = nt;
-        C.uoff[k + 1] = C.uoff[k] + ((C.nk[k] + ipb - 1) / ipb) * nt;
+        C.uoff[k + 1] = C.uoff[k] + ((C.nk[k] + ipb - 1) / ipb) * nt * per_tile;
         C.uoff_pot[k + 1] = C.uoff_pot[k] + nt * nt;
         for (int64_t lo = C.noff[k]; lo < C.noff[k + 1]; lo += SEG_BODIES) {
             C.seg_k.push_back(k);
@@ -297,14 +300,16 @@ int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan
     pl.precision = precision;
     pl.pl.mode = mode_of(precision);
     const int64_t mean = C.n / (C.K > 0 ? C.K : 1);
-    int I, bps = 0;
+    int I, bps = 0, jt = 0;
     PairShape tuned;
     if (force) {
         I = force->I;
         bps = force->blocks_per_sm;
+        jt = force->jt;
     } else if (use_table && tune_lookup(tune_key(P, C, precision), &tuned)) {
         I = tuned.I;
         bps = tuned.blocks_per_sm;
+        jt = tuned.jt;
     } else if (pl.pl.mode == PM_FP64) {
         I = 1;
     } else if (mean < 16384) {
@@ -318,15 +323,24 @@ int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan
         return set_error(NB_EINVAL, "no pair kernel with %d bodies per thread for this precision",
                          I);
     pl.pl.I = I;
-    int rc = set_layout(C, TILE * I, st);
-    if (rc) return rc;
     const int occ = pair_occupancy(pl.pl.mode, I);
     pl.pl.blocks_per_sm = bps > 0 && bps < occ ? bps : occ;
     if (pl.pl.blocks_per_sm < 1) pl.pl.blocks_per_sm = 1;
+    const int64_t want = (int64_t)P.num_sms * pl.pl.blocks_per_sm;
+    if (jt == 0) {
+        // full-width j-tiles, halved while the units are too few to give
+        // every resident block one (small clusters)
+        int64_t w_full = 0;
+        for (int32_t k = 0; k < C.K; ++k)
+            w_full += ((C.nk[k] + TILE * I - 1) / (TILE * I)) * ((C.nk[k] + TILE - 1) / TILE);
+        jt = TILE;
+        while (jt > 32 && w_full * (TILE / jt) < want) jt /= 2;
+    }
+    int rc = set_layout(C, TILE * I, st, jt);
+    if (rc) return rc;
     const int64_t W = C.uoff[C.K];
-    int64_t G = (int64_t)P.num_sms * pl.pl.blocks_per_sm;
-    if (W / 2 < G) G = W / 2 > 0 ? W / 2 : 1;   // at least two units per block
-    pl.pl.d = make_decomp(W, C.max_ntiles, TILE * I, G, P.s.part_slots);
+    int64_t G = want < W ? want : W;   // at least one unit per block
+    pl.pl.d = make_decomp(W, C.max_ntiles, TILE * I, G, P.s.part_slots, jt);
     for (int32_t k = 0; k < C.K; ++k)
         if (C.eps2d[k] == 0.0) pl.pl.d.mask_self = 1;
     int occ_pot = pair_occupancy(PM_FP64, 1);

@@ -67,9 +67,10 @@ void set_destroy(ClusterSet &C);
 // eps[k] and step scale dts[k] (NULL: 1).  Host only; set_layout uploads.
 int set_define(ClusterSet &C, int32_t K, const int64_t *boff, const int64_t *nk,
                const double *eps, const double *dts);
-// Count pair units for i-blocks of ipb bodies, build reduction segments and
-// upload every table (stream-ordered).
-int set_layout(ClusterSet &C, int ipb, cudaStream_t st);
+// Count pair units for i-blocks of ipb bodies and j-ranges of jt bodies (a
+// divisor of TILE), build reduction segments and upload every table
+// (stream-ordered).
+int set_layout(ClusterSet &C, int ipb, cudaStream_t st, int jt = TILE);
 
 struct Plan {
     int precision = -1;
@@ -77,11 +78,13 @@ struct Plan {
     Decomp pot{};
 };
 // Launch shape of the pair kernel: I bodies per thread (i-block width
-// TILE * I) and blocks_per_sm resident blocks (grid = blocks_per_sm * SMs,
-// at most half the unit count).
+// TILE * I), jt j bodies per unit (TILE, TILE / 2 or TILE / 4) and
+// blocks_per_sm resident blocks (grid = blocks_per_sm * SMs, at most the
+// unit count).
 struct PairShape {
     int I = 0;
     int blocks_per_sm = 0;
+    int jt = 0;   // 0: chosen by the planner
 };
 // Choose the pair kernel variant and decompositions for a cluster set and
 // lay the set out for it.  The shape is `force` when given, else the tuned

@@ -111,15 +111,18 @@ struct DevState {
 };
 
 // Persistent ("stream-K") decomposition of the pair work of a cluster set.
-// A unit is (cluster k, i-block b, j-tile t); units are numbered cluster by
-// cluster, u = uoff[k] + b * ntiles[k] + t, W units in all.  Persistent block
-// g owns the contiguous units [U(g), U(g+1)), U(g) = floor(g W / G); every
-// unit is TILE x TILE*I pairs, so blocks get equal work whatever the cluster
-// sizes.  Each (cluster, i-block, block g) segment writes its own partial
+// A unit is (cluster k, i-block b, j-range t of jt bodies); units are
+// numbered cluster by cluster, u = uoff[k] + b * units_per_iblock(ntiles[k])
+// + t, W units in all.  Persistent block g owns the contiguous units
+// [U(g), U(g+1)), U(g) = floor(g W / G); every unit is jt x TILE*I pairs, so
+// blocks get equal work whatever the cluster sizes.  Each (cluster, i-block, block g) segment writes its own partial
 // slot g - gfirst; consumers add an i-block's slots in slot order, so results
 // do not depend on timing.
 struct Decomp {
     int32_t ipb = TILE;   // bodies per i-block = TILE * I
+    // j bodies per unit: TILE or a divisor of it down to 32 (finer units give
+    // small clusters enough of them to fill the GPU)
+    int32_t jt = TILE;
     int64_t W = 0;        // total units
     int64_t G = 1;        // persistent blocks (grid size), 1 <= G <= W
     int64_t slots = 1;    // max partial slots any i-block needs
@@ -131,6 +134,11 @@ struct Decomp {
     __host__ __device__ int64_t U(int64_t g) const { return (g * W) / G; }
     // largest g with U(g) <= u
     __host__ __device__ int64_t owner(int64_t u) const { return ((u + 1) * G + W - 1) / W - 1; }
+    // units per i-block of a cluster of ntiles TILE-wide j-tiles
+    __host__ __device__ int64_t units_per_iblock(int64_t ntiles) const
+    {
+        return ntiles * (TILE / jt);
+    }
 };
 
 // Partial slots of the i-block holding linear body t of cluster k, and the
@@ -139,7 +147,7 @@ __device__ __forceinline__ void iblock_slots(const Decomp &d, const Clusters &c,
                                              int64_t li, int64_t &first, int64_t &count)
 {
     const int64_t b = li / d.ipb;
-    const int64_t nt = c.ntiles[k];
+    const int64_t nt = d.units_per_iblock(c.ntiles[k]);
     const int64_t u0 = c.uoff[k] + b * nt;
     first = d.owner(u0);
     count = d.owner(u0 + nt - 1) - first + 1;
@@ -181,7 +189,8 @@ int pair_occupancy(int mode, int I);
 bool pair_variant_exists(int mode, int I);
 // Decomposition of the pair work of clusters with host-side sizes nk and
 // tiles, given units per cluster (host arrays), i-block width, target grid.
-Decomp make_decomp(int64_t W, int64_t max_ntiles, int ipb, int64_t G, int64_t slot_cap);
+Decomp make_decomp(int64_t W, int64_t max_ntiles, int ipb, int64_t G, int64_t slot_cap,
+                   int jt = TILE);
 cudaError_t launch_pair(const DevState &s, const PairLaunch &pl, const HostTab &ht, double G,
                         cudaStream_t st);
 // Potential sums phi_i = sum_{j != i} m_j / sqrt(r^2 + eps^2) (FP64) into

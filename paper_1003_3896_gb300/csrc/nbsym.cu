@@ -584,6 +584,7 @@ int nb_tune(nb_ctx *c, int reps, nb_tune_t *out)
         out->precision = rep.precision;
         out->bodies_per_thread = rep.shape.I;
         out->blocks_per_sm = rep.shape.blocks_per_sm;
+        out->j_tile = rep.shape.jt;
         out->candidates = rep.candidates;
         out->grid = rep.grid;
         out->pair_ms = rep.pair_ms;
@@ -592,12 +593,14 @@ int nb_tune(nb_ctx *c, int reps, nb_tune_t *out)
     return NB_OK;
 }
 
-int nb_pair_shape(nb_ctx *c, int *bodies_per_thread, int *blocks_per_sm, int64_t *grid)
+int nb_pair_shape(nb_ctx *c, int *bodies_per_thread, int *blocks_per_sm, int *j_tile,
+                  int64_t *grid)
 {
     if (!c) return set_error(NB_EINVAL, "ctx is NULL");
     if (c->n == 0 || !c->planned) return set_error(NB_ESTATE, "nothing loaded");
     if (bodies_per_thread) *bodies_per_thread = c->plan.pl.I;
     if (blocks_per_sm) *blocks_per_sm = c->plan.pl.blocks_per_sm;
+    if (j_tile) *j_tile = c->plan.pl.d.jt;
     if (grid) *grid = c->plan.pl.d.G;
     return NB_OK;
 }

@@ -34,16 +34,18 @@
 
 namespace nb {
 
-Decomp make_decomp(int64_t W, int64_t max_ntiles, int ipb, int64_t G, int64_t slot_cap)
+Decomp make_decomp(int64_t W, int64_t max_ntiles, int ipb, int64_t G, int64_t slot_cap, int jt)
 {
     Decomp d;
     d.ipb = ipb;
+    d.jt = jt;
+    const int64_t max_units = d.units_per_iblock(max_ntiles);
     d.W = W > 0 ? W : 1;
     if (G > d.W) G = d.W;
     if (G < 1) G = 1;
     for (;;) {
         d.G = G;
-        d.slots = (max_ntiles * G + d.W - 1) / d.W + 1;
+        d.slots = (max_units * G + d.W - 1) / d.W + 1;
         if (d.slots <= slot_cap || G == 1) break;
         G = G - G / 8 - 1;
         if (G < 1) G = 1;
@@ -111,7 +113,7 @@ __device__ __forceinline__ Segment segment_at(const Decomp &d, const ParamTab<KC
     Segment s;
     s.k = KC == 1 ? 0 : find_in(t.uoff, t.K, u);
     const int64_t u0 = t.uoff[s.k];
-    const int32_t nt = t.ntiles[s.k];
+    const int32_t nt = (int32_t)d.units_per_iblock(t.ntiles[s.k]);
     const int64_t lu = u - u0;
     s.b = (int32_t)(lu / nt);
     s.t0 = (int32_t)(lu - (int64_t)s.b * nt);
@@ -129,7 +131,7 @@ __device__ __forceinline__ Segment segment_at(const Decomp &d, const Clusters &c
     Segment s;
     s.k = find_cluster(c.uoff, c.K, u);
     const int64_t u0 = c.uoff[s.k];
-    const int32_t nt = c.ntiles[s.k];
+    const int32_t nt = (int32_t)d.units_per_iblock(c.ntiles[s.k]);
     const int64_t lu = u - u0;
     s.b = (int32_t)(lu / nt);
     s.t0 = (int32_t)(lu - (int64_t)s.b * nt);
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
 #pragma unroll
         for (int r = 0; r < 6 * I; ++r) acc_sh[r][tid] = 0.f;
 
-        const int J0 = sg.t0 * TILE, J1 = sg.t1 * TILE;
+        const int J0 = sg.t0 * d.jt, J1 = sg.t1 * d.jt;
         float4 pf[4];
         {
             const int j = J0 + lane;
@@ -300,8 +302,9 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
             else
                 chunk_pass<P, MODE, false>(cb, jc, ibase, ip, eps2);
             __syncwarp();
-            if (((jc + CH - J0) & (TILE - 1)) == 0) {
-                // end of a 128-j tile: fold the tile sums into the running sums
+            if (((jc + CH - J0) & (TILE - 1)) == 0 || jc + CH >= J1) {
+                // every TILE j and at the segment's end: fold the tile sums
+                // into the running sums
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
 #pragma unroll
@@ -344,8 +347,9 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
 }
 
 // Double-precision pair kernel: the plain FP64 baseline (Sect. 3.2's DP mode
-// with structures of four doubles).  A j-tile of TILE bodies is staged in
-// shared memory per block and broadcast to one i body per thread.  With POT
+// with structures of four doubles).  The block's j-range is staged through
+// shared memory up to TILE bodies at a time and broadcast to the threads'
+// i bodies.  With POT
 // it sums the softened potential m_j / sqrt(r^2 + eps^2) of eq. 4 instead
 // (j = i always excluded), for the energy diagnostic.
 template <int I, bool POT>
@@ -379,23 +383,26 @@ __global__ void __launch_bounds__(TILE) pair_fp64_kernel(
             zi[k] = z[ic];
             ax[k] = ay[k] = az[k] = 0.0;
         }
-        for (int t = sg.t0; t < sg.t1; ++t) {
-            const int jglob = t * TILE;
+        const int J0 = sg.t0 * d.jt, J1 = sg.t1 * d.jt;
+        for (int jglob = J0; jglob < J1; jglob += TILE) {
+            const int w = J1 - jglob < TILE ? J1 - jglob : TILE;   // j bodies staged
             const int j = jglob + tid;
             __syncthreads();
-            if (j < n) {
-                sx[tid] = x[base + j];
-                sy[tid] = y[base + j];
-                sz[tid] = z[base + j];
-                sm[tid] = m[base + j];
-            } else {
-                sx[tid] = sy[tid] = sz[tid] = FAR_D;
-                sm[tid] = 0.0;
+            if (tid < w) {
+                if (j < n) {
+                    sx[tid] = x[base + j];
+                    sy[tid] = y[base + j];
+                    sz[tid] = z[base + j];
+                    sm[tid] = m[base + j];
+                } else {
+                    sx[tid] = sy[tid] = sz[tid] = FAR_D;
+                    sm[tid] = 0.0;
+                }
             }
             __syncthreads();
-            const bool diag = mask_self && jglob < ib0 + d.ipb && jglob + TILE > ib0;
+            const bool diag = mask_self && jglob < ib0 + d.ipb && jglob + w > ib0;
 #pragma unroll 2
-            for (int jj = 0; jj < TILE; ++jj) {
+            for (int jj = 0; jj < w; ++jj) {
                 const double xj = sx[jj], yj = sy[jj], zj = sz[jj], mj = sm[jj];
 #pragma unroll
                 for (int k = 0; k < I; ++k) {

@@ -1,15 +1,15 @@
 // tune.cu -- autotuner of the pair kernels' launch shape.
 //
-// The shape of one pair-force launch is (I, b): I bodies per thread, which
-// sets the width TILE * I of the i-block a work unit covers (the unit is that
-// i-block against one TILE-wide j-tile), and b resident blocks per SM, which
-// sets the persistent grid G = b * SMs (at most half the unit count) and so
-// how finely the (i-block, j-tile) units are cut into per-block runs.  The
-// best shape depends on the arithmetic (registers per thread), on N (small
-// clusters need more, smaller units to fill 152 SMs) and on the cluster mix of
-// a batch, so it is measured rather than modelled: every variant the library
-// has compiled is timed on the loaded state with CUDA events and the fastest
-// is kept.
+// The shape of one pair-force launch is (I, jt, b): I bodies per thread,
+// which sets the width TILE * I of the i-block a work unit covers; jt, the
+// j bodies of a unit (TILE, TILE / 2 or TILE / 4), which sets how many units
+// a small cluster has; and b resident blocks per SM, which sets the persistent
+// grid G = b * SMs (at most the unit count) and so how finely the units are
+// cut into per-block runs.  The best shape depends on the arithmetic
+// (registers per thread), on N (small clusters need more, smaller units to
+// fill 152 SMs) and on the cluster mix of a batch, so it is measured rather
+// than modelled: every variant the library has compiled is timed on the
+// loaded state with CUDA events and the fastest is kept.
 //
 // Choices are remembered process-wide per workload shape (SM count,
 // precision, cluster count, bodies, widest cluster in tiles), so every
@@ -37,7 +37,8 @@ Key key_of(const TuneKey &k) { return Key(k.sms, k.precision, k.K, k.n, k.max_nt
 
 bool shape_valid(int precision, const PairShape &s)
 {
-    return s.I > 0 && s.blocks_per_sm > 0 && pair_variant_exists(mode_of(precision), s.I);
+    return s.I > 0 && s.blocks_per_sm > 0 && s.jt >= 32 && s.jt <= TILE && TILE % s.jt == 0 &&
+           pair_variant_exists(mode_of(precision), s.I);
 }
 
 }  // namespace
@@ -85,12 +86,12 @@ int tune_save(const char *path)
     std::lock_guard<std::mutex> lk(g_mu);
     FILE *f = std::fopen(path, "w");
     if (!f) return set_error(NB_EINVAL, "cannot open %s for writing", path);
-    std::fprintf(f, "nbsym-tune 1\n");
+    std::fprintf(f, "nbsym-tune 2\n");
     for (const auto &e : g_table) {
         const Key &k = e.first;
-        std::fprintf(f, "%d %d %d %lld %lld %d %d\n", std::get<0>(k), std::get<1>(k),
+        std::fprintf(f, "%d %d %d %lld %lld %d %d %d\n", std::get<0>(k), std::get<1>(k),
                      (int)std::get<2>(k), (long long)std::get<3>(k), (long long)std::get<4>(k),
-                     e.second.I, e.second.blocks_per_sm);
+                     e.second.I, e.second.jt, e.second.blocks_per_sm);
     }
     const bool ok = std::fclose(f) == 0;
     return ok ? NB_OK : set_error(NB_EINVAL, "writing %s failed", path);
@@ -101,23 +102,24 @@ int tune_load(const char *path, int64_t *loaded)
     FILE *f = std::fopen(path, "r");
     if (!f) return set_error(NB_EINVAL, "cannot open %s", path);
     int version = 0;
-    if (std::fscanf(f, "nbsym-tune %d", &version) != 1 || version != 1) {
+    if (std::fscanf(f, "nbsym-tune %d", &version) != 1 || version != 2) {
         std::fclose(f);
-        return set_error(NB_EINVAL, "%s is not a tuning file of version 1", path);
+        return set_error(NB_EINVAL, "%s is not a tuning file of version 2", path);
     }
     int64_t count = 0;
-    int sms, prec, K, I, b;
+    int sms, prec, K, I, jt, b;
     long long n, mt;
     std::map<Key, PairShape> add;
     for (;;) {
-        const int r = std::fscanf(f, "%d %d %d %lld %lld %d %d", &sms, &prec, &K, &n, &mt, &I, &b);
+        const int r =
+            std::fscanf(f, "%d %d %d %lld %lld %d %d %d", &sms, &prec, &K, &n, &mt, &I, &jt, &b);
         if (r == EOF) break;
-        if (r != 7 || sms <= 0 || prec < NB_FP64 || prec > NB_DS_FULL || K <= 0 || n <= 0 ||
+        if (r != 8 || sms <= 0 || prec < NB_FP64 || prec > NB_DS_FULL || K <= 0 || n <= 0 ||
             mt <= 0) {
             std::fclose(f);
             return set_error(NB_EINVAL, "%s: malformed entry %lld", path, (long long)count + 1);
         }
-        PairShape s{I, b};
+        PairShape s{I, b, jt};
         if (!shape_valid(prec, s)) {
             std::fclose(f);
             return set_error(NB_EINVAL, "%s: entry %lld names a shape this build lacks", path,
@@ -171,9 +173,9 @@ int tune_pair(const Pool &P, ClusterSet &C, int precision, const Phys &ph, cudaS
     int rc = NB_OK;
     rep = TuneReport();
     rep.precision = precision;
-    PairShape best{0, 0};
+    PairShape best{0, 0, 0};
     double best_ms = 0;
-    std::vector<int64_t> seen;   // (I, G) pairs already timed
+    std::vector<int64_t> seen;   // (I, grid, jt) already timed
     do {
         // the shape the planner would pick without a tuned entry
         Plan def;
@@ -185,12 +187,18 @@ int tune_pair(const Pool &P, ClusterSet &C, int precision, const Phys &ph, cudaS
         for (int I : Is) {
             if (!pair_variant_exists(mode, I)) continue;
             const int occ = pair_occupancy(mode, I);
+            // finer j-ranges only pay when full-width units are scarce
+            int64_t w_full = 0;
+            for (int32_t k = 0; k < C.K; ++k)
+                w_full += ((C.nk[k] + TILE * I - 1) / (TILE * I)) * ((C.nk[k] + TILE - 1) / TILE);
+            const bool scarce = w_full < 2 * (int64_t)P.num_sms * occ;
+            for (int jt = TILE; rc == NB_OK && jt >= (scarce ? 32 : TILE); jt /= 2)
             for (int b = occ; b >= 1 && b > occ - 4; --b) {
-                const PairShape s{I, b};
+                const PairShape s{I, b, jt};
                 Plan pl;
                 rc = plan_make(P, C, precision, st, pl, &s, false);
                 if (rc) break;
-                const int64_t tag = pl.pl.d.G * 16 + I;
+                const int64_t tag = (pl.pl.d.G * 16 + I) * 256 + jt;
                 bool dup = false;
                 for (int64_t v : seen) dup = dup || v == tag;
                 if (dup) continue;

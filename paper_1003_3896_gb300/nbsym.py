@@ -52,7 +52,8 @@ class PeaksT(C.Structure):
 
 class TuneT(C.Structure):
     _fields_ = [("precision", C.c_int), ("bodies_per_thread", C.c_int),
-                ("blocks_per_sm", C.c_int), ("candidates", C.c_int), ("grid", C.c_int64),
+                ("blocks_per_sm", C.c_int), ("j_tile", C.c_int), ("candidates", C.c_int),
+                ("grid", C.c_int64),
                 ("pair_ms", C.c_double), ("default_ms", C.c_double)]
 
 
@@ -98,7 +99,7 @@ nb_tune_save = _sig("nb_tune_save", C.c_int, C.c_char_p)
 nb_tune_load = _sig("nb_tune_load", C.c_int64, C.c_char_p)
 nb_tune_entries = _sig("nb_tune_entries", C.c_int64)
 nb_pair_shape = _sig("nb_pair_shape", C.c_int, _ctxp, C.POINTER(C.c_int), C.POINTER(C.c_int),
-                     C.POINTER(C.c_int64))
+                     C.POINTER(C.c_int), C.POINTER(C.c_int64))
 nb_tune_clear = _sig("nb_tune_clear", None)
 
 
@@ -294,9 +295,10 @@ class Context:
 
     def pair_shape(self) -> dict:
         """Bodies per thread, blocks per SM and grid of the current plan."""
-        i, b, g = C.c_int(), C.c_int(), C.c_int64()
-        check(nb_pair_shape(self._h, C.byref(i), C.byref(b), C.byref(g)))
-        return {"bodies_per_thread": i.value, "blocks_per_sm": b.value, "grid": g.value}
+        i, b, j, g = C.c_int(), C.c_int(), C.c_int(), C.c_int64()
+        check(nb_pair_shape(self._h, C.byref(i), C.byref(b), C.byref(j), C.byref(g)))
+        return {"bodies_per_thread": i.value, "blocks_per_sm": b.value, "j_tile": j.value,
+                "grid": g.value}
 
     def prof_enable(self, on: bool = True):
         check(nb_prof_enable(self._h, int(bool(on))))

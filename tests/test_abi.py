@@ -42,7 +42,7 @@ def test_every_declared_symbol_exported(lib):
 
 def test_abi_version_and_defaults(lib):
     from paper_1003_3896_gb300 import nbsym
-    assert nbsym.nb_abi_version() == 1
+    assert nbsym.nb_abi_version() == 2
     p = nbsym.Params()
     nbsym.nb_params_default(C.byref(p))
     assert p.G == 1.0 and p.eps == 0.0 and p.precision == nbsym.NB_DS
@@ -89,20 +89,21 @@ def test_tuning_table_files_without_gpu(lib, tmp_path):
     nbsym.tune_clear()
     assert nbsym.tune_entries() == 0
     good = tmp_path / "good.txt"
-    good.write_text("nbsym-tune 1\n152 1 1 65536 512 4 6\n152 0 512 1289617 64 1 8\n")
+    good.write_text("nbsym-tune 2\n152 1 1 65536 512 4 128 6\n152 0 512 1289617 64 1 32 8\n")
     assert nbsym.tune_load(str(good)) == 2
     assert nbsym.tune_entries() == 2
     out = tmp_path / "out.txt"
     nbsym.tune_save(str(out))
     lines = [ln for ln in out.read_text().splitlines() if ln]
-    assert lines[0] == "nbsym-tune 1" and len(lines) == 3
+    assert lines[0] == "nbsym-tune 2" and len(lines) == 3
     nbsym.tune_clear()
     assert nbsym.tune_load(str(out)) == 2
     nbsym.tune_clear()
     bad = tmp_path / "bad.txt"
-    for text in ("nbsym-tune 1\n152 1 1 65536 512 3 6\n",   # no kernel with 3 bodies/thread
-                 "nbsym-tune 1\n152 1 1 65536\n",            # truncated entry
-                 "nbsym-tune 2\n",                            # unknown version
+    for text in ("nbsym-tune 2\n152 1 1 65536 512 3 128 6\n",  # no kernel with I = 3
+                 "nbsym-tune 2\n152 1 1 65536 512 4 48 6\n",   # j-tile must divide 128
+                 "nbsym-tune 2\n152 1 1 65536\n",              # truncated entry
+                 "nbsym-tune 1\n",                              # unknown version
                  "garbage\n"):
         bad.write_text(text)
         assert nbsym.nb_tune_load(os.fsencode(str(bad))) == nbsym.NB_EINVAL
@@ -110,4 +111,4 @@ def test_tuning_table_files_without_gpu(lib, tmp_path):
     assert nbsym.nb_tune_load(None) == nbsym.NB_EINVAL
     assert nbsym.nb_tune_save(None) == nbsym.NB_EINVAL
     assert nbsym.nb_tune(None, 2, None) == nbsym.NB_EINVAL
-    assert nbsym.nb_pair_shape(None, None, None, None) == nbsym.NB_EINVAL
+    assert nbsym.nb_pair_shape(None, None, None, None, None) == nbsym.NB_EINVAL

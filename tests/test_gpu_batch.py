@@ -70,7 +70,10 @@ def test_batch_accel_matches_oracle_and_alone(nbs, orc, prec):
 @pytest.mark.parametrize("prec", ["fp64", "ds"])
 def test_batch_steps_equal_alone_runs(nbs, orc, prec):
     """Four SI6A steps of the whole ensemble with per-cluster softening and
-    per-cluster step scale against each cluster stepped alone."""
+    per-cluster step scale against each cluster stepped alone.  A cluster
+    alone may get a different launch shape (narrower j-ranges for small N),
+    which moves where per-tile float sums are cut, so the mixed-precision bar
+    is its stated tolerance (positions after 4 steps 1e-6), not bit equality."""
     cl = clusters(SIZES, base_seed=200)
     pos, vel, m = concat(cl)
     eps = [c[3] for c in cl]
@@ -83,7 +86,7 @@ def test_batch_steps_equal_alone_runs(nbs, orc, prec):
         b.step(6, dt, 4)
         x, v = b.get_state()
     off = 0
-    tol = 1e-12 if prec == "fp64" else 1e-8
+    tol = 1e-12 if prec == "fp64" else 1e-6
     for k, ((p, vv, mm, e), n) in enumerate(zip(cl, SIZES)):
         with nbs.Context(n, eps=e, precision=prec) as c:
             c.load(p, vv, mm)

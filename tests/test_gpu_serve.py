@@ -55,7 +55,10 @@ def test_each_result_same_alone_and_in_mix(nbs):
             c.load(pos, vel, m)
             c.step(order, dt, steps)
             xa, va = c.get_state()
-        tol = 1e-12 if prec == "fp64" else 1e-8
+        # alone, a small job may get a different launch shape (narrower
+        # j-ranges), which moves where per-tile float sums are cut: the mixed
+        # bar is its stated tolerance, FP64 agrees to rounding
+        tol = 1e-12 if prec == "fp64" else 1e-6
         assert np.abs(x - xa).max() <= tol, (k, np.abs(x - xa).max())
         assert np.abs(v - va).max() <= 10 * tol
 

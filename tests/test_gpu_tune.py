@@ -42,6 +42,7 @@ def test_tuned_plan_keeps_parity_and_is_reused(nbs, orc, prec, n, tol):
         shape = ctx.pair_shape()
         assert shape["bodies_per_thread"] == r["bodies_per_thread"]
         assert shape["blocks_per_sm"] == r["blocks_per_sm"]
+        assert shape["j_tile"] == r["j_tile"]
         assert shape["grid"] == r["grid"]
         tuned = ctx.accel()
         assert rel_rms(tuned, ref) < tol
@@ -107,7 +108,7 @@ def test_saved_table_replays(nbs, tmp_path):
 def test_tune_needs_loaded_state(nbs):
     with nbs.Context(100, eps=1e-3, precision="ds") as ctx:
         assert nbs.nb_tune(ctx.handle, 2, None) == nbs.NB_ESTATE
-        assert nbs.nb_pair_shape(ctx.handle, None, None, None) == nbs.NB_ESTATE
+        assert nbs.nb_pair_shape(ctx.handle, None, None, None, None) == nbs.NB_ESTATE
         pos, vel, m = ics.henon_plummer(100, 1)
         ctx.load(pos, vel, m)
         assert nbs.nb_tune(ctx.handle, 0, None) == nbs.NB_EINVAL
