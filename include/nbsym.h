@@ -43,7 +43,10 @@ typedef struct nb_ctx nb_ctx;
  *             coordinate difference of close pairs re-formed from
  *             double-single (hi + lo) coordinates, per-tile sums folded
  *             into double-single accumulators (the paper's software
- *             double-single idea, Sect. 4.2).
+ *             double-single idea, Sect. 4.2).  On small sets (sum of N_k^2
+ *             at most 2^27, e.g. one cluster of N <= 11585) the close-pair
+ *             pass costs more than forming the double-single difference for
+ *             every pair, so NB_DS then evaluates as NB_DS_FULL.
  *  NB_FP32 -- pure single precision: coordinates rounded to float
  *             (relative to the same reference point), float accumulation.
  *  NB_DS_FULL -- as NB_DS but the double-single coordinate difference is

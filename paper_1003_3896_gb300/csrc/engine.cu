@@ -298,7 +298,7 @@ int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan
 {
     Plan pl;
     pl.precision = precision;
-    pl.pl.mode = mode_of(precision);
+    pl.pl.mode = plan_mode(C, precision);
     const int64_t mean = C.n / (C.K > 0 ? C.K : 1);
     int I, bps = 0, jt = 0;
     PairShape tuned;
@@ -306,7 +306,8 @@ int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan
         I = force->I;
         bps = force->blocks_per_sm;
         jt = force->jt;
-    } else if (use_table && tune_lookup(tune_key(P, C, precision), &tuned)) {
+    } else if (use_table && tune_lookup(tune_key(P, C, precision), &tuned) &&
+               pair_variant_exists(pl.pl.mode, tuned.I)) {
         I = tuned.I;
         bps = tuned.blocks_per_sm;
         jt = tuned.jt;
@@ -353,6 +354,22 @@ int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan
     return NB_OK;
 }
 
+int plan_mode(const ClusterSet &C, int precision)
+{
+    const int m = mode_of(precision);
+    if (m != PM_DS_NEAR) return m;
+    double pairs = 0;
+    for (int32_t k = 0; k < C.K; ++k) pairs += (double)C.nk[k] * (double)C.nk[k];
+    return pairs <= DS_FULL_MAX_PAIRS ? PM_DS_FULL : PM_DS_NEAR;
+}
+
+DevState view(const Pool &P, const ClusterSet &C, const Plan &pl)
+{
+    DevState s = view(P, C, (int)pl.precision);
+    if (pl.pl.mode != PM_DS_NEAR) s.corr = nullptr;
+    return s;
+}
+
 DevState view(const Pool &P, const ClusterSet &C, int precision)
 {
     DevState s = P.s;
@@ -393,7 +410,7 @@ int enq_split(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph
               cudaStream_t st, int64_t *kernels)
 {
     if (!float_planes(pl.precision)) return NB_OK;
-    const DevState s = view(P, C, pl.precision);
+    const DevState s = view(P, C, pl);
     NB_TRY(launch_frame(s, ph.near_frac, st));
     NB_TRY(launch_split(s, st));
     count(kernels, 3);
@@ -403,7 +420,7 @@ int enq_split(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph
 int enq_force(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph,
               cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1, int64_t *kernels)
 {
-    const DevState s = view(P, C, pl.precision);
+    const DevState s = view(P, C, pl);
     // inside a stream capture an event record must be an external node to
     // time anything; outside it is a plain record
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -421,7 +438,7 @@ int enq_force(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph
     NB_TRY(launch_pair(s, pl.pl, ht, ph.G, st));
     if (ev1) NB_TRY(cudaEventRecordWithFlags(ev1, st, evf));
     count(kernels, 1);
-    if (pl.precision == NB_DS) {
+    if (pl.pl.mode == PM_DS_NEAR) {
         NB_TRY(launch_near_correct(s, ph.G, st));
         count(kernels, NEAR_KERNELS);
     }
@@ -432,7 +449,7 @@ int enq_step(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph,
              double h, cudaStream_t st, const std::vector<cudaEvent_t> *evs, int64_t *kernels)
 {
     const bool sp = float_planes(pl.precision);
-    const DevState s = view(P, C, pl.precision);
+    const DevState s = view(P, C, pl);
     double wk[7];
     int K;
     if (order == 2) {
@@ -468,7 +485,7 @@ int enq_step(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph,
 int enq_accel_out(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph,
                   double *out, cudaStream_t st, int64_t *kernels)
 {
-    const DevState s = view(P, C, pl.precision);
+    const DevState s = view(P, C, pl);
     NB_TRY(launch_accel_out(s, pl.pl.d, ph.ext, out, st));
     count(kernels, 1);
     return NB_OK;
@@ -477,7 +494,7 @@ int enq_accel_out(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys
 int enq_energy(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph,
                cudaStream_t st, int64_t *kernels)
 {
-    DevState s = view(P, C, pl.precision);
+    DevState s = view(P, C, pl);
     s.cl = C.cl_pot;
     NB_TRY(launch_potential(s, pl.pot, st));
     NB_TRY(launch_energy_reduce(s, pl.pot, ph.ext, ph.G, st));

@@ -125,8 +125,15 @@ struct Phys {
     ExtField ext{};
 };
 
-// Kernel-facing state of a cluster set: the pool arrays with the set's tables.
+// Kernel-facing state of a cluster set: the pool arrays with the set's tables
+// (near-pair correction attached when the precision is NB_DS, or, given a
+// plan, when the plan runs the near-pair pass).
 DevState view(const Pool &P, const ClusterSet &C, int precision);
+DevState view(const Pool &P, const ClusterSet &C, const Plan &pl);
+// Pair-kernel family of a plan: the precision's, except that NB_DS on a set
+// of at most DS_FULL_MAX_PAIRS pairs forms the double-single difference on
+// every pair (no near-pair pass).
+int plan_mode(const ClusterSet &C, int precision);
 int mode_of(int precision);
 bool float_planes(int precision);
 

@@ -177,6 +177,11 @@ struct PairLaunch {
 // addresses then live in uniform registers); larger sets read the device
 // tables of Clusters.
 constexpr int PARAM_CLUSTERS = 512;
+
+// Up to this many pairs per evaluation the mixed mode forms the double-single
+// difference on every pair (PM_DS_FULL) instead of running the near-pair
+// pass, whose fixed launch cost exceeds that extra arithmetic on small sets.
+constexpr double DS_FULL_MAX_PAIRS = 134217728.0;   // 2^27
 struct HostTab {
     int32_t K = 0;
     const int64_t *uoff = nullptr, *boff = nullptr, *nk = nullptr;

@@ -212,7 +212,8 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
         PairLaunch pl;
         pl.mode = p->precision == NB_FP64 ? PM_FP64
                   : p->precision == NB_FP32 ? PM_FP32
-                  : p->precision == NB_DS_FULL ? PM_DS_FULL : PM_DS_NEAR;
+                  : p->precision == NB_DS_FULL ? PM_DS_FULL
+                  : (double)n * (double)n <= DS_FULL_MAX_PAIRS ? PM_DS_FULL : PM_DS_NEAR;
         pl.I = pl.mode == PM_FP64 ? 1 : 2;
         const int ipb = TILE * pl.I;
         pl.blocks_per_sm = pair_occupancy(pl.mode, pl.I);

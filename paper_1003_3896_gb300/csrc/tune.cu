@@ -140,7 +140,7 @@ int tune_load(const char *path, int64_t *loaded)
 static int time_plan(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph,
                      cudaStream_t st, int reps, cudaEvent_t e0, cudaEvent_t e1, double *ms)
 {
-    const DevState s = view(P, C, pl.precision);
+    const DevState s = view(P, C, pl);
     HostTab ht;
     ht.K = C.K;
     ht.uoff = C.uoff.data();
@@ -163,7 +163,7 @@ int tune_pair(const Pool &P, ClusterSet &C, int precision, const Phys &ph, cudaS
               int reps, TuneReport &rep, Plan &out)
 {
     if (reps < 1) reps = 1;
-    const int mode = mode_of(precision);
+    const int mode = plan_mode(C, precision);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     NB_TRY(cudaEventCreate(&e0));
     if (cudaEventCreate(&e1) != cudaSuccess) {

@@ -327,11 +327,13 @@ def test_c3_full_size_sampled(nbs, orc):
 
 
 def test_near_pair_correction_is_what_makes_mixed_accurate(nbs, orc):
-    """Orbit geometry at N = 4099: with the near radius shrunk to nothing the
-    mixed result is the centred-float one (error set by the closest pairs);
-    the default radius brings it under 1e-6; a radius covering every pair
-    re-forms all of them from the double-single difference."""
-    n = 4099
+    """Orbit geometry at N = 12289 (above the size where NB_DS switches to the
+    every-pair double-single difference): with the near radius shrunk to
+    nothing the mixed result is the centred-float one (error set by the
+    closest pairs); the default radius brings it under 1e-6; a radius
+    covering every pair re-forms all of them from the double-single
+    difference."""
+    n = 12289
     pos, vel, m = system(n, seed=29, offset=True)
     eps = ics.paper_softening(n)
     ref = orc.accel(pos, m, ext_params(orc, eps, True))
