@@ -18,6 +18,12 @@ bench.py.  Inputs are seeded and synthetic (paper_1003_3896_gb300.ics).
       {FP64, mixed}, step count log-uniform on [10, 1000] capped at steps_cap;
       a bounded trace of the first ``--jobs`` arrivals; latency includes
       queueing.
+  paper  The paper's own test workload (Sect. 3, Sect. 5.1): a uniform sphere
+      (R = 1, M = 1, virial ratio Q = 0.3) at the sizes of its Table 3,
+      N = 480, 30720 and 1536000, one leapfrog step per precision (FP64 only
+      up to N = 30720: at 1536000 one FP64 evaluation takes over a minute),
+      in GFLOPS at 20 flops per pair beside the single-GPU figures that table
+      reports for its Tesla C1060 (context, other hardware).
 """
 from __future__ import annotations
 
@@ -187,13 +193,55 @@ def c5(args, nbsym, torch):
             "(first jobs, capped N and steps)"}
 
 
+# Table 3 of the paper, one Tesla C1060, leapfrog, GFLOPS at 20 flops per
+# pair: single precision and double precision at N = 480, 30720, 1536000.
+PAPER_TABLE3_SP = {480: 5.97, 30720: 409.0, 1536000: 423.0}
+PAPER_TABLE3_DP = {480: 3.36, 30720: 21.9, 1536000: 22.0}
+
+
+def paper(args, nbsym, torch):
+    eps = ics.paper_softening  # eps = 0.005 R / N^(1/3), R = 1
+    rows = []
+    for n in (480, 30720, 1536000):
+        pos, vel, m = ics.uniform_sphere(n, 0, q_vir=0.3)
+        for prec in ("fp32", "ds", "fp64"):
+            if prec == "fp64" and n > 30720:
+                continue
+            with nbsym.Context(n, eps=eps(n), precision=prec) as c:
+                c.load(pos, vel, m)
+                if not args.no_tune and n <= 30720:
+                    c.tune(reps=3)
+                c.step(2, 5e-4, 1)          # warm-up (graph capture)
+                c.load(pos, vel, m)
+                torch.cuda.synchronize()
+                c.prof_enable(True)
+                t0 = time.perf_counter()
+                c.step(2, 5e-4, 1)
+                torch.cuda.synchronize()
+                wall = time.perf_counter() - t0
+                pr = c.prof_read()
+            pair_rate = n * n / (pr["pair_ms"] * 1e-3)
+            ref = (PAPER_TABLE3_DP if prec == "fp64" else PAPER_TABLE3_SP)[n]
+            rows.append({"n": n, "precision": prec, "step_ms": 1e3 * wall,
+                         "pair_ms": pr["pair_ms"], "gpairs_s": pair_rate / 1e9,
+                         "gflops": 20 * pair_rate / 1e9,
+                         "paper_c1060_gflops": ref,
+                         "paper_table": "Table 3 " + ("DP" if prec == "fp64" else "SP")})
+    best = max(r["gpairs_s"] for r in rows if r["precision"] == "ds")
+    return {"metric": "paper workload series (uniform sphere Q = 0.3, leapfrog)",
+            "unit": UNIT, "value": best, "higher_is_better": True,
+            "workload": "uniform_sphere_Q0.3_N480_30720_1536000_leapfrog_dt5e-4",
+            "rows": rows,
+            "note": "paper figures are context (Tesla C1060, 2010), not targets"}
+
+
 def run(args):
     import torch
     torch.cuda.set_device(0)
     from paper_1003_3896_gb300 import build as nbbuild
     nbbuild.build()
     from paper_1003_3896_gb300 import nbsym
-    fn = {"c1": c1, "c3": c3, "c4": c4, "c5": c5}[args.workload]
+    fn = {"c1": c1, "c3": c3, "c4": c4, "c5": c5, "paper": paper}[args.workload]
     line = fn(args, nbsym, torch)
     line["impl"] = "ours"
     line["data"] = "synthetic"

@@ -36,14 +36,14 @@ extern "C" {
  * stream, captured step graphs and launch configuration.  Library-owned. */
 typedef struct nb_ctx nb_ctx;
 
-/* Arithmetic of the pair-force sum (Sect. 4.2; abstract):
+/* Arithmetic of the pair-force sum (Sect. 5.2; abstract):
  *  NB_FP64 -- all pair arithmetic and accumulation in double precision.
  *  NB_DS   -- mixed: pair arithmetic in single precision on coordinates
  *             taken relative to a reference point near the system, the
  *             coordinate difference of close pairs re-formed from
  *             double-single (hi + lo) coordinates, per-tile sums folded
  *             into double-single accumulators (the paper's software
- *             double-single idea, Sect. 4.2).  On small sets (sum of N_k^2
+ *             double-single idea, Sect. 5.2).  On small sets (sum of N_k^2
  *             at most 2^27, e.g. one cluster of N <= 11585) the close-pair
  *             pass costs more than forming the double-single difference for
  *             every pair, so NB_DS then evaluates as NB_DS_FULL.
@@ -90,7 +90,7 @@ typedef struct {
                           difference; <= 0 selects the default 0.4 */
 } nb_params;
 
-/* Diagnostics of Sect. 4.1 (eq. 9-10 use E and L):
+/* Diagnostics of Sect. 5.1 (eq. 9-10 use E and L):
  *   K = 1/2 sum m v^2,  W = -G sum_{i<j} m_i m_j / sqrt(r_ij^2 + eps^2)
  *   (eq. 4), W_ext = sum m_i Phi(r_i), E = K + W + W_ext,
  *   P = sum m v,  L = sum m r x v.   Always computed in double precision. */
@@ -190,7 +190,7 @@ int nb_accel_device(nb_ctx *ctx, double *d_acc_out);
  * NB_ECUDA. */
 int nb_step(nb_ctx *ctx, int order, double dt, int64_t nsteps);
 
-/* Energy, momentum and angular momentum of the current state (Sect. 4.1),
+/* Energy, momentum and angular momentum of the current state (Sect. 5.1),
  * summed over the clusters of a batch.  Errors: NB_ESTATE, NB_EINVAL,
  * NB_ENONFINITE, NB_ECUDA. */
 int nb_energy(nb_ctx *ctx, nb_energy_t *out);
@@ -227,7 +227,7 @@ int nb_prof_read(nb_ctx *ctx, nb_prof_t *out);
 
 /* Measure the arithmetic peaks the pair kernels are bounded by (the
  * denominators of their plain-ALU roofline; the paper quotes nominal SP/DP
- * peaks, Sect. 3.1): each micro-kernel runs independent FMA / MUFU chains on
+ * peaks, Sect. 4.1): each micro-kernel runs independent FMA / MUFU chains on
  * every SM for a few milliseconds, timed with CUDA events (best of three).
  * Allocates 64 bytes of device memory and a stream for the duration of the
  * call.  Errors: NB_EINVAL (NULL out, bad device), NB_ECUDA. */
@@ -259,7 +259,7 @@ int nb_accel_static(const nb_params *p, int64_t n, const double *d_pos,
                     const double *d_mass, double *d_acc_out);
 
 /* ---- autotuner (no counterpart in the paper: the paper fixes one block
- * shape for its GPU, Sect. 3.2) ---------------------------------------------
+ * shape for its GPU, Sect. 4.2) ---------------------------------------------
  * The launch shape of the pair kernel is (bodies per thread I, j-tile width
  * jt, resident blocks per SM b): one work unit is an i-block of 128 * I
  * bodies against a j-range of jt bodies (128, 64 or 32: narrower ranges give

@@ -179,7 +179,7 @@ void orc_accel(int64_t n, const double *pos, const double *mass,
 }
 
 /*
- * Diagnostics of Sect. 4.1 (eq. 9-10 use E and L):
+ * Diagnostics of Sect. 5.1 (eq. 9-10 use E and L):
  *   out[0] K     = 1/2 sum m_i |v_i|^2
  *   out[1] W     = -G sum_{i<j} m_i m_j / sqrt(|r_ij|^2 + eps^2)   (eq. 4)
  *   out[2] W_ext = sum m_i Phi(r_i)  (0 when the field is off)

@@ -1,8 +1,8 @@
 // integrate.cu -- O(N) kernels over a set of clusters: state layout
 // conversion, the per-cluster float frame and split, the fused kick(+external
 // field)/drift substep of the symplectic schemes (Sect. 3.1), and
-// deterministic per-cluster reductions for the diagnostics of Sect. 4.1.
-// All state arithmetic is double precision (Sect. 3.2: the time advance is
+// deterministic per-cluster reductions for the diagnostics of Sect. 5.1.
+// All state arithmetic is double precision (Sect. 4.2: the time advance is
 // the round-off sensitive part).
 //
 // Per-body kernels run over linear body indices t (cluster after cluster);
@@ -208,7 +208,7 @@ cudaError_t launch_frame(const DevState &s, double near_frac, cudaStream_t st)
 }
 
 // hi = fl32(x - c), lo = fl32((x - c) - hi): the double-single representation
-// of Sect. 4.2, taken relative to the cluster's frame origin.
+// of Sect. 5.2, taken relative to the cluster's frame origin.
 __device__ __forceinline__ void split_one(const DevState &s, const Frame &f, int64_t i,
                                           double x, double y, double z)
 {

@@ -16,7 +16,7 @@ constexpr int TILE = 128;
 constexpr float FAR_F = 1.0e18f;
 constexpr double FAR_D = 1.0e150;
 
-// Reference frame of one cluster's single-precision coordinates (Sect. 4.2's
+// Reference frame of one cluster's single-precision coordinates (Sect. 5.2's
 // "delicate evaluation of coordinate difference"): positions are stored as
 // float hi = fl(x - c) and lo = fl((x - c) - hi).
 struct Frame {

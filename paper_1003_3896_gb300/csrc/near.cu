@@ -3,7 +3,7 @@
 // The mixed pair kernel evaluates every pair in float on coordinates taken
 // relative to the cluster's frame origin c (hi = fl(x - c)).  For pairs
 // closer than the near radius d_th the rounding of hi dominates the error of
-// the coordinate difference (Sect. 4.2's "delicate evaluation of coordinate
+// the coordinate difference (Sect. 5.2's "delicate evaluation of coordinate
 // difference"), so this pass finds them with a spatial grid and adds, per
 // body i,
 //     corr_i = G sum_{j near i, j != i} [ f(d_ij^ds) - f(d_ij^float) ]

@@ -6,12 +6,12 @@
 // gets the same amount of work whatever the cluster sizes are (one cluster,
 // or an ensemble of uneven clusters in one launch).  Each thread owns I
 // i-bodies and keeps their sums in registers; every pair of each cluster's
-// N x N array is evaluated, as in the paper (Sect. 3.2), not N(N-1)/2.
+// N x N array is evaluated, as in the paper (Sect. 4.2), not N(N-1)/2.
 //
 // Single-precision family (one template, three modes):
 //   PM_DS_NEAR  float pair arithmetic on coordinates relative to the cluster's
 //               frame origin, per-tile float sums folded into double-single
-//               accumulators (Sect. 4.2's software double precision); pairs
+//               accumulators (Sect. 5.2's software double precision); pairs
 //               closer than the near radius are re-formed from the
 //               double-single coordinate difference (hi_j - hi_i) +
 //               (lo_j - lo_i) by the separate correction pass of near.cu.
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
     }
 }
 
-// Double-precision pair kernel: the plain FP64 baseline (Sect. 3.2's DP mode
+// Double-precision pair kernel: the plain FP64 baseline (Sect. 4.2's DP mode
 // with structures of four doubles).  The block's j-range is staged through
 // shared memory up to TILE bodies at a time and broadcast to the threads'
 // i bodies.  With POT

@@ -18,7 +18,7 @@ Workloads (all seeded, synthetic):
   the analytic Plummer model means a = 3 pi / 16.
 * ``salpeter_masses``: power-law mass function dN/dm ~ m^{-2.35} on
   [0.1, 100], normalised to total mass M.
-* ``uniform_sphere``: the paper's own test workload (Sect. 3 and Sect. 4.1):
+* ``uniform_sphere``: the paper's own test workload (Sect. 3 and Sect. 5.1):
   positions uniform in a sphere of radius R, velocities isotropic with a
   uniformly distributed modulus, scaled so the expected virial ratio is Q
   (Q = 0.3 in the paper).
@@ -147,7 +147,7 @@ def henon_plummer(n: int, seed: int, masses: np.ndarray | None = None):
 
 def uniform_sphere(n: int, seed: int, q_vir: float = 0.3, radius: float = 1.0,
                    total_mass: float = 1.0):
-    """The paper's test workload (Sect. 3, Sect. 4.1): equal masses m = M/N,
+    """The paper's test workload (Sect. 3, Sect. 5.1): equal masses m = M/N,
     positions uniform inside a sphere of radius R, velocities uniform in
     direction with modulus uniform on [0, v_max].
 
