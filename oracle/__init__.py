@@ -40,13 +40,16 @@ def build(force: bool = False) -> str:
 class _Params(C.Structure):
     _fields_ = [("G", C.c_double), ("eps", C.c_double), ("ext_on", C.c_int),
                 ("Md", C.c_double), ("ad", C.c_double), ("bd", C.c_double),
-                ("Mb", C.c_double), ("ab", C.c_double)]
+                ("Mb", C.c_double), ("ab", C.c_double), ("Mbh", C.c_double),
+                ("eps_bh", C.c_double)]
 
 
 @dataclass
 class Params:
-    """Physical parameters: G, softening eps, and the optional disk + bulge
-    external field (Miyamoto-Nagai M_d, a_d, b_d; Plummer M_b, a_b)."""
+    """Physical parameters: G, softening eps, and the optional external
+    field: Miyamoto-Nagai disk (M_d, a_d, b_d), Plummer bulge (M_b, a_b) and
+    a central point mass M_bh softened by eps_bh (the black hole of Sect. 6.2;
+    0 = none)."""
     G: float = 1.0
     eps: float = 0.0
     ext_on: bool = False
@@ -55,10 +58,12 @@ class Params:
     bd: float = 0.26
     Mb: float = 15.0
     ab: float = 0.7
+    Mbh: float = 0.0
+    eps_bh: float = 0.0
 
     def _c(self) -> _Params:
         return _Params(self.G, self.eps, int(self.ext_on), self.Md, self.ad,
-                       self.bd, self.Mb, self.ab)
+                       self.bd, self.Mb, self.ab, self.Mbh, self.eps_bh)
 
 
 def _load():

@@ -20,7 +20,10 @@
  *   - the j = i term is always skipped (eq. 2); for eps > 0 it is exactly
  *     zero anyway (remark after eq. 5);
  *   - the external field is a Miyamoto-Nagai disk plus a Plummer bulge,
- *     axisymmetric like the disk of the paper's galactic model (Sect. 3).
+ *     axisymmetric like the disk of the paper's galactic model (Sect. 3),
+ *     plus an optional point mass at the galactic centre, Plummer-softened
+ *     by eps_bh: the massive black hole of the collision runs of Sect. 6.2,
+ *     read as a static central mass.
  */
 #include <math.h>
 #include <stdint.h>
@@ -36,6 +39,7 @@ typedef struct {
     int ext_on;     /* 1: add the external field of eq. 3 */
     double Md, ad, bd;  /* Miyamoto-Nagai disk mass, scale length, scale height */
     double Mb, ab;      /* Plummer bulge mass and scale */
+    double Mbh, eps_bh; /* central point mass and its softening (0: none) */
 } orc_params;
 
 int orc_abi_version(void) { return 1; }
@@ -126,7 +130,8 @@ void orc_accel_int_at(int64_t n, const double *pos, const double *mass, double G
 /*
  * External potential Phi(x) (per unit mass), the smooth galactic term of
  * eq. 3 with F_ext = -grad Phi:
- *   Phi = -G Md / sqrt(R^2 + (ad + sqrt(z^2 + bd^2))^2) - G Mb / sqrt(r^2 + ab^2).
+ *   Phi = -G Md / sqrt(R^2 + (ad + sqrt(z^2 + bd^2))^2) - G Mb / sqrt(r^2 + ab^2)
+ *         - G Mbh / sqrt(r^2 + eps_bh^2).
  */
 double orc_ext_phi(const orc_params *p, const double *x)
 {
@@ -134,7 +139,9 @@ double orc_ext_phi(const orc_params *p, const double *x)
     const double s = sqrt(x[2] * x[2] + p->bd * p->bd);
     const double D = sqrt(R2 + (p->ad + s) * (p->ad + s));
     const double rb = sqrt(R2 + x[2] * x[2] + p->ab * p->ab);
-    return -p->G * p->Md / D - p->G * p->Mb / rb;
+    const double rh = sqrt(R2 + x[2] * x[2] + p->eps_bh * p->eps_bh);
+    const double ph = p->Mbh > 0 ? p->G * p->Mbh / rh : 0.0;   /* no black hole: no term */
+    return -p->G * p->Md / D - p->G * p->Mb / rb - ph;
 }
 
 /* External acceleration a = -grad Phi of the potential above, in closed form. */
@@ -146,11 +153,14 @@ void orc_ext_accel_one(const orc_params *p, const double *x, double *a)
     const double D3 = D2 * sqrt(D2);
     const double rb2 = R2 + x[2] * x[2] + p->ab * p->ab;
     const double rb3 = rb2 * sqrt(rb2);
+    const double rh2 = R2 + x[2] * x[2] + p->eps_bh * p->eps_bh;
+    const double rh3 = rh2 * sqrt(rh2);
     const double kd = p->G * p->Md / D3;
     const double kb = p->G * p->Mb / rb3;
-    a[0] = -kd * x[0] - kb * x[0];
-    a[1] = -kd * x[1] - kb * x[1];
-    a[2] = -kd * x[2] * (p->ad + s) / s - kb * x[2];
+    const double kh = p->Mbh > 0 ? p->G * p->Mbh / rh3 : 0.0;
+    a[0] = -kd * x[0] - kb * x[0] - kh * x[0];
+    a[1] = -kd * x[1] - kb * x[1] - kh * x[1];
+    a[2] = -kd * x[2] * (p->ad + s) / s - kb * x[2] - kh * x[2];
 }
 
 void orc_ext_accel(int64_t n, const double *pos, const orc_params *p, double *acc)

@@ -357,6 +357,76 @@ def test_torque_closed_form(orc):
                                rtol=1e-14, atol=1e-18)
 
 
+
+# ------------------------------------------- central black hole (Sect. 6.2)
+
+def test_black_hole_is_a_plummer_sphere_of_its_softening(orc):
+    """The central point mass M_bh softened by eps_bh and a Plummer bulge with
+    M_b = M_bh, a_b = eps_bh are the same field; the bulge term is pinned on
+    its own above (centre value, far field, -grad Phi)."""
+    rng = np.random.default_rng(21)
+    bh = _params(orc, ext_on=True, Md=0.0, Mb=0.0, Mbh=7.0, eps_bh=0.4)
+    bu = _params(orc, ext_on=True, Md=0.0, Mb=7.0, ab=0.4)
+    for x in np.vstack([[0.0, 0, 0], [0.3, -0.2, 0.1], rng.normal(scale=3, size=(5, 3))]):
+        assert abs(orc.ext_phi(bh, x) - orc.ext_phi(bu, x)) <= 1e-15 * abs(orc.ext_phi(bu, x))
+        np.testing.assert_allclose(orc.ext_accel(bh, x)[0], orc.ext_accel(bu, x)[0],
+                                   rtol=1e-15, atol=0)
+
+
+def test_black_hole_field_is_minus_grad_phi(orc):
+    """With the black hole added to disk and bulge, a_ext = -grad Phi still
+    holds (fourth-order differences), including well inside eps_bh."""
+    p = _params(orc, ext_on=True, Mbh=50.0, eps_bh=0.05)
+    for x in ([0.02, 0.01, -0.005], [0.2, 0.1, -0.05], [3.0, -1.0, 0.5], [10.0, 0.0, 0.0]):
+        x = np.array(x)
+        a = orc.ext_accel(p, x)[0]
+        g = _fd_grad(orc, p, x, h=1e-5 if np.linalg.norm(x) < 0.1 else 2e-4)
+        np.testing.assert_allclose(a, -g, rtol=1e-7, atol=1e-9 * np.abs(a).max())
+
+
+def _bh_kepler_error(orc, nsteps):
+    """Test particle about an unsoftened point mass fixed at the origin (no
+    disk, no bulge): e = 0.5 orbit, compared after 0.6 periods with the
+    solution of Kepler's equation for mu = M_bh."""
+    M, a, e = 3.0, 1.0, 0.5
+    rp = a * (1 - e)
+    vp = math.sqrt(M * (1 + e) / rp)
+    pos0 = np.array([[0.0, 0, 0], [rp, 0, 0]])
+    vel0 = np.array([[0.0, 0, 0], [0, vp, 0]])
+    t = 0.6 * 2 * math.pi * math.sqrt(a ** 3 / M)
+    exact = _kepler_closed_form(pos0, vel0, np.array([M, 0.0]), t)[1]
+    p = _params(orc, ext_on=True, Md=0.0, Mb=0.0, Mbh=M, eps_bh=0.0)
+    x, _ = orc.run(pos0[1:], vel0[1:], [1.0], p, 6, t / nsteps, nsteps)
+    return np.abs(x[0] - exact).max()
+
+
+def test_orbit_about_black_hole_is_keplerian(orc):
+    """The point-mass term integrates to Kepler's orbit at sixth order (error
+    ratio ~64 per dt halving; a wrong exponent or a missing G M fails)."""
+    e1 = _bh_kepler_error(orc, 240)
+    e2 = _bh_kepler_error(orc, 480)
+    assert e1 < 1e-5, e1
+    assert 45 < e1 / e2 < 85, (e1, e2, e1 / e2)
+
+
+def test_angular_momentum_rate_is_external_torque(orc):
+    """L changes only through the external torque of eq. 8 (internal forces
+    are central, Sect. 5.1): (L(h) - L(-h)) / 2h from two sixth-order steps
+    matches M_ext at t = 0 to O(h^2); the black hole, central about the
+    origin, adds no torque of its own."""
+    pos, vel, m = ics.plummer(64, seed=8)
+    pos = 0.5 * pos + np.array([6.0, 1.0, 0.8])
+    p = _params(orc, eps=0.01, ext_on=True, Mbh=5.0, eps_bh=0.1)
+    h = 1e-3
+    xf, vf = orc.run(pos, vel, m, p, 6, h, 1)
+    xb, vb = orc.run(pos, vel, m, p, 6, -h, 1)
+    dL = (orc.energy(xf, vf, m, p).L - orc.energy(xb, vb, m, p).L) / (2 * h)
+    tq = orc.torque(pos, m, p)
+    assert np.abs(tq).max() > 0
+    np.testing.assert_allclose(dL, tq, rtol=0, atol=1e-6 * np.abs(tq).max())
+    only_bh = _params(orc, eps=0.01, ext_on=True, Md=0.0, Mb=0.0, Mbh=5.0, eps_bh=0.1)
+    assert np.abs(orc.torque(pos, m, only_bh)).max() < 1e-14 * np.abs(tq).max() * 1e3
+
 # ------------------------------------------------------------ diagnostics
 
 def test_energy_closed_forms(orc):
