@@ -210,7 +210,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the pair-kernel shape autotuner (nb_tune) before timing")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5", "paper"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5", "paper", "plunge"],
                     help="c2 (default): the headline line; the others print their own "
                          "labelled lines (see bench_workloads.py)")
     ap.add_argument("--jobs", type=int, default=48, help="c5: jobs in the bounded trace")

@@ -18,6 +18,14 @@ bench.py.  Inputs are seeded and synthetic (paper_1003_3896_gb300.ics).
       {FP64, mixed}, step count log-uniform on [10, 1000] capped at steps_cap;
       a bounded trace of the first ``--jobs`` arrivals; latency includes
       queueing.
+  plunge  Sect. 6.2's quasi-radial collisions with a massive black hole at the
+      galactic centre: a Plummer cluster (N = 15360, M = 1, a = 1) released at
+      (10, 0, 0) with velocity 0.001 v_c, black hole masses 0.1, 1, 50 and 105
+      times the cluster's (static, softened by 0.05 so the passages through
+      it are resolvable), disk + bulge field, SI6A with dt = 2e-4 over
+      t in [0, 4] (NB_PLUNGE_STEPS steps, default 20000), mixed precision: relative
+      energy and angular momentum changes (the quantities of Table 8) and
+      the external torque of eq. 8 at the start and the end.
   paper  The paper's own test workload (Sect. 3, Sect. 5.1): a uniform sphere
       (R = 1, M = 1, virial ratio Q = 0.3) at the sizes of its Table 3,
       N = 480, 30720 and 1536000, one leapfrog step per precision (FP64 only
@@ -48,14 +56,28 @@ def _rel_rms(a, ref):
     return math.sqrt(((a - ref) ** 2).sum() / (ref ** 2).sum())
 
 
-def c1(args, nbsym, torch):
+def _cpu_baseline_c1(pos, vel, m, eps, dt, nsteps):
+    """CPU baseline leg of C1: the oracle's full run on the host cores (timed),
+    with the energies of its initial and final states."""
     import oracle
+    oracle.build()
+    p = oracle.Params(eps=eps)
+    t0 = time.perf_counter()
+    rx, rv = oracle.run(pos, vel, m, p, 2, dt, nsteps)
+    wall = time.perf_counter() - t0
+    e0 = oracle.energy(pos, vel, m, p).E
+    e1 = oracle.energy(rx, rv, m, p).E
+    cores = oracle.max_threads()
+    return rx, abs((e1 - e0) / e0), {
+        "value": 1e6 * wall / nsteps, "unit": "us/step", "cores": cores, "kind": "oracle",
+        "sample": f"the full run ({nsteps} steps of N = {pos.shape[0]}), FP64, "
+                  f"{wall:.2f} s on {cores} host threads"}
+
+
+def c1(args, nbsym, torch):
     n, eps, dt, nsteps = 1024, 1e-3, 1.0 / 1024, 64
     pos, vel, m = ics.henon_plummer(n, 0)
-    p = oracle.Params(eps=eps)
-    e0 = oracle.energy(pos, vel, m, p).E
-    rx, rv = oracle.run(pos, vel, m, p, 2, dt, nsteps)
-    de_ref = abs((oracle.energy(rx, rv, m, p).E - e0) / e0)
+    rx, de_ref, cpu = _cpu_baseline_c1(pos, vel, m, eps, dt, nsteps)
     out = {}
     for prec in ("fp64", "ds"):
         with _ctx(nbsym, n, eps=eps, precision=prec) as c:
@@ -63,12 +85,13 @@ def c1(args, nbsym, torch):
             tuning = None if args.no_tune else c.tune(reps=5)
             c.step(2, dt, 3)             # warm-up (graph capture)
             c.load(pos, vel, m)
+            e0 = c.energy().E
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             c.step(2, dt, nsteps)
             wall = time.perf_counter() - t0
             x, v = c.get_state()
-        de = abs((oracle.energy(x, v, m, p).E - e0) / e0)
+            de = abs((c.energy().E - e0) / e0)
         out[prec] = {"us_per_step": 1e6 * wall / nsteps,
                      "value": nsteps * n * n / wall / 1e9,
                      "dE_over_E": de, "dE_over_E_oracle": de_ref,
@@ -77,15 +100,30 @@ def c1(args, nbsym, torch):
     return {"metric": "leapfrog step latency, N=1024", "workload":
             "plummer_N1024_henon_eps1e-3_dkd_dt1/1024_64steps", "unit": "us/step",
             "value": out["fp64"]["us_per_step"], "higher_is_better": False,
-            "detail": out}
+            "detail": out, "cpu_baseline": cpu}
+
+
+def _cpu_baseline_c3(pos, m, idx, eps):
+    """CPU baseline leg of C3: the oracle's sums for the sampled bodies
+    against all N sources on the host cores (timed)."""
+    import oracle
+    oracle.build()
+    n = m.size
+    t0 = time.perf_counter()
+    ref = oracle.accel_int_at(pos, m, idx, 1.0, eps)
+    wall = time.perf_counter() - t0
+    cores = oracle.max_threads()
+    return ref, {"value": idx.size * n / wall / 1e9, "unit": UNIT, "cores": cores,
+                 "kind": "oracle",
+                 "sample": f"{idx.size} target bodies x {n} sources, FP64, {wall:.2f} s "
+                           f"on {cores} host threads"}
 
 
 def c3(args, nbsym, torch):
-    import oracle
     n, eps = 262144, 1e-4
     pos, vel, m = ics.plummer(n, 0, masses=ics.salpeter_masses(n, 0))
     idx = np.unique(np.random.default_rng(2).choice(n, 256, replace=False))
-    ref = oracle.accel_int_at(pos, m, idx, 1.0, eps)
+    ref, cpu = _cpu_baseline_c3(pos, m, idx, eps)
     sweep = {}
     with _ctx(nbsym, n, eps=eps, precision="ds") as c:
         c.load(pos, vel, m)
@@ -113,7 +151,7 @@ def c3(args, nbsym, torch):
             "workload": "plummer_salpeter_N262144_eps1e-4", "unit": UNIT,
             "value": 20 * n * n / wall / 1e9, "higher_is_better": True,
             "sweep": sweep, "tolerance": {"fp64": 1e-12, "ds": 1e-6, "fp32": 1e-5},
-            "tuning": tunings}
+            "tuning": tunings, "cpu_baseline": cpu}
 
 
 def c4(args, nbsym, torch):
@@ -235,13 +273,62 @@ def paper(args, nbsym, torch):
             "note": "paper figures are context (Tesla C1060, 2010), not targets"}
 
 
+# Table 8 of the paper (N = 15360, its own units and field): |dE/E0| and
+# |dL/L0| over its run, per black hole to cluster mass ratio.
+PAPER_TABLE8 = {0.1: (3.06e-7, 5.90e-4), 1.0: (7.75e-6, 1.06e-2), 50.0: (9.23e-5, 2.65),
+                105.0: (5.63e-3, 3.91)}
+
+
+def plunge(args, nbsym, torch):
+    n = 15360
+    eps = ics.paper_softening(n)
+    eps_bh = 0.05
+    nsteps = int(os.environ.get("NB_PLUNGE_STEPS", "20000"))
+    dt = 4.0 / nsteps
+    pos, vel, m = ics.plunge_cluster(n, 0)
+    rows = []
+    total_pairs = 0.0
+    total_wall = 0.0
+    for q in (0.1, 1.0, 50.0, 105.0):
+        with nbsym.Context(n, eps=eps, precision="ds", ext_on=True, Mbh=q,
+                           eps_bh=eps_bh) as c:
+            c.load(pos, vel, m)
+            if not args.no_tune:
+                c.tune(reps=3)
+            e0 = c.energy()
+            tq0 = c.torque()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            c.step(6, dt, nsteps)
+            wall = time.perf_counter() - t0
+            e1 = c.energy()
+            tq1 = c.torque()
+            x, _ = c.get_state()
+        L0 = np.linalg.norm(e0.L)
+        rows.append({"mbh_over_m": q, "dE_over_E0": abs((e1.E - e0.E) / e0.E),
+                     "dL_over_L0": float(np.linalg.norm(e1.L - e0.L) / L0),
+                     "torque_start": tq0.tolist(), "torque_end": tq1.tolist(),
+                     "barycentre_end": (m @ x / m.sum()).tolist(),
+                     "s_per_run": wall,
+                     "paper_table8": {"dE_over_E0": PAPER_TABLE8[q][0],
+                                      "dL_over_L0": PAPER_TABLE8[q][1]}})
+        total_pairs += 7.0 * nsteps * n * n
+        total_wall += wall
+    return {"metric": "black-hole collision runs (Sect. 6.2)", "unit": UNIT,
+            "value": total_pairs / total_wall / 1e9, "higher_is_better": True,
+            "workload": f"plunge_plummer_N{n}_r0_10_v0.001vc_epsbh0.05_si6a_t4_{nsteps}steps_ds",
+            "rows": rows,
+            "note": "Table 8 values are context only: another field, other units"}
+
+
 def run(args):
     import torch
     torch.cuda.set_device(0)
     from paper_1003_3896_gb300 import build as nbbuild
     nbbuild.build()
     from paper_1003_3896_gb300 import nbsym
-    fn = {"c1": c1, "c3": c3, "c4": c4, "c5": c5, "paper": paper}[args.workload]
+    fn = {"c1": c1, "c3": c3, "c4": c4, "c5": c5, "paper": paper,
+          "plunge": plunge}[args.workload]
     line = fn(args, nbsym, torch)
     line["impl"] = "ours"
     line["data"] = "synthetic"

@@ -75,9 +75,12 @@ typedef struct {
                           sum of eq. 2 with the j != i exclusion */
     int precision;     /* enum nb_precision */
     int ext_on;        /* 1: add the external field of eq. 3, a
-                          Miyamoto-Nagai disk plus a Plummer bulge:
+                          Miyamoto-Nagai disk plus a Plummer bulge plus an
+                          optional central point mass (Mbh below):
                           Phi = -G Md / sqrt(R^2 + (ad + sqrt(z^2 + bd^2))^2)
-                                - G Mb / sqrt(r^2 + ab^2),  a_ext = -grad Phi */
+                                - G Mb / sqrt(r^2 + ab^2)
+                                - G Mbh / sqrt(r^2 + eps_bh^2),
+                          a_ext = -grad Phi */
     double Md, ad, bd; /* disk mass, scale length, scale height (bd > 0) */
     double Mb, ab;     /* bulge mass, scale (ab > 0) */
     int device;        /* CUDA device ordinal */
@@ -88,6 +91,11 @@ typedef struct {
                           centre of mass, so the radius scales with the mean
                           spacing) get the double-single coordinate
                           difference; <= 0 selects the default 0.4 */
+    double Mbh;        /* mass of a point at the galactic centre (the
+                          massive black hole of Sect. 6.2's collision runs,
+                          static), >= 0; 0 = none.  Part of the external
+                          field: used only when ext_on */
+    double eps_bh;     /* its Plummer softening, >= 0 */
 } nb_params;
 
 /* Diagnostics of Sect. 5.1 (eq. 9-10 use E and L):
@@ -338,6 +346,7 @@ typedef struct {
     int ext_on;
     double Md, ad, bd, Mb, ab;
     double near_frac;         /* as nb_params (NB_DS jobs) */
+    double Mbh, eps_bh;       /* as nb_params */
 } nb_server_params;
 
 typedef struct {

@@ -411,9 +411,10 @@ int enq_split(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph
 {
     if (!float_planes(pl.precision)) return NB_OK;
     const DevState s = view(P, C, pl);
-    NB_TRY(launch_frame(s, ph.near_frac, st));
+    const bool near = pl.pl.mode == PM_DS_NEAR;
+    NB_TRY(launch_frame(s, ph.near_frac, near, st));
     NB_TRY(launch_split(s, st));
-    count(kernels, 3);
+    count(kernels, near ? 5 : 3);
     return NB_OK;
 }
 
@@ -462,8 +463,9 @@ int enq_step(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph,
         for (int k = 0; k < 7; ++k) wk[k] = seq[k];
     }
     if (sp) {
-        NB_TRY(launch_frame(s, ph.near_frac, st));
-        count(kernels, 2);
+        const bool near = pl.pl.mode == PM_DS_NEAR;
+        NB_TRY(launch_frame(s, ph.near_frac, near, st));
+        count(kernels, near ? 4 : 2);
     }
     // drift of the first leapfrog's half step (and the split it feeds)
     NB_TRY(launch_kick_drift(s, pl.pl.d, 0.0, 0.5 * wk[0] * h, 0, sp ? 1 : 0, ph.ext, st));

@@ -51,16 +51,22 @@ __device__ __forceinline__ void field_accel(const ExtField &e, double x, double 
     const double kd = e.G * e.Md * (rD * rD * rD);
     const double rB = rsqrt(R2 + z * z + e.ab * e.ab);
     const double kb = e.G * e.Mb * (rB * rB * rB);
-    ax = -(kd + kb) * x;
-    ay = -(kd + kb) * y;
-    az = -(kd * q * rs + kb) * z;
+    double kh = 0.0;   // softened central point mass
+    if (e.Mbh > 0) {
+        const double rH = rsqrt(R2 + z * z + e.eps2bh);
+        kh = e.G * e.Mbh * (rH * rH * rH);
+    }
+    ax = -(kd + kb + kh) * x;
+    ay = -(kd + kb + kh) * y;
+    az = -(kd * q * rs + kb + kh) * z;
 }
 
 __device__ __forceinline__ double field_phi(const ExtField &e, double x, double y, double z)
 {
     const double R2 = x * x + y * y;
     const double q = e.ad + sqrt(z * z + e.bd * e.bd);
-    return -e.G * e.Md * rsqrt(R2 + q * q) - e.G * e.Mb * rsqrt(R2 + z * z + e.ab * e.ab);
+    const double ph = e.Mbh > 0 ? e.G * e.Mbh * rsqrt(R2 + z * z + e.eps2bh) : 0.0;
+    return -e.G * e.Md * rsqrt(R2 + q * q) - e.G * e.Mb * rsqrt(R2 + z * z + e.ab * e.ab) - ph;
 }
 
 // Tree reduction of NV doubles over a block of RT threads; fixed order.
@@ -189,21 +195,72 @@ __global__ void frame_final_kernel(DevState s, double near_frac)
         f.cz = M > 0 ? v[3] / M : 0.0;
         const double r2 = M > 0 ? v[4] / M - (f.cx * f.cx + f.cy * f.cy + f.cz * f.cz) : 0.0;
         f.r2rms = r2 > 0 ? r2 : 0.0;
-        // near-pair radius: near_frac times the rms radius over N^{1/3}, a
-        // mean-spacing scale like the paper's softening rule (Sect. 2), so
-        // the expected number of near neighbours per body is independent of N
+        // no near-pair radius yet (set by frame_scale_kernel when the plan
+        // runs the near-pair pass)
+        f.th2 = (float)s.cl.eps2d[k];
+        f.dth = 0.f;
+        s.cl.frame[k] = f;
+    }
+}
+
+// Harmonic moment about the frame origin: sum m / |x - c| (per segment),
+// with a floor of 1e-3 R_rms on the distance.
+__global__ void frame_harmonic_kernel(DevState s)
+{
+    __shared__ double sh[2 * RT];
+    const int sg = blockIdx.x;
+    const int32_t k = s.cl.seg_k[sg];
+    const int64_t base = s.cl.boff[k] - s.cl.noff[k];
+    const Frame f = s.cl.frame[k];
+    const double floor2 = 1e-6 * f.r2rms + 1e-300;
+    double v[2] = {0, 0};
+    for (int64_t t = s.cl.seg_lo[sg] + threadIdx.x; t < s.cl.seg_hi[sg]; t += RT) {
+        const int64_t i = base + t;
+        const double dx = s.x[i] - f.cx, dy = s.y[i] - f.cy, dz = s.z[i] - f.cz;
+        v[0] += s.m[i] * rsqrt(dx * dx + dy * dy + dz * dz + floor2);
+        v[1] += s.m[i];
+    }
+    block_sum<2>(v, sh);
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 2; ++q) s.red[(int64_t)sg * 16 + q] = v[q];
+}
+
+// Near-pair radius d_th = near_frac * S / N^{1/3}: a mean-spacing scale like
+// the paper's softening rule (Sect. 2), so the expected number of near
+// neighbours per body does not grow with N.  S = min(R_rms, 3 R_h) with the
+// harmonic radius R_h = M / sum(m / |x - c|): for centrally concentrated
+// clusters (Plummer: R_rms = 2.6 R_h; uniform sphere: 1.2 R_h) S is the rms
+// radius, but once escapers or a disrupted halo inflate R_rms, S follows the
+// bound core instead, so the core does not crowd into a few cells.
+__global__ void frame_scale_kernel(DevState s, double near_frac)
+{
+    __shared__ double sh[2 * RT];
+    double v[2];
+    cluster_sum<2>(s, v, sh);
+    if (threadIdx.x == 0) {
+        const int k = blockIdx.x;
+        Frame f = s.cl.frame[k];
+        double scale2 = f.r2rms;
+        if (v[0] > 0) {
+            const double rh = v[1] / v[0];
+            if (9.0 * rh * rh < scale2) scale2 = 9.0 * rh * rh;
+        }
         const double nk = (double)s.cl.nk[k];
-        const double spacing2 = f.r2rms / cbrt(nk * nk);
+        const double spacing2 = scale2 / cbrt(nk * nk);
         f.th2 = (float)(near_frac * near_frac * spacing2 + s.cl.eps2d[k]);
         f.dth = (float)(near_frac * sqrt(spacing2));
         s.cl.frame[k] = f;
     }
 }
 
-cudaError_t launch_frame(const DevState &s, double near_frac, cudaStream_t st)
+cudaError_t launch_frame(const DevState &s, double near_frac, bool near, cudaStream_t st)
 {
     frame_partial_kernel<<<s.cl.S, RT, 0, st>>>(s);
     frame_final_kernel<<<s.cl.K, RT, 0, st>>>(s, near_frac);
+    if (near) {
+        frame_harmonic_kernel<<<s.cl.S, RT, 0, st>>>(s);
+        frame_scale_kernel<<<s.cl.K, RT, 0, st>>>(s, near_frac);
+    }
     return cudaGetLastError();
 }
 

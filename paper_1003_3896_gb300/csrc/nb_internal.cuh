@@ -156,6 +156,7 @@ __device__ __forceinline__ void iblock_slots(const Decomp &d, const Clusters &c,
 struct ExtField {
     int on;
     double G, Md, ad, bd, Mb, ab;
+    double Mbh, eps2bh;   // central point mass (0: none) and its softening^2
 };
 
 // ---- launchers (pair.cu) ---------------------------------------------------
@@ -216,7 +217,9 @@ cudaError_t launch_cluster_map(const Clusters &c, int32_t *cid, int64_t n, cudaS
 cudaError_t launch_unpack(const DevState &s, const double *pos, const double *vel,
                           const double *mass, cudaStream_t st);
 cudaError_t launch_pack(const DevState &s, double *pos, double *vel, cudaStream_t st);
-cudaError_t launch_frame(const DevState &s, double near_frac, cudaStream_t st);
+// Frame origin and rms radius of every cluster; with near, also the
+// near-pair radius of the mixed mode's correction pass (2 or 4 kernels).
+cudaError_t launch_frame(const DevState &s, double near_frac, bool near, cudaStream_t st);
 cudaError_t launch_split(const DevState &s, cudaStream_t st);
 // One fused substep: optional kick v += wk dt_k (a_int + a_ext) from the
 // partial slots of decomposition d, then drift x += wd dt_k v, then

@@ -80,6 +80,8 @@ int check_params(const nb_params *p)
             return set_error(NB_EINVAL, "external field needs Md, Mb, ad >= 0 and bd, ab > 0");
     }
     if (!std::isfinite(p->near_frac)) return set_error(NB_EINVAL, "near_frac must be finite");
+    if (!std::isfinite(p->Mbh) || p->Mbh < 0 || !std::isfinite(p->eps_bh) || p->eps_bh < 0)
+        return set_error(NB_EINVAL, "Mbh and eps_bh must be finite and >= 0");
     return NB_OK;
 }
 
@@ -95,6 +97,8 @@ Phys phys_of(const nb_params &p)
     ph.ext.bd = p.bd;
     ph.ext.Mb = p.Mb;
     ph.ext.ab = p.ab;
+    ph.ext.Mbh = p.Mbh;
+    ph.ext.eps2bh = p.eps_bh * p.eps_bh;
     return ph;
 }
 

@@ -133,6 +133,7 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
     if (!(p->G > 0) || !(p->eps >= 0) || p->precision < NB_FP64 || p->precision > NB_DS_FULL)
         return NB_EINVAL;
     if (p->ext_on && !(p->bd > 0 && p->ab > 0)) return NB_EINVAL;
+    if (!(p->Mbh >= 0) || !(p->eps_bh >= 0)) return NB_EINVAL;
     int prev = -1;
     if (cudaGetDevice(&prev) != cudaSuccess) return NB_ECUDA;
     if (p->device != prev && cudaSetDevice(p->device) != cudaSuccess) return NB_EINVAL;
@@ -250,13 +251,16 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
         ext.bd = p->bd;
         ext.Mb = p->Mb;
         ext.ab = p->ab;
+        ext.Mbh = p->Mbh;
+        ext.eps2bh = p->eps_bh * p->eps_bh;
 
         na_tables_kernel<<<1, 32, 0, st>>>(t, n, p->eps, ipb);
         na_unpack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, d_pos, d_mass);
         if (cudaGetLastError() != cudaSuccess) { rc = NB_ECUDA; break; }
         if (pl.mode != PM_FP64) {
             const double nf = p->near_frac > 0 ? p->near_frac : 0.4;
-            if (launch_frame(s, nf, st) != cudaSuccess || launch_split(s, st) != cudaSuccess) {
+            if (launch_frame(s, nf, pl.mode == PM_DS_NEAR, st) != cudaSuccess ||
+                launch_split(s, st) != cudaSuccess) {
                 rc = NB_ECUDA;
                 break;
             }

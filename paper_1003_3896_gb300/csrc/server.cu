@@ -371,7 +371,8 @@ int nb_server_create(const nb_server_params *p, nb_server **out)
     if (!out) return set_error(NB_EINVAL, "out is NULL");
     *out = nullptr;
     if (!p || !(p->hbm_budget_bytes > 0) || p->max_jobs < 1 || p->max_jobs > (1 << 16) ||
-        !(p->G > 0) || (p->ext_on && !(p->bd > 0 && p->ab > 0)))
+        !(p->G > 0) || (p->ext_on && !(p->bd > 0 && p->ab > 0)) || !(p->Mbh >= 0) ||
+        !std::isfinite(p->Mbh) || !(p->eps_bh >= 0) || !std::isfinite(p->eps_bh))
         return set_error(NB_EINVAL, "bad server parameters");
     int ndev = 0;
     NB_TRY(cudaGetDeviceCount(&ndev));
@@ -389,6 +390,8 @@ int nb_server_create(const nb_server_params *p, nb_server **out)
     s->phys.ext.bd = p->bd;
     s->phys.ext.Mb = p->Mb;
     s->phys.ext.ab = p->ab;
+    s->phys.ext.Mbh = p->Mbh;
+    s->phys.ext.eps2bh = p->eps_bh * p->eps_bh;
     int64_t cap = (int64_t)(p->hbm_budget_bytes / BYTES_PER_BODY);
     if (cap > ((int64_t)1 << 26)) cap = (int64_t)1 << 26;
     if (cap < 1) {

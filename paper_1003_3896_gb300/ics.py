@@ -42,6 +42,8 @@ __all__ = [
     "kepler_pair",
     "place_on_orbit",
     "VC_R50",
+    "VC_R10",
+    "plunge_cluster",
     "DISK_BULGE",
     "ensemble_sizes",
     "serving_trace",
@@ -57,6 +59,10 @@ DISK_BULGE = (100.0, 6.5, 0.26, 15.0, 0.7)
 #: v_c^2 = 100*2500/(2500+6.76^2)^{3/2} + 15*2500/(2500+0.49)^{3/2}.
 #: tests/test_oracle_pins.py checks it against the oracle's field.
 VC_R50 = 1.4987666537924513
+
+#: The same at R = 10 (the start of the quasi-radial black-hole collision runs
+#: of Sect. 6.2): v_c^2 = 100*100/(100+6.76^2)^{3/2} + 15*100/(100+0.49)^{3/2}.
+VC_R10 = 2.678662467336762
 
 
 def paper_softening(n: int, radius: float = 1.0) -> float:
@@ -190,6 +196,18 @@ def place_on_orbit(pos: np.ndarray, vel: np.ndarray, radius: float = 50.0,
     p[:, 0] += radius
     v[:, 1] += vc
     return p, v
+
+
+def plunge_cluster(n: int, seed: int, r0: float = 10.0, vc: float = VC_R10,
+                   vfrac: float = 1e-3):
+    """Initial conditions of the quasi-radial collision runs of Sect. 6.2:
+    a Plummer cluster (M = 1, a = 1) with its barycentre at (r0, 0, 0) and
+    velocity (0, vfrac * v_c, 0), v_c the local circular speed, so it falls
+    almost radially through the galactic centre."""
+    pos, vel, m = plummer(n, seed)
+    pos = pos + np.array([r0, 0.0, 0.0])
+    vel = vel + np.array([0.0, vfrac * vc, 0.0])
+    return np.ascontiguousarray(pos), np.ascontiguousarray(vel), m
 
 
 def ensemble_sizes(n_clusters: int = 512, n_lo: int = 256, n_hi: int = 8192,

@@ -31,7 +31,8 @@ class Params(C.Structure):
     _fields_ = [("G", C.c_double), ("eps", C.c_double), ("precision", C.c_int),
                 ("ext_on", C.c_int), ("Md", C.c_double), ("ad", C.c_double),
                 ("bd", C.c_double), ("Mb", C.c_double), ("ab", C.c_double),
-                ("device", C.c_int), ("stream", C.c_void_p), ("near_frac", C.c_double)]
+                ("device", C.c_int), ("stream", C.c_void_p), ("near_frac", C.c_double),
+                ("Mbh", C.c_double), ("eps_bh", C.c_double)]
 
 
 class EnergyT(C.Structure):
@@ -178,7 +179,7 @@ class Context:
                  precision: int | str = NB_DS, ext_on: bool = False,
                  Md: float = 100.0, ad: float = 6.5, bd: float = 0.26, Mb: float = 15.0,
                  ab: float = 0.7, device: int = 0, stream=None, near_frac: float = 0.0,
-                 sizes=None):
+                 sizes=None, Mbh: float = 0.0, eps_bh: float = 0.0):
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
         p = Params()
@@ -188,6 +189,7 @@ class Context:
         p.device = device
         p.stream = _addr(stream) if stream is not None else None
         p.near_frac = near_frac
+        p.Mbh, p.eps_bh = Mbh, eps_bh
         h = _ctxp()
         if sizes is None:
             check(nb_create(C.byref(p), int(capacity), C.byref(h)))
@@ -316,7 +318,7 @@ class ServerParams(C.Structure):
     _fields_ = [("device", C.c_int), ("hbm_budget_bytes", C.c_double), ("max_jobs", C.c_int),
                 ("G", C.c_double), ("ext_on", C.c_int), ("Md", C.c_double), ("ad", C.c_double),
                 ("bd", C.c_double), ("Mb", C.c_double), ("ab", C.c_double),
-                ("near_frac", C.c_double)]
+                ("near_frac", C.c_double), ("Mbh", C.c_double), ("eps_bh", C.c_double)]
 
 
 class JobDesc(C.Structure):

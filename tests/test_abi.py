@@ -47,11 +47,13 @@ def test_abi_version_and_defaults(lib):
     nbsym.nb_params_default(C.byref(p))
     assert p.G == 1.0 and p.eps == 0.0 and p.precision == nbsym.NB_DS
     assert (p.Md, p.ad, p.bd, p.Mb, p.ab) == (100.0, 6.5, 0.26, 15.0, 0.7)
+    assert (p.Mbh, p.eps_bh) == (0.0, 0.0)
     nbsym.nb_params_default(None)   # NULL-safe
 
 
 @pytest.mark.parametrize("field,value", [("G", 0.0), ("G", float("nan")), ("eps", -1.0),
-                                         ("precision", 7), ("bd", 0.0)])
+                                         ("precision", 7), ("bd", 0.0), ("Mbh", -1.0),
+                                         ("Mbh", float("inf")), ("eps_bh", -0.5)])
 def test_create_rejects_bad_params_without_gpu(lib, field, value):
     from paper_1003_3896_gb300 import nbsym
     p = nbsym.Params()

@@ -355,3 +355,27 @@ def test_measured_peaks_are_plausible(nbs):
         assert 0.2 * cap < p[k] <= 2.05 * cap, (k, p[k], cap)
     assert 0 < p["dfma_tflops"] < cap
     assert p["rsqrt_gops"] > 0 and p["pairmix_gpairs"] > 0
+
+
+def test_mixed_with_escapers_stays_accurate_and_fast(nbs, orc):
+    """2% of the mass flung to ~1000 length units inflates the rms radius
+    400-fold; the near-pair radius follows the bound core (harmonic radius),
+    so the correction neither crowds the core into a few cells nor loses
+    accuracy."""
+    import time
+    n = 20000
+    pos, vel, m = system(n, seed=61)
+    rng = np.random.default_rng(62)
+    far = rng.choice(n, n // 50, replace=False)
+    pos[far] *= 1000.0 / np.linalg.norm(pos[far], axis=1, keepdims=True)
+    eps = ics.paper_softening(n)
+    ref = orc.accel_int(pos, m, 1.0, eps)
+    with nbs.Context(n, eps=eps, precision="ds") as c:
+        c.load(pos, vel, m)
+        a = c.accel()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            c.accel()
+        wall = time.perf_counter() - t0
+    assert rel_rms(a, ref) <= TOL["ds"], rel_rms(a, ref)
+    assert wall < 0.5, wall

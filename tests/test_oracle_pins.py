@@ -203,10 +203,13 @@ def test_ext_symmetries(orc):
 
 
 def test_circular_speed_constant(orc):
-    """VC_R50 (input module constant) equals sqrt(R |a_R|) at R = 50, z = 0."""
+    """VC_R50 and VC_R10 (input module constants) equal sqrt(R |a_R|) at
+    R = 50 and R = 10, z = 0."""
     p = _params(orc, ext_on=True)
     a = orc.ext_accel(p, np.array([50.0, 0, 0]))[0]
     assert abs(math.sqrt(50.0 * -a[0]) / ics.VC_R50 - 1) < 1e-14
+    a = orc.ext_accel(p, np.array([10.0, 0, 0]))[0]
+    assert abs(math.sqrt(10.0 * -a[0]) / ics.VC_R10 - 1) < 1e-14
 
 
 def test_circular_orbit_stays_circular(orc):
