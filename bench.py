@@ -115,8 +115,8 @@ class ClockSampler:
 # byte-identical to the captured source (first 16 hex digits of its SHA-256);
 # any change to the kernel or its shape makes the figure stale and the bench
 # then reports null.
-PAIR_TRAFFIC = {"source_sha256": "c8d323ce115f4d62", "n": 65536, "precision": "ds",
-                "bodies_per_thread": 4, "blocks_per_sm": 6, "bytes_per_launch": 2936576.0}
+PAIR_TRAFFIC = {"source_sha256": "e4e1e544794806b8", "n": 65536, "precision": "ds",
+                "bodies_per_thread": 8, "blocks_per_sm": 3, "bytes_per_launch": 2979840.0}
 
 
 def pair_traffic(n: int, precision: str, shape: dict):
@@ -210,6 +210,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the pair-kernel shape autotuner (nb_tune) before timing")
+    ap.add_argument("--tune-save", default="",
+                    help="write the tuned-shape table (nb_tune_save) to this file after tuning")
+    ap.add_argument("--tune-load", default="",
+                    help="load a tuned-shape table (nb_tune_load) and skip tuning, so a "
+                         "profiled run times the same kernel shapes as the run that saved it")
     ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5", "paper", "plunge"],
                     help="c2 (default): the headline line; the others print their own "
                          "labelled lines (see bench_workloads.py)")
@@ -247,8 +252,11 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     ctx = nbsym.Context(n, eps=eps, precision=args.precision, ext_on=True, device=local,
                         stream=stream.cuda_stream, near_frac=args.near_frac)
+    if args.tune_load:
+        nbsym.tune_load(args.tune_load)
     ctx.load(pos, vel, m)
-    tuning = None if args.no_tune else ctx.tune(reps=3)
+    tune = not args.no_tune and not args.tune_load
+    tuning = ctx.tune(reps=3) if tune else None
     for _ in range(args.warmup):
         ctx.step(6, dt, 1)
 
@@ -305,7 +313,9 @@ def main():
 
     # plain FP64 kernel on the same state and configuration
     ctx.set_precision("fp64")
-    tuning64 = None if args.no_tune else ctx.tune(reps=1)
+    tuning64 = ctx.tune(reps=1) if tune else None
+    if args.tune_save:
+        nbsym.tune_save(args.tune_save)
     ctx.prof_enable(True)
     for _ in range(2):
         ctx.accel()
