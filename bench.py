@@ -134,6 +134,49 @@ def pair_traffic(n: int, precision: str, shape: dict):
     return t["bytes_per_launch"]
 
 
+# ---- multi-rank host logic (one process per GPU; no data-path collective) ----
+
+def rank_env():
+    """(world, rank, local_rank) of this process as torchrun sets them."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def _reduce(value: float, op: str, device) -> float:
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def max_over_ranks(value: float, device="cpu") -> float:
+    """The largest of every rank's value (the job's time is its slowest rank's)."""
+    return _reduce(value, "max", device)
+
+
+def sum_over_ranks(value: float, device="cpu") -> float:
+    """The sum of every rank's value (work done by the whole job)."""
+    return _reduce(value, "sum", device)
+
+
+def shard_clusters(sizes, world: int):
+    """Whole clusters per rank for an ensemble: longest-processing-time
+    assignment by N_k^2 (the pair work), ties to the lower rank; each
+    cluster goes to exactly one rank, every rank's list ascending."""
+    sizes = np.asarray(sizes, dtype=np.int64)
+    order = sorted(range(sizes.size), key=lambda k: (-int(sizes[k]) ** 2, k))
+    load = [0] * world
+    out = [[] for _ in range(world)]
+    for k in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        out[r].append(k)
+        load[r] += int(sizes[k]) ** 2
+    return [np.array(sorted(o), dtype=np.int64) for o in out]
+
+
 def fp32_peak_tflops(sms: int, mhz: float) -> float:
     """FP32 FMA peak from unit counts: 128 FP32 lanes per SM, 2 flops per FMA."""
     return sms * 128 * 2 * mhz * 1e6 / 1e12
@@ -220,14 +263,15 @@ def main():
                          "labelled lines (see bench_workloads.py)")
     ap.add_argument("--jobs", type=int, default=48, help="c5: jobs in the bounded trace")
     ap.add_argument("--steps-cap", type=int, default=20, help="c5: cap on steps per job")
+    ap.add_argument("--rates", default="",
+                    help="c5: comma-separated arrival rates (jobs/s) to replay the trace at "
+                         "after the 200/s run, e.g. 2,4,8 (the rate sweep)")
     args = ap.parse_args()
     if args.workload != "c2":
         import bench_workloads
         return bench_workloads.run(args)
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
@@ -281,14 +325,11 @@ def main():
     shape = ctx.pair_shape()
     ctx.prof_enable(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    t_ms = sum(step_ms)
+    t_ms = max_over_ranks(sum(step_ms), dev)
     if world > 1:
-        t = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
         dist.barrier()
-    pairs_rank = 7 * args.steps * n * n
-    value = world * pairs_rank / (t_ms * 1e-3) / 1e9
+    pairs_all = sum_over_ranks(7 * args.steps * n * n, dev)
+    value = pairs_all / (t_ms * 1e-3) / 1e9
 
     # end-to-end through the public API: host buffers in pinned memory, the
     # state uploaded before and read back after every step
@@ -309,7 +350,8 @@ def main():
             ctx.step(6, dt, 1)
             nbsym.check(nbsym.nb_get_state(ctx.handle, nbsym._p(out_p), nbsym._p(out_v)))
             e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_value = world * 7 * n * n / (statistics.mean(e_ms) * 1e-3) / 1e9
+    e2e_ms = max_over_ranks(statistics.mean(e_ms), dev)
+    e2e_value = sum_over_ranks(7 * n * n, dev) / (e2e_ms * 1e-3) / 1e9
 
     # plain FP64 kernel on the same state and configuration
     ctx.set_precision("fp64")

@@ -155,10 +155,16 @@ def c3(args, nbsym, torch):
 
 
 def c4(args, nbsym, torch):
-    sizes = ics.ensemble_sizes(512, 256, 8192, seed=0)
+    import bench
+    world, rank, local = bench.rank_env()
+    all_sizes = ics.ensemble_sizes(512, 256, 8192, seed=0)
+    # under torchrun each rank integrates its share of whole clusters (no
+    # data-path collective); the job's time is its slowest rank's
+    mine = bench.shard_clusters(all_sizes, world)[rank]
+    sizes = all_sizes[mine]
     pos, vel, mass, eps = [], [], [], []
-    for k, n in enumerate(sizes):
-        p, v, m = ics.henon_plummer(int(n), k)
+    for k, n in zip(mine, sizes):
+        p, v, m = ics.henon_plummer(int(n), int(k))
         pos.append(p)
         vel.append(v)
         mass.append(m)
@@ -173,26 +179,33 @@ def c4(args, nbsym, torch):
         b.step(6, dt, max(1, args.warmup))
         steps = args.steps
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
         b.prof_enable(True)
         t0 = time.perf_counter()
         b.step(6, dt, steps)
         wall = time.perf_counter() - t0
         pr = b.prof_read()
-    value = 7 * steps * pairs / wall / 1e9
+    wall = bench.max_over_ranks(wall, "cuda")
+    pairs_all = bench.sum_over_ranks(pairs, "cuda")
+    value = 7 * steps * pairs_all / wall / 1e9
     achieved = 20 * pr["interactions"] / (pr["pair_ms"] * 1e-3) / 1e12
     return {"metric": "batched ensemble throughput", "unit": UNIT, "value": value,
-            "higher_is_better": True,
+            "higher_is_better": True, "n_gpus": world,
+            "scaling": "strong" if world > 1 else "weak",
             "workload": "512_plummer_clusters_N256-8192_henon_si6a_dt1/512_ds",
-            "clusters": int(sizes.size), "bodies": int(sizes.sum()),
-            "sum_N2_per_eval": pairs, "steps": steps, "ms_per_step": 1e3 * wall / steps,
+            "clusters": int(all_sizes.size), "clusters_rank0": int(sizes.size),
+            "bodies": int(all_sizes.sum()),
+            "sum_N2_per_eval": pairs_all, "steps": steps, "ms_per_step": 1e3 * wall / steps,
             "pair_kernel_tflops": achieved, "pair_launches": pr["pair_launches"],
             "pair_kernel_ms_mean": pr["pair_ms"] / max(1, pr["pair_launches"]),
             "gpu_launches": pr["kernel_launches"], "tuning": tuning}
 
 
-def c5(args, nbsym, torch):
-    n_cap = int(os.environ.get("NB_SERVE_NCAP", "32768"))
-    trace = ics.serving_trace(n_jobs=args.jobs, rate_hz=200.0, seed=0, n_hi=n_cap)
+def _serve_trace(args, nbsym, rate_hz, n_cap):
+    """Replay the first args.jobs arrivals at rate_hz through one server;
+    per-job latency is submission to completion (queueing included)."""
+    trace = ics.serving_trace(n_jobs=args.jobs, rate_hz=rate_hz, seed=0, n_hi=n_cap)
     dt = 1.0 / 512
     prepared = []
     for j in trace:
@@ -220,15 +233,28 @@ def c5(args, nbsym, torch):
         stats = srv.stats()
     lat.sort()
     q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))]
+    return {"rate_hz": rate_hz, "p50_s": q(0.5), "p99_s": q(0.99), "jobs_done": len(lat),
+            "throughput_gpairs_s": pairs / makespan / 1e9, "makespan_s": makespan,
+            "offered_gpairs_s": pairs / max(trace[-1].arrival_s, 1e-9) / 1e9,
+            "completed": stats["completed"], "failed": stats["failed"]}
+
+
+def c5(args, nbsym, torch):
+    n_cap = int(os.environ.get("NB_SERVE_NCAP", "32768"))
+    r = _serve_trace(args, nbsym, 200.0, n_cap)
+    sweep = []
+    for rate in [float(x) for x in args.rates.split(",") if x.strip()]:
+        sweep.append(_serve_trace(args, nbsym, rate, n_cap))
     return {"metric": "serving latency p50/p99 (bounded trace)", "unit": "s",
-            "value": q(0.5), "p99_s": q(0.99), "higher_is_better": False,
+            "value": r["p50_s"], "p99_s": r["p99_s"], "higher_is_better": False,
             "workload": f"poisson200hz_first{args.jobs}_N1024-{n_cap}_steps<= {args.steps_cap}"
                         "_order2or6_fp64orDS_dt1/512",
-            "jobs_done": len(lat), "throughput_gpairs_s": pairs / makespan / 1e9,
-            "makespan_s": makespan, "completed": stats["completed"],
-            "failed": stats["failed"], "note": "latency includes queueing; the trace "
-            "offers far more work than one GPU serves at 200/s, so it is bounded "
-            "(first jobs, capped N and steps)"}
+            "jobs_done": r["jobs_done"], "throughput_gpairs_s": r["throughput_gpairs_s"],
+            "makespan_s": r["makespan_s"], "completed": r["completed"],
+            "failed": r["failed"], "rate_sweep": sweep,
+            "note": "latency includes queueing; the trace offers far more work than one "
+            "GPU serves at 200/s, so it is bounded (first jobs, capped N and steps); "
+            "rate_sweep replays the same jobs at lower arrival rates"}
 
 
 # Table 3 of the paper, one Tesla C1060, leapfrog, GFLOPS at 20 flops per
@@ -322,15 +348,32 @@ def plunge(args, nbsym, torch):
 
 
 def run(args):
+    """One workload line.  Under torchrun only the ensemble (c4) shards across
+    ranks (whole clusters per rank); the single-system workloads run on rank
+    0 alone and the other ranks exit without work."""
+    import bench
     import torch
-    torch.cuda.set_device(0)
+    world, rank, local = bench.rank_env()
+    if world > 1 and args.workload != "c4":
+        if rank != 0:
+            return 0
+        world = 1
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", init_method="env://")
     from paper_1003_3896_gb300 import build as nbbuild
-    nbbuild.build()
+    if rank == 0:
+        nbbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
     from paper_1003_3896_gb300 import nbsym
     fn = {"c1": c1, "c3": c3, "c4": c4, "c5": c5, "paper": paper,
           "plunge": plunge}[args.workload]
     line = fn(args, nbsym, torch)
     line["impl"] = "ours"
     line["data"] = "synthetic"
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
     return 0
