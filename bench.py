@@ -247,7 +247,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=65536)
-    ap.add_argument("--precision", default="ds", choices=["ds", "ds_full", "fp32", "fp64"])
+    ap.add_argument("--precision", default="ds", choices=["ds", "ds_full", "fp32", "fp64", "dd"])
     ap.add_argument("--near-frac", type=float, default=0.0,
                     help="mixed mode near-pair radius in units of R_rms / N^(1/3) (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -375,7 +375,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"ds": "f32-pair/ds-acc", "ds_full": "f32-pair/ds-acc",
-                  "fp32": "f32", "fp64": "f64"}[args.precision],
+                  "fp32": "f32", "fp64": "f64", "dd": "f32x2-pair/f32x2-acc"}[args.precision],
         "data": "synthetic", "config": config_dict(args, world),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": pair_traffic(n, args.precision, shape),

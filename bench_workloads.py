@@ -79,7 +79,7 @@ def c1(args, nbsym, torch):
     pos, vel, m = ics.henon_plummer(n, 0)
     rx, de_ref, cpu = _cpu_baseline_c1(pos, vel, m, eps, dt, nsteps)
     out = {}
-    for prec in ("fp64", "ds"):
+    for prec in ("fp64", "ds", "dd"):
         with _ctx(nbsym, n, eps=eps, precision=prec) as c:
             c.load(pos, vel, m)
             tuning = None if args.no_tune else c.tune(reps=5)
@@ -128,7 +128,7 @@ def c3(args, nbsym, torch):
     with _ctx(nbsym, n, eps=eps, precision="ds") as c:
         c.load(pos, vel, m)
         tunings = {}
-        for prec in ("fp64", "ds", "fp32"):
+        for prec in ("fp64", "ds", "fp32", "dd"):
             c.set_precision(prec)
             # the FP64 kernel takes seconds per launch here: tuned only by request
             if not args.no_tune and prec != "fp64":
@@ -150,7 +150,7 @@ def c3(args, nbsym, torch):
     return {"metric": "accuracy sweep and leapfrog throughput, N=262144 Salpeter",
             "workload": "plummer_salpeter_N262144_eps1e-4", "unit": UNIT,
             "value": 20 * n * n / wall / 1e9, "higher_is_better": True,
-            "sweep": sweep, "tolerance": {"fp64": 1e-12, "ds": 1e-6, "fp32": 1e-5},
+            "sweep": sweep, "tolerance": {"fp64": 1e-12, "ds": 1e-6, "fp32": 1e-5, "dd": 1e-12},
             "tuning": tunings, "cpu_baseline": cpu}
 
 
@@ -202,7 +202,7 @@ def c4(args, nbsym, torch):
             "gpu_launches": pr["kernel_launches"], "tuning": tuning}
 
 
-def _serve_trace(args, nbsym, rate_hz, n_cap):
+def _serve_trace(args, nbsym, rate_hz, n_cap, fp64_via_dd=0):
     """Replay the first args.jobs arrivals at rate_hz through one server;
     per-job latency is submission to completion (queueing included)."""
     trace = ics.serving_trace(n_jobs=args.jobs, rate_hz=rate_hz, seed=0, n_hi=n_cap)
@@ -211,7 +211,7 @@ def _serve_trace(args, nbsym, rate_hz, n_cap):
     for j in trace:
         p, v, m = ics.henon_plummer(j.n, j.seed)
         prepared.append((j, p, v, m, ics.paper_softening(j.n)))
-    with nbsym.Server(hbm_budget_bytes=150e9, max_jobs=256) as srv:
+    with nbsym.Server(hbm_budget_bytes=150e9, max_jobs=256, fp64_via_dd=fp64_via_dd) as srv:
         t0 = time.perf_counter()
         ids = []
         for j, p, v, m, e in prepared:
@@ -242,6 +242,9 @@ def _serve_trace(args, nbsym, rate_hz, n_cap):
 def c5(args, nbsym, torch):
     n_cap = int(os.environ.get("NB_SERVE_NCAP", "32768"))
     r = _serve_trace(args, nbsym, 200.0, n_cap)
+    # the same trace with the FP64 jobs run in float-float arithmetic (FP64
+    # tolerance, FP32 pipes)
+    r_dd = _serve_trace(args, nbsym, 200.0, n_cap, fp64_via_dd=1)
     sweep = []
     for rate in [float(x) for x in args.rates.split(",") if x.strip()]:
         sweep.append(_serve_trace(args, nbsym, rate, n_cap))
@@ -251,7 +254,7 @@ def c5(args, nbsym, torch):
                         "_order2or6_fp64orDS_dt1/512",
             "jobs_done": r["jobs_done"], "throughput_gpairs_s": r["throughput_gpairs_s"],
             "makespan_s": r["makespan_s"], "completed": r["completed"],
-            "failed": r["failed"], "rate_sweep": sweep,
+            "failed": r["failed"], "rate_sweep": sweep, "fp64_jobs_via_dd": r_dd,
             "note": "latency includes queueing; the trace offers far more work than one "
             "GPU serves at 200/s, so it is bounded (first jobs, capped N and steps); "
             "rate_sweep replays the same jobs at lower arrival rates"}

@@ -49,11 +49,19 @@ typedef struct nb_ctx nb_ctx;
  *             every pair, so NB_DS then evaluates as NB_DS_FULL.
  *  NB_FP32 -- pure single precision: coordinates rounded to float
  *             (relative to the same reference point), float accumulation.
+ *  NB_DD   -- float-float: every quantity of the pair sum (coordinate
+ *             difference, r^2 + eps^2, 1/sqrt, m/r^3, the sums) is a pair
+ *             hi + lo of floats, about 48 significant bits, on the FP32
+ *             pipes; agrees with FP64 to ~1e-14 relative (FP64 tolerance
+ *             1e-12).  The FP64 pipe of this GPU runs at 1/77 of the FP32
+ *             rate, so this is the fast way to FP64-class accelerations.
+ *             No counterpart in the paper, which joins hi and lo only for
+ *             the coordinate difference (Sect. 5.2).
  *  NB_DS_FULL -- as NB_DS but the double-single coordinate difference is
  *             formed for every pair, as the paper's DSP code does.
  * In every mode the state (positions, velocities), the kick/drift update,
  * the external field and the energy diagnostic are double precision. */
-enum nb_precision { NB_FP64 = 0, NB_DS = 1, NB_FP32 = 2, NB_DS_FULL = 3 };
+enum nb_precision { NB_FP64 = 0, NB_DS = 1, NB_FP32 = 2, NB_DS_FULL = 3, NB_DD = 4 };
 
 enum nb_status {
     NB_OK = 0,
@@ -347,12 +355,16 @@ typedef struct {
     double Md, ad, bd, Mb, ab;
     double near_frac;         /* as nb_params (NB_DS jobs) */
     double Mbh, eps_bh;       /* as nb_params */
+    int fp64_via_dd;          /* 1: jobs submitted as NB_FP64 run the NB_DD
+                                 (float-float) arithmetic, which meets the FP64
+                                 tolerance at ~8x the FP64 pipe's rate; 0
+                                 (default): the plain FP64 kernel */
 } nb_server_params;
 
 typedef struct {
     int64_t n;        /* bodies, 1 <= n <= pool capacity */
     int order;        /* 2 or 6 */
-    int precision;    /* NB_FP64 or NB_DS */
+    int precision;    /* NB_FP64, NB_DS or NB_DD */
     double dt;        /* step length > 0 */
     int64_t nsteps;   /* >= 1 */
     double eps;       /* softening >= 0 */

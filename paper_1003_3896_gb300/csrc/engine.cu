@@ -287,6 +287,7 @@ int mode_of(int precision)
     case NB_FP64: return PM_FP64;
     case NB_FP32: return PM_FP32;
     case NB_DS_FULL: return PM_DS_FULL;
+    case NB_DD: return PM_DD;
     default: return PM_DS_NEAR;
     }
 }

@@ -282,10 +282,11 @@ __device__ __forceinline__ void split_one(const DevState &s, const Frame &f, int
     s.yl[i] = ly;
     s.zl[i] = lz;
     const float m = s.mf[i];
+    const float ml = __double2float_rn(s.m[i] - (double)m);   // mass lo part (float-float mode)
     s.jd[2 * i] = make_float4(hx, hx, hy, hy);
     s.jd[2 * i + 1] = make_float4(hz, hz, m, m);
     s.jl[2 * i] = make_float4(lx, lx, ly, ly);
-    s.jl[2 * i + 1] = make_float4(lz, lz, 0.f, 0.f);
+    s.jl[2 * i + 1] = make_float4(lz, lz, ml, ml);
 }
 
 __global__ void split_kernel(DevState s)

@@ -87,7 +87,8 @@ struct DevState {
     float *xl = nullptr, *yl = nullptr, *zl = nullptr;
     // j-stream copies, two float4 per body, each coordinate duplicated so a
     // packed f32x2 operand serves two i bodies: jd = (xh, xh, yh, yh),
-    // (zh, zh, m, m); jl = (xl, xl, yl, yl), (zl, zl, 0, 0).
+    // (zh, zh, m, m); jl = (xl, xl, yl, yl), (zl, zl, ml, ml) with ml the
+    // float rounding residue of the mass.
     float4 *jd = nullptr, *jl = nullptr;
     double *part = nullptr;     // partial sums [slot][3][cap]
     int64_t part_slots = 0;
@@ -162,8 +163,9 @@ struct ExtField {
 // ---- launchers (pair.cu) ---------------------------------------------------
 // mode: 0 = mixed (float pairs, double-single sums; near pairs corrected by
 // near.cu), 1 = mixed with double-single difference on every pair,
-// 2 = pure float, 3 = double.
-enum PairMode { PM_DS_NEAR = 0, PM_DS_FULL = 1, PM_FP32 = 2, PM_FP64 = 3 };
+// 2 = pure float, 3 = double, 4 = float-float (every operation on hi + lo
+// pairs of floats, FP64-class accuracy on the FP32 pipes).
+enum PairMode { PM_DS_NEAR = 0, PM_DS_FULL = 1, PM_FP32 = 2, PM_FP64 = 3, PM_DD = 4 };
 
 struct PairLaunch {
     int mode;

@@ -130,7 +130,7 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
 {
     if (!p || !d_pos || !d_mass || !d_acc_out) return NB_EINVAL;
     if (n < 1 || n > NA_MAX_N) return NB_EINVAL;
-    if (!(p->G > 0) || !(p->eps >= 0) || p->precision < NB_FP64 || p->precision > NB_DS_FULL)
+    if (!(p->G > 0) || !(p->eps >= 0) || p->precision < NB_FP64 || p->precision > NB_DD)
         return NB_EINVAL;
     if (p->ext_on && !(p->bd > 0 && p->ab > 0)) return NB_EINVAL;
     if (!(p->Mbh >= 0) || !(p->eps_bh >= 0)) return NB_EINVAL;
@@ -214,6 +214,7 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
         pl.mode = p->precision == NB_FP64 ? PM_FP64
                   : p->precision == NB_FP32 ? PM_FP32
                   : p->precision == NB_DS_FULL ? PM_DS_FULL
+                  : p->precision == NB_DD ? PM_DD
                   : (double)n * (double)n <= DS_FULL_MAX_PAIRS ? PM_DS_FULL : PM_DS_NEAR;
         pl.I = pl.mode == PM_FP64 ? 1 : 2;
         const int ipb = TILE * pl.I;

@@ -346,6 +346,246 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
     }
 }
 
+// ---- float-float pair kernel (PM_DD) -------------------------------------------
+// FP64-class accuracy on the FP32 pipes: every quantity of the pair sum is an
+// unevaluated sum hi + lo of two floats (about 48 significant bits), built from
+// Knuth's two-sum, Dekker's fast two-sum and FMA-exact products, packed over two
+// i bodies per f32x2 instruction.  Coordinates are the double-single split of
+// x - c (the paper's 14-digit format, Sect. 5.2); the coordinate difference,
+// r^2 + eps^2, 1/sqrt (a float rsqrt estimate refined by one Newton step in
+// float-float), m / r^3 and the sums are all float-float.  Against a plain FP64
+// sum it agrees to ~1e-14 relative (the 48-bit coordinates alone account for
+// that), so it stands in for the FP64 pipe, which on this GPU runs at 1/77 of
+// the FP32 rate.
+
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __fadd2_rn(a, f2neg(b)); }
+
+// s + e = a + b exactly (Knuth).
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e)
+{
+    s = __fadd2_rn(a, b);
+    const float2 bb = f2sub(s, a);
+    e = __fadd2_rn(f2sub(a, f2sub(s, bb)), f2sub(b, bb));
+}
+
+// s + e = a + b exactly when |a| >= |b| (Dekker).
+__device__ __forceinline__ void fast_two_sum2(float2 a, float2 b, float2 &s, float2 &e)
+{
+    s = __fadd2_rn(a, b);
+    e = f2sub(b, f2sub(s, a));
+}
+
+// (ah + al) - (bh + bl), normalised.
+__device__ __forceinline__ void ff_diff(float2 ah, float2 al, float2 bh, float2 bl, float2 &dh,
+                                        float2 &dl)
+{
+    float2 s, e;
+    two_sum2(ah, f2neg(bh), s, e);
+    e = __fadd2_rn(e, f2sub(al, bl));
+    fast_two_sum2(s, e, dh, dl);
+}
+
+// h^2 + (2 h l) as an unnormalised pair (p, e): p = fl(h^2), e its error plus
+// the cross term.
+__device__ __forceinline__ void ff_sq(float2 h, float2 l, float2 &p, float2 &e)
+{
+    p = __fmul2_rn(h, h);
+    e = __ffma2_rn(h, h, f2neg(p));
+    e = __ffma2_rn(__fadd2_rn(h, h), l, e);
+}
+
+// (ah + al)(bh + bl) without the al bl term, unnormalised.
+__device__ __forceinline__ void ff_mul(float2 ah, float2 al, float2 bh, float2 bl, float2 &p,
+                                       float2 &e)
+{
+    p = __fmul2_rn(ah, bh);
+    e = __ffma2_rn(ah, bh, f2neg(p));
+    e = __ffma2_rn(ah, bl, e);
+    e = __ffma2_rn(al, bh, e);
+}
+
+template <int P>
+struct FFI {
+    float2 xh[P], yh[P], zh[P], xl[P], yl[P], zl[P];         // i coordinates
+    float2 axh[P], axl[P], ayh[P], ayl[P], azh[P], azl[P];   // running sums
+};
+
+template <int P, bool MASK>
+__device__ __forceinline__ void chunk_pass_ff(const float4 (*cb)[4], int j0, int ibase,
+                                              FFI<P> &q, float2 e2h, float2 e2l)
+{
+    const float2 one = make_float2(1.f, 1.f), half = make_float2(0.5f, 0.5f);
+#pragma unroll 2
+    for (int jj = 0; jj < CH; ++jj) {
+        const float4 A = cb[jj][0], B = cb[jj][1], Cl = cb[jj][2], D = cb[jj][3];
+        const float2 xjh = make_float2(A.x, A.y), yjh = make_float2(A.z, A.w);
+        const float2 zjh = make_float2(B.x, B.y), mjh = make_float2(B.z, B.w);
+        const float2 xjl = make_float2(Cl.x, Cl.y), yjl = make_float2(Cl.z, Cl.w);
+        const float2 zjl = make_float2(D.x, D.y), mjl = make_float2(D.z, D.w);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            float2 dxh, dxl, dyh, dyl, dzh, dzl;
+            ff_diff(xjh, xjl, q.xh[p], q.xl[p], dxh, dxl);
+            ff_diff(yjh, yjl, q.yh[p], q.yl[p], dyh, dyl);
+            ff_diff(zjh, zjl, q.zh[p], q.zl[p], dzh, dzl);
+            // r^2 + eps^2
+            float2 px, ex, py, ey, pz, ez;
+            ff_sq(dxh, dxl, px, ex);
+            ff_sq(dyh, dyl, py, ey);
+            ff_sq(dzh, dzl, pz, ez);
+            float2 s1, t1, s2, t2, s3, t3;
+            two_sum2(px, py, s1, t1);
+            two_sum2(s1, pz, s2, t2);
+            two_sum2(s2, e2h, s3, t3);
+            float2 err = __fadd2_rn(__fadd2_rn(__fadd2_rn(ex, ey), __fadd2_rn(ez, e2l)),
+                                    __fadd2_rn(__fadd2_rn(t1, t2), t3));
+            float2 rh, rl;
+            fast_two_sum2(s3, err, rh, rl);
+            // 1 / sqrt(r^2): float estimate, one Newton step in float-float
+            const float2 y0 = make_float2(rsqrt_mufu(rh.x), rsqrt_mufu(rh.y));
+            const float2 th = __fmul2_rn(y0, y0);
+            const float2 tl = __ffma2_rn(y0, y0, f2neg(th));
+            const float2 pp = __fmul2_rn(rh, th);
+            float2 pe = __ffma2_rn(rh, th, f2neg(pp));
+            pe = __ffma2_rn(rh, tl, pe);
+            pe = __ffma2_rn(rl, th, pe);
+            const float2 v = f2sub(f2sub(one, pp), pe);   // 1 - r^2 y0^2 (1 - pp exact)
+            float2 yh, yl;
+            fast_two_sum2(y0, __fmul2_rn(__fmul2_rn(half, y0), v), yh, yl);
+            // s = m / r^3
+            float2 p2, e2, p3, e3, sh, sl;
+            ff_sq(yh, yl, p2, e2);
+            ff_mul(p2, e2, yh, yl, p3, e3);
+            ff_mul(mjh, mjl, p3, e3, sh, sl);
+            if (MASK) {
+                const int j = j0 + jj;
+                if (j == ibase + 2 * p * TILE) sh.x = sl.x = 0.f;
+                if (j == ibase + (2 * p + 1) * TILE) sh.y = sl.y = 0.f;
+            }
+            // a += s d
+            float2 fh, fl, t, te;
+            ff_mul(sh, sl, dxh, dxl, fh, fl);
+            two_sum2(q.axh[p], fh, t, te);
+            q.axh[p] = t;
+            q.axl[p] = __fadd2_rn(q.axl[p], __fadd2_rn(te, fl));
+            ff_mul(sh, sl, dyh, dyl, fh, fl);
+            two_sum2(q.ayh[p], fh, t, te);
+            q.ayh[p] = t;
+            q.ayl[p] = __fadd2_rn(q.ayl[p], __fadd2_rn(te, fl));
+            ff_mul(sh, sl, dzh, dzl, fh, fl);
+            two_sum2(q.azh[p], fh, t, te);
+            q.azh[p] = t;
+            q.azl[p] = __fadd2_rn(q.azl[p], __fadd2_rn(te, fl));
+        }
+    }
+}
+
+template <int P, int KC>
+__global__ void __launch_bounds__(TILE) pair_ff_kernel(
+    const float4 *__restrict__ jd, const float4 *__restrict__ jl,
+    const float *__restrict__ xh, const float *__restrict__ yh, const float *__restrict__ zh,
+    const float *__restrict__ xl, const float *__restrict__ yl, const float *__restrict__ zl,
+    Clusters c, const __grid_constant__ TabOf<KC> tab, Decomp d, double G,
+    double *__restrict__ part, int64_t cap)
+{
+    constexpr int I = 2 * P;
+    __shared__ __align__(16) float4 cbuf[WARPS][CH][4];
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int w = tid >> 5;
+    const float4(*cb)[4] = cbuf[w];
+    const int64_t g = blockIdx.x;
+    int64_t u = d.U(g);
+    const int64_t uend = d.U(g + 1);
+    const float4 far4 = make_float4(FAR_F, FAR_F, FAR_F, FAR_F);
+    const float4 farm = make_float4(FAR_F, FAR_F, 0.f, 0.f);
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    while (u < uend) {
+        const Segment sg = KC > 0 ? segment_at(d, tab, g, u, uend) : segment_at(d, c, g, u, uend);
+        const int n = sg.nk;
+        const int64_t base = sg.base;
+        const float e2hf = KC > 0 ? tab.eps2f[sg.k] : c.eps2f[sg.k];
+        const float e2lf = __double2float_rn(c.eps2d[sg.k] - (double)e2hf);
+        const float2 e2h = make_float2(e2hf, e2hf), e2l = make_float2(e2lf, e2lf);
+        const bool mask_self = d.mask_self != 0;
+        const int ib0 = sg.b * d.ipb;
+        const int ibase = ib0 + tid;
+        const float4 *jdk = jd + 2 * base;
+        const float4 *jlk = jl + 2 * base;
+
+        FFI<P> q;
+        // chunk sums are float-float; they are added into FP64 running sums
+        // after every chunk of CH j bodies, so the float lo word never
+        // accumulates more than CH roundings
+        double dax[I], day[I], daz[I];
+#pragma unroll
+        for (int k = 0; k < I; ++k) dax[k] = day[k] = daz[k] = 0.0;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const int ia = ibase + 2 * p * TILE, ib = ia + TILE;
+            const int64_t ca = base + (ia < n ? ia : n - 1), cb2 = base + (ib < n ? ib : n - 1);
+            q.xh[p] = make_float2(xh[ca], xh[cb2]);
+            q.yh[p] = make_float2(yh[ca], yh[cb2]);
+            q.zh[p] = make_float2(zh[ca], zh[cb2]);
+            q.xl[p] = make_float2(xl[ca], xl[cb2]);
+            q.yl[p] = make_float2(yl[ca], yl[cb2]);
+            q.zl[p] = make_float2(zl[ca], zl[cb2]);
+            q.axh[p] = q.axl[p] = q.ayh[p] = q.ayl[p] = q.azh[p] = q.azl[p] = make_float2(0.f, 0.f);
+        }
+        const int J0 = sg.t0 * d.jt, J1 = sg.t1 * d.jt;
+        float4 pf[4];
+        {
+            const int j = J0 + lane;
+            pf[0] = j < n ? jdk[2 * j] : far4;
+            pf[1] = j < n ? jdk[2 * j + 1] : farm;
+            pf[2] = j < n ? jlk[2 * j] : zero4;
+            pf[3] = j < n ? jlk[2 * j + 1] : zero4;
+        }
+        for (int jc = J0; jc < J1; jc += CH) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) cbuf[w][lane][v] = pf[v];
+            __syncwarp();
+            if (jc + CH < J1) {
+                const int j = jc + CH + lane;
+                pf[0] = j < n ? jdk[2 * j] : far4;
+                pf[1] = j < n ? jdk[2 * j + 1] : farm;
+                pf[2] = j < n ? jlk[2 * j] : zero4;
+                pf[3] = j < n ? jlk[2 * j + 1] : zero4;
+            }
+            const bool diag = mask_self && jc < ib0 + d.ipb && jc + CH > ib0;
+            if (diag)
+                chunk_pass_ff<P, true>(cb, jc, ibase, q, e2h, e2l);
+            else
+                chunk_pass_ff<P, false>(cb, jc, ibase, q, e2h, e2l);
+            __syncwarp();
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                dax[2 * p] += (double)q.axh[p].x + (double)q.axl[p].x;
+                dax[2 * p + 1] += (double)q.axh[p].y + (double)q.axl[p].y;
+                day[2 * p] += (double)q.ayh[p].x + (double)q.ayl[p].x;
+                day[2 * p + 1] += (double)q.ayh[p].y + (double)q.ayl[p].y;
+                daz[2 * p] += (double)q.azh[p].x + (double)q.azl[p].x;
+                daz[2 * p + 1] += (double)q.azh[p].y + (double)q.azl[p].y;
+                q.axh[p] = q.axl[p] = q.ayh[p] = q.ayl[p] = q.azh[p] = q.azl[p] =
+                    make_float2(0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < I; ++k) {
+            const int i = ibase + k * TILE;
+            if (i < n) {
+                double *o = part + (sg.slot * 3) * cap + base + i;
+                o[0] = G * dax[k];
+                o[cap] = G * day[k];
+                o[2 * cap] = G * daz[k];
+            }
+        }
+        u += sg.t1 - sg.t0;
+    }
+}
+
 // Double-precision pair kernel: the plain FP64 baseline (Sect. 4.2's DP mode
 // with structures of four doubles).  The block's j-range is staged through
 // shared memory up to TILE bodies at a time and broadcast to the threads'
@@ -462,6 +702,8 @@ static sp_kernel_t<KC> sp_variant(int mode, int I)
     NB_SP(PM_DS_FULL, 2) NB_SP(PM_DS_FULL, 4)
     NB_SP(PM_FP32, 2) NB_SP(PM_FP32, 4) NB_SP(PM_FP32, 8)
 #undef NB_SP
+    if (mode == PM_DD && I == 2) return pair_ff_kernel<1, KC>;
+    if (mode == PM_DD && I == 4) return pair_ff_kernel<2, KC>;
     return nullptr;
 }
 

@@ -101,7 +101,7 @@ struct nb_server {
     Pool pool;
     RangeAlloc ranges;
     int64_t cap = 0;
-    Group groups[4];
+    Group groups[6];   // (FP64, NB_DS, NB_DD) x (order 2, order 6)
     ClusterSet io;                        // one-cluster set for uploads and downloads
     cudaStream_t io_stream = nullptr;
     std::mutex mu;
@@ -124,7 +124,14 @@ double now_s(const nb_server *s)
     return std::chrono::duration<double>(Clock::now() - s->t0).count();
 }
 
-int group_index(int precision, int order) { return (precision == NB_FP64 ? 0 : 2) + (order == 6 ? 1 : 0); }
+// Group of a job: its arithmetic (FP64 jobs run float-float when the server
+// was created with fp64_via_dd) and its order.
+int group_index(const nb_server *s, int precision, int order)
+{
+    if (precision == NB_FP64 && s->p.fp64_via_dd) precision = NB_DD;
+    const int a = precision == NB_FP64 ? 0 : (precision == NB_DS ? 1 : 2);
+    return 2 * a + (order == 6 ? 1 : 0);
+}
 
 // Copy a job's interleaved host arrays into its pool range (io stream).
 int upload(nb_server *s, Job &j)
@@ -207,7 +214,7 @@ void admit(nb_server *s)
             continue;
         }
         j.state = NB_JOB_RUNNING;
-        j.group = group_index(j.d.precision, j.d.order);
+        j.group = group_index(s, j.d.precision, j.d.order);
         Group &g = s->groups[j.group];
         g.members.push_back(j.id);
         g.dirty = true;
@@ -342,7 +349,7 @@ void run(nb_server *s)
 bool valid_desc(const nb_server *s, const nb_job_desc *d)
 {
     return d && d->n >= 1 && d->n <= s->cap && (d->order == 2 || d->order == 6) &&
-           (d->precision == NB_FP64 || d->precision == NB_DS) &&
+           (d->precision == NB_FP64 || d->precision == NB_DS || d->precision == NB_DD) &&
            std::isfinite(d->dt) && d->dt > 0 && d->nsteps >= 1 && std::isfinite(d->eps) &&
            d->eps >= 0;
 }
@@ -400,9 +407,9 @@ int nb_server_create(const nb_server_params *p, nb_server **out)
     }
     s->cap = cap;
     int rc = pool_create(s->pool, p->device, cap);
-    for (int g = 0; g < 4 && !rc; ++g) {
+    for (int g = 0; g < 6 && !rc; ++g) {
         Group &gr = s->groups[g];
-        gr.precision = g < 2 ? NB_FP64 : NB_DS;
+        gr.precision = g < 2 ? NB_FP64 : (g < 4 ? NB_DS : NB_DD);
         gr.order = (g & 1) ? 6 : 2;
         rc = set_create(gr.set, p->max_jobs, cap);
         if (!rc && (cudaStreamCreateWithFlags(&gr.stream, cudaStreamNonBlocking) != cudaSuccess ||

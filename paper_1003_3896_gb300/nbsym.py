@@ -20,8 +20,9 @@ if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with paper_1003_3896_gb300.build.build()")
 _lib = C.CDLL(LIB_PATH)
 
-NB_FP64, NB_DS, NB_FP32, NB_DS_FULL = 0, 1, 2, 3
-PRECISIONS = {"fp64": NB_FP64, "ds": NB_DS, "fp32": NB_FP32, "ds_full": NB_DS_FULL}
+NB_FP64, NB_DS, NB_FP32, NB_DS_FULL, NB_DD = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": NB_FP64, "ds": NB_DS, "fp32": NB_FP32, "ds_full": NB_DS_FULL,
+              "dd": NB_DD}
 NB_OK, NB_EINVAL, NB_ENOMEM, NB_ECUDA, NB_ESTATE, NB_ETIMEOUT, NB_ENONFINITE = 0, -1, -2, -3, -4, -5, -6
 STATUS_NAMES = {0: "NB_OK", -1: "NB_EINVAL", -2: "NB_ENOMEM", -3: "NB_ECUDA", -4: "NB_ESTATE",
                 -5: "NB_ETIMEOUT", -6: "NB_ENONFINITE"}
@@ -318,7 +319,8 @@ class ServerParams(C.Structure):
     _fields_ = [("device", C.c_int), ("hbm_budget_bytes", C.c_double), ("max_jobs", C.c_int),
                 ("G", C.c_double), ("ext_on", C.c_int), ("Md", C.c_double), ("ad", C.c_double),
                 ("bd", C.c_double), ("Mb", C.c_double), ("ab", C.c_double),
-                ("near_frac", C.c_double), ("Mbh", C.c_double), ("eps_bh", C.c_double)]
+                ("near_frac", C.c_double), ("Mbh", C.c_double), ("eps_bh", C.c_double),
+                ("fp64_via_dd", C.c_int)]
 
 
 class JobDesc(C.Structure):

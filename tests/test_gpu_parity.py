@@ -18,7 +18,8 @@ from paper_1003_3896_gb300 import ics
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "ds": 1e-6, "ds_full": 1e-6, "fp32": 1e-5}
+# NB_DD (float-float pair arithmetic) is held to the FP64 bar
+TOL = {"fp64": 1e-12, "ds": 1e-6, "ds_full": 1e-6, "fp32": 1e-5, "dd": 1e-12}
 
 
 @pytest.fixture(scope="module")
@@ -60,7 +61,7 @@ def test_accel_fp64_small(nbs, orc, n, eps):
     np.testing.assert_allclose(a, ref, rtol=1e-9, atol=1e-12 * np.abs(ref).max())
 
 
-@pytest.mark.parametrize("prec", ["ds", "ds_full", "fp32"])
+@pytest.mark.parametrize("prec", ["ds", "ds_full", "fp32", "dd"])
 @pytest.mark.parametrize("n,offset", [(2, False), (33, True), (129, False), (1000, True),
                                       (4099, True), (9000, False)])
 def test_accel_mixed_small(nbs, orc, prec, n, offset):
@@ -93,7 +94,7 @@ def test_accel_ext_field_fp64(nbs, orc):
 
 def test_unsoftened_two_body(nbs, orc):
     pos, vel, m = ics.kepler_pair(0.6, 0.4, 1.0, 0.5)
-    for prec in ("fp64", "ds", "fp32"):
+    for prec in ("fp64", "ds", "fp32", "dd"):
         with nbs.Context(2, eps=0.0, precision=prec) as c:
             c.load(pos, vel, m)
             a = c.accel()
@@ -105,7 +106,7 @@ def test_coincident_unsoftened_is_reported(nbs):
     pos = np.array([[0.0, 0, 0], [0.0, 0, 0], [1.0, 0, 0]])
     vel = np.zeros((3, 3))
     m = np.ones(3)
-    for prec in ("fp64", "ds"):
+    for prec in ("fp64", "ds", "dd"):
         with nbs.Context(3, eps=0.0, precision=prec) as c:
             c.load(pos, vel, m)
             with pytest.raises(nbs.NBError) as e:
@@ -137,7 +138,7 @@ def test_energy_parity(nbs, orc, ext_on):
 
 
 @pytest.mark.parametrize("order", [2, 6])
-@pytest.mark.parametrize("prec", ["fp64", "ds"])
+@pytest.mark.parametrize("prec", ["fp64", "ds", "dd"])
 def test_four_steps_positions(nbs, orc, order, prec):
     """Positions after 4 steps in the orbit-in-field geometry."""
     n = 2500
@@ -149,7 +150,7 @@ def test_four_steps_positions(nbs, orc, order, prec):
         c.step(order, dt, 4)
         x, v = c.get_state()
     rx, rv = orc.run(pos, vel, m, ext_params(orc, eps, True), order, dt, 4)
-    tol = 1e-10 if prec == "fp64" else 1e-6
+    tol = 1e-10 if prec in ("fp64", "dd") else 1e-6
     assert np.abs(x - rx).max() <= tol, np.abs(x - rx).max()
     assert np.abs(v - rv).max() <= tol * 50
 
@@ -174,7 +175,7 @@ def test_long_run_energy_leapfrog_fp64(nbs, orc):
     assert np.abs(x - rx).max() < 1e-10
 
 
-@pytest.mark.parametrize("prec", ["ds", "fp64"])
+@pytest.mark.parametrize("prec", ["ds", "fp64", "dd"])
 def test_long_run_energy_sixth_order_field(nbs, orc, prec):
     n = 1536
     pos, vel, m = system(n, seed=3, offset=True)
@@ -304,7 +305,7 @@ def test_c2_full_size_sampled(nbs, orc):
     ext = orc.ext_accel(pe, pos[idx])
     with nbs.Context(n, eps=eps, precision="ds", ext_on=True) as c:
         c.load(pos, vel, m)
-        for prec in ("ds", "ds_full", "fp32", "fp64"):
+        for prec in ("ds", "ds_full", "fp32", "fp64", "dd"):
             c.set_precision(prec)
             a = c.accel()[idx] - ext
             err = rel_rms(a, ref)
@@ -320,7 +321,7 @@ def test_c3_full_size_sampled(nbs, orc):
     ref = orc.accel_int_at(pos, m, idx, 1.0, 1e-4)
     with nbs.Context(n, eps=1e-4, precision="ds") as c:
         c.load(pos, vel, m)
-        for prec in ("ds", "fp32", "fp64"):
+        for prec in ("ds", "fp32", "fp64", "dd"):
             c.set_precision(prec)
             a = c.accel()[idx]
             assert rel_rms(a, ref) <= TOL[prec], (prec, rel_rms(a, ref))

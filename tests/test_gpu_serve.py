@@ -133,3 +133,19 @@ def test_bad_jobs_rejected(nbs):
         p2, v2, m2, _ = ic(500, 901)
         with pytest.raises(nbs.NBError):
             srv.submit(p2, v2, m2, 2, 0.01, 1)
+
+
+def test_fp64_jobs_via_float_float(nbs, orc):
+    """With fp64_via_dd the server runs FP64 jobs in float-float arithmetic:
+    the result still meets the FP64 bar against the oracle (4 steps,
+    positions within 1e-10), and NB_DD jobs are accepted directly."""
+    n, order, dt, steps = 1500, 6, 1.0 / 512, 4
+    pos, vel, m, eps = ic(n, 77)
+    rx, _ = orc.run(pos, vel, m, orc.Params(eps=eps), order, dt, steps)
+    with nbs.Server(hbm_budget_bytes=1e9, max_jobs=8, fp64_via_dd=1) as srv:
+        a = srv.submit(pos, vel, m, order, dt, steps, precision="fp64", eps=eps)
+        b = srv.submit(pos, vel, m, order, dt, steps, precision="dd", eps=eps)
+        for jid in (a, b):
+            assert srv.wait(jid, 300)["state"] == nbs.JOB_DONE
+            x, _ = srv.result(jid)
+            assert np.abs(x - rx).max() <= 1e-10, np.abs(x - rx).max()
