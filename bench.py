@@ -258,7 +258,7 @@ def main():
     ap.add_argument("--tune-load", default="",
                     help="load a tuned-shape table (nb_tune_load) and skip tuning, so a "
                          "profiled run times the same kernel shapes as the run that saved it")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5", "paper", "plunge"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5", "paper", "plunge", "sym"],
                     help="c2 (default): the headline line; the others print their own "
                          "labelled lines (see bench_workloads.py)")
     ap.add_argument("--jobs", type=int, default=48, help="c5: jobs in the bounded trace")

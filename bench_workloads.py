@@ -26,6 +26,9 @@ bench.py.  Inputs are seeded and synthetic (paper_1003_3896_gb300.ics).
       t in [0, 4] (NB_PLUNGE_STEPS steps, default 20000), mixed precision: relative
       energy and angular momentum changes (the quantities of Table 8) and
       the external torque of eq. 8 at the start and the end.
+  sym  The N(N-1)/2 variant (each unordered pair once, Newton's third law;
+      float class) against the full N x N float kernel on Plummer spheres of
+      N = 16384, 65536, 262144: pair-kernel time and N^2 / time for both.
   paper  The paper's own test workload (Sect. 3, Sect. 5.1): a uniform sphere
       (R = 1, M = 1, virial ratio Q = 0.3) at the sizes of its Table 3,
       N = 480, 30720 and 1536000, one leapfrog step per precision (FP64 only
@@ -350,6 +353,37 @@ def plunge(args, nbsym, torch):
             "note": "Table 8 values are context only: another field, other units"}
 
 
+def sym(args, nbsym, torch):
+    rows = []
+    for n in (16384, 65536, 262144):
+        pos, vel, m = ics.henon_plummer(n, 0)
+        eps = ics.paper_softening(n)
+        with nbsym.Context(n, eps=eps, precision="fp32") as c:
+            c.load(pos, vel, m)
+            if not args.no_tune:
+                c.tune(reps=3)
+            c.accel()
+            c.prof_enable(True)
+            full = c.accel()
+            pr = c.prof_read()
+            c.prof_enable(False)
+            c.accel_symmetric()
+            times = []
+            for _ in range(3):
+                a, ms = c.accel_symmetric()
+                times.append(ms)
+        ms = sorted(times)[1]
+        rows.append({"n": n, "full_ms": pr["pair_ms"], "sym_ms": ms,
+                     "full_gpairs_s": n * n / (pr["pair_ms"] * 1e-3) / 1e9,
+                     "sym_gpairs_s": n * n / (ms * 1e-3) / 1e9,
+                     "sym_over_full": pr["pair_ms"] / ms,
+                     "rel_diff": float(np.sqrt(((a - full) ** 2).sum() / (full ** 2).sum()))})
+    return {"metric": "N(N-1)/2 variant vs full N^2 sum (float class)", "unit": UNIT,
+            "value": rows[-1]["sym_gpairs_s"], "higher_is_better": True,
+            "workload": "henon_plummer_N16384_65536_262144_fp32", "rows": rows,
+            "note": "interactions counted as N^2 for both, so the rates compare time"}
+
+
 def run(args):
     """One workload line.  Under torchrun only the ensemble (c4) shards across
     ranks (whole clusters per rank); the single-system workloads run on rank
@@ -371,7 +405,7 @@ def run(args):
         torch.distributed.barrier()
     from paper_1003_3896_gb300 import nbsym
     fn = {"c1": c1, "c3": c3, "c4": c4, "c5": c5, "paper": paper,
-          "plunge": plunge}[args.workload]
+          "plunge": plunge, "sym": sym}[args.workload]
     line = fn(args, nbsym, torch)
     line["impl"] = "ours"
     line["data"] = "synthetic"

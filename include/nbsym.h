@@ -274,6 +274,19 @@ int nb_measure_peaks(int device, nb_peaks_t *out);
 int nb_accel_static(const nb_params *p, int64_t n, const double *d_pos,
                     const double *d_mass, double *d_acc_out);
 
+/* The N(N-1)/2 variant of the internal sum (Newton's third law: each
+ * unordered pair evaluated once and its force added to both bodies), which
+ * the paper rejects for its GPU (Sect. 4.2); provided to measure it here.
+ * Accelerations of the loaded one-cluster state (internal sum of eq. 5 in
+ * float arithmetic on frame-centred coordinates, the class of NB_FP32, plus
+ * the external field when ext_on) to acc_out (n rows of x, y, z, host),
+ * whatever the context's precision; the pair kernel's time (CUDA events) to
+ * *pair_ms when pair_ms is not NULL.  Sums are combined with float atomics,
+ * so results are not bit-reproducible.  Allocates and frees 36 bytes per body
+ * of device memory per call; synchronous.  Errors: NB_EINVAL (NULL, more than
+ * one cluster), NB_ESTATE (nothing loaded), NB_ENOMEM, NB_ECUDA. */
+int nb_accel_symmetric(nb_ctx *ctx, double *acc_out, double *pair_ms);
+
 /* ---- autotuner (no counterpart in the paper: the paper fixes one block
  * shape for its GPU, Sect. 4.2) ---------------------------------------------
  * The launch shape of the pair kernel is (bodies per thread I, j-tile width

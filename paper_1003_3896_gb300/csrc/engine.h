@@ -157,6 +157,13 @@ int enq_energy(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &p
 int enq_torque(const Pool &P, const ClusterSet &C, const Phys &ph, cudaStream_t st,
                int64_t *kernels);
 
+// N(N-1)/2 variant (sym.cu): accelerations of a one-cluster set with each
+// unordered pair evaluated once, float arithmetic, float-atomic sums in acc
+// (device, 3 n floats); interleaved double rows to out (device).  e0/e1
+// bracket the pair kernel.  Needs the float planes current.
+int sym_accel(const Pool &P, const ClusterSet &C, const Phys &ph, float *acc, double *out,
+              cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1);
+
 // SI6A weights (Kinoshita, Yoshida & Nakai 1991, Table 1 first column =
 // Yoshida's 1990 solution A); w0 = 1 - 2 (w1 + w2 + w3).
 constexpr double SI6_W1 = -1.17767998417887;

@@ -571,6 +571,56 @@ int nb_set_precision(nb_ctx *c, int precision)
     return NB_OK;
 }
 
+int nb_accel_symmetric(nb_ctx *c, double *acc_out, double *pair_ms)
+{
+    if (!c || !acc_out) return set_error(NB_EINVAL, "NULL argument");
+    if (c->n == 0) return set_error(NB_ESTATE, "nb_accel_symmetric before nb_load");
+    if (c->set.K != 1) return set_error(NB_EINVAL, "nb_accel_symmetric takes one cluster");
+    DeviceGuard dg(c->p.device);
+    const int64_t n = c->n;
+    float *acc = nullptr;
+    double *out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = NB_OK;
+    do {
+        if (cudaMalloc(&acc, sizeof(float) * 3 * (size_t)n) != cudaSuccess ||
+            cudaMalloc(&out, sizeof(double) * 3 * (size_t)n) != cudaSuccess) {
+            cudaGetLastError();
+            rc = set_error(NB_ENOMEM, "device allocation failed");
+            break;
+        }
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+            rc = set_error(NB_ECUDA, "event creation failed");
+            break;
+        }
+        // float planes about a fresh frame (the context's own split, if any,
+        // is recomputed before its next float-plane use)
+        const DevState s = view(c->pool, c->set, NB_FP32);
+        if (launch_frame(s, c->phys.near_frac, false, c->stream) != cudaSuccess ||
+            launch_split(s, c->stream) != cudaSuccess) {
+            rc = set_error(NB_ECUDA, "frame/split launch failed");
+            break;
+        }
+        c->split_stale = true;
+        rc = sym_accel(c->pool, c->set, c->phys, acc, out, c->stream, e0, e1);
+        if (rc) break;
+        if (cudaMemcpyAsync(acc_out, out, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToHost,
+                            c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            rc = set_error(NB_ECUDA, "copy-out failed: %s", cudaGetErrorString(cudaGetLastError()));
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (pair_ms) *pair_ms = ms;
+    } while (0);
+    if (acc) cudaFree(acc);
+    if (out) cudaFree(out);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return rc;
+}
+
 int nb_tune(nb_ctx *c, int reps, nb_tune_t *out)
 {
     if (!c) return set_error(NB_EINVAL, "ctx is NULL");

@@ -97,6 +97,7 @@ nb_clusters = _sig("nb_clusters", C.c_int64, _ctxp)
 nb_energy_clusters = _sig("nb_energy_clusters", C.c_int, _ctxp, C.POINTER(EnergyT))
 nb_accel_static = _sig("nb_accel_static", C.c_int, C.POINTER(Params), C.c_int64, _vp, _vp, _vp)
 nb_tune = _sig("nb_tune", C.c_int, _ctxp, C.c_int, C.POINTER(TuneT))
+nb_accel_symmetric = _sig("nb_accel_symmetric", C.c_int, _ctxp, _dp, C.POINTER(C.c_double))
 nb_tune_save = _sig("nb_tune_save", C.c_int, C.c_char_p)
 nb_tune_load = _sig("nb_tune_load", C.c_int64, C.c_char_p)
 nb_tune_entries = _sig("nb_tune_entries", C.c_int64)
@@ -288,6 +289,13 @@ class Context:
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
         check(nb_set_precision(self._h, int(precision)))
+
+    def accel_symmetric(self):
+        """(accelerations, pair-kernel ms) from the N(N-1)/2 float variant."""
+        out = np.empty((self.n, 3))
+        ms = C.c_double()
+        check(nb_accel_symmetric(self._h, _p(out), C.byref(ms)))
+        return out, ms.value
 
     def tune(self, reps: int = 3) -> dict:
         """Time every compiled pair-kernel shape on the loaded state and keep
