@@ -97,7 +97,7 @@ int set_create(ClusterSet &C, int32_t kcap, int64_t body_cap)
     const size_t bytes = al(k8) * 2 + al(k81) * 3 + al((size_t)kcap * 4) * 2 + al(k8) * 2 +
                          al((size_t)C.scap * 4) + al((size_t)C.scap * 8) * 2 +
                          al((size_t)(kcap + 1) * 4) + al((size_t)kcap * sizeof(Frame)) +
-                         al((size_t)kcap * DIAG_STRIDE * 8);
+                         al((size_t)kcap * DIAG_STRIDE * 8) + al(k8);
     if (cudaMalloc(&C.dmem, bytes) != cudaSuccess) {
         cudaGetLastError();
         C.dmem = nullptr;
@@ -236,6 +236,8 @@ int set_layout(ClusterSet &C, int ipb, cudaStream_t st, int jt)
     int32_t *d_segoff = (int32_t *)take((size_t)(C.kcap + 1) * 4);
     C.frame = (Frame *)take((size_t)C.kcap * sizeof(Frame));
     C.diag = (double *)take((size_t)C.kcap * DIAG_STRIDE * 8);
+    double *d_mu = (double *)take(k8);
+    if ((int32_t)C.mu.size() != K) C.mu.assign(K, 0.0);
     auto up = [&](void *dst, const void *src, size_t bytes) {
         return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st)
                      : cudaSuccess;
@@ -249,6 +251,7 @@ int set_layout(ClusterSet &C, int ipb, cudaStream_t st, int jt)
     NB_TRY(up(d_eps2f, C.eps2f.data(), K * 4));
     NB_TRY(up(d_eps2d, C.eps2d.data(), K * 8));
     NB_TRY(up(d_dts, C.dts.data(), K * 8));
+    NB_TRY(up(d_mu, C.mu.data(), K * 8));
     NB_TRY(up(d_segk, C.seg_k.data(), S * 4));
     NB_TRY(up(d_seglo, C.seg_lo.data(), S * 8));
     NB_TRY(up(d_seghi, C.seg_hi.data(), S * 8));
@@ -263,6 +266,7 @@ int set_layout(ClusterSet &C, int ipb, cudaStream_t st, int jt)
     c.eps2f = d_eps2f;
     c.eps2d = d_eps2d;
     c.dts = d_dts;
+    c.mu = d_mu;
     c.frame = C.frame;
     c.S = (int32_t)S;
     c.seg_k = d_segk;
@@ -340,6 +344,8 @@ int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan
     }
     int rc = set_layout(C, TILE * I, st, jt);
     if (rc) return rc;
+    pl.pl.um = pl.pl.mode != PM_FP64 && pl.pl.mode != PM_DD;
+    for (int32_t k = 0; k < C.K && pl.pl.um; ++k) pl.pl.um = C.mu[k] > 0;
     const int64_t W = C.uoff[C.K];
     int64_t G = want < W ? want : W;   // at least one unit per block
     pl.pl.d = make_decomp(W, C.max_ntiles, TILE * I, G, P.s.part_slots, jt);
@@ -437,11 +443,12 @@ int enq_force(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph
     ht.nk = C.nk.data();
     ht.ntiles = C.ntiles.data();
     ht.eps2f = C.eps2f.data();
+    ht.mu = C.mu.data();
     NB_TRY(launch_pair(s, pl.pl, ht, ph.G, st));
     if (ev1) NB_TRY(cudaEventRecordWithFlags(ev1, st, evf));
     count(kernels, 1);
     if (pl.pl.mode == PM_DS_NEAR) {
-        NB_TRY(launch_near_correct(s, ph.G, st));
+        NB_TRY(launch_near_correct(s, ph.G, pl.pl.um, st));
         count(kernels, NEAR_KERNELS);
     }
     return NB_OK;

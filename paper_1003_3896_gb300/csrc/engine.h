@@ -46,6 +46,8 @@ struct ClusterSet {
     std::vector<int32_t> ntiles, seg_k, seg_off;
     std::vector<float> eps2f;
     std::vector<double> eps, eps2d, dts;
+    std::vector<double> mu;    // common mass per cluster (0: masses differ); set by
+                               // the loader before planning, uploaded by set_layout
     char *dmem = nullptr;      // device copy of the tables
     double *red = nullptr;     // reduction partials [scap][16]
     // per-set scratch, so sets in one pool can run concurrently on different

@@ -203,6 +203,55 @@ __global__ void frame_final_kernel(DevState s, double near_frac)
     }
 }
 
+// Smallest and largest mass per segment, then per cluster (into diag[k][0..1]).
+__global__ void mass_range_partial_kernel(DevState s)
+{
+    __shared__ double lo_sh[RT], hi_sh[RT];
+    const int sg = blockIdx.x;
+    const int32_t k = s.cl.seg_k[sg];
+    const int64_t base = s.cl.boff[k] - s.cl.noff[k];
+    double lo = INFINITY, hi = -INFINITY;
+    for (int64_t t = s.cl.seg_lo[sg] + threadIdx.x; t < s.cl.seg_hi[sg]; t += RT) {
+        const double m = s.m[base + t];
+        lo = fmin(lo, m);
+        hi = fmax(hi, m);
+    }
+    lo_sh[threadIdx.x] = lo;
+    hi_sh[threadIdx.x] = hi;
+    __syncthreads();
+    for (int w = RT / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            lo_sh[threadIdx.x] = fmin(lo_sh[threadIdx.x], lo_sh[threadIdx.x + w]);
+            hi_sh[threadIdx.x] = fmax(hi_sh[threadIdx.x], hi_sh[threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        s.red[(int64_t)sg * 16] = lo_sh[0];
+        s.red[(int64_t)sg * 16 + 1] = hi_sh[0];
+    }
+}
+
+__global__ void mass_range_final_kernel(DevState s)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= s.cl.K) return;
+    double lo = INFINITY, hi = -INFINITY;
+    for (int sg = s.cl.seg_off[k]; sg < s.cl.seg_off[k + 1]; ++sg) {
+        lo = fmin(lo, s.red[(int64_t)sg * 16]);
+        hi = fmax(hi, s.red[(int64_t)sg * 16 + 1]);
+    }
+    s.diag[(int64_t)k * DIAG_STRIDE] = lo;
+    s.diag[(int64_t)k * DIAG_STRIDE + 1] = hi;
+}
+
+cudaError_t launch_mass_range(const DevState &s, cudaStream_t st)
+{
+    mass_range_partial_kernel<<<s.cl.S, RT, 0, st>>>(s);
+    mass_range_final_kernel<<<(s.cl.K + 127) / 128, 128, 0, st>>>(s);
+    return cudaGetLastError();
+}
+
 // Harmonic moment about the frame origin: sum m / |x - c| (per segment),
 // with a floor of 1e-3 R_rms on the distance.
 __global__ void frame_harmonic_kernel(DevState s)

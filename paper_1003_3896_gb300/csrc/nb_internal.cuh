@@ -48,6 +48,8 @@ struct Clusters {
     const int64_t *seg_hi = nullptr;
     const int32_t *seg_off = nullptr;// [K+1] segments of cluster k: [seg_off[k], seg_off[k+1])
     const int32_t *cid = nullptr;    // [noff[K]] cluster of each linear body (K > 1)
+    const double *mu = nullptr;      // [K]   the common mass of cluster k's bodies, 0 if
+                                     //       they differ
 };
 
 // Cluster of linear body t: one load from the precomputed map (K = 1: 0).
@@ -172,6 +174,9 @@ struct PairLaunch {
     int I;           // i-bodies per thread
     int blocks_per_sm;
     Decomp d;
+    // every cluster has equal masses (mu[k] > 0): the single-precision
+    // kernels leave m out of the pair term and scale the sums by mu[k]
+    bool um = false;
 };
 
 // Host copy of the per-cluster values the pair kernels need per segment.  Up
@@ -190,6 +195,7 @@ struct HostTab {
     const int64_t *uoff = nullptr, *boff = nullptr, *nk = nullptr;
     const int32_t *ntiles = nullptr;
     const float *eps2f = nullptr;
+    const double *mu = nullptr;
 };
 
 // Resident blocks per SM of a pair-kernel variant (occupancy query).
@@ -210,7 +216,9 @@ cudaError_t launch_potential(const DevState &s, const Decomp &d, cudaStream_t st
 int64_t near_table_size(int64_t n);
 // corr_i = G sum over pairs closer than the cluster's near radius of the
 // double-single minus the float contribution (written to s.corr).
-cudaError_t launch_near_correct(const DevState &s, double G, cudaStream_t st);
+// um: the pair kernel left the (uniform) mass out of the pair term; the
+// correction does the same and scales by cl.mu[k].
+cudaError_t launch_near_correct(const DevState &s, double G, bool um, cudaStream_t st);
 
 // ---- launchers (integrate.cu) ----------------------------------------------
 // Fill the body -> cluster map cid[0, n) of a cluster set.
@@ -222,6 +230,8 @@ cudaError_t launch_pack(const DevState &s, double *pos, double *vel, cudaStream_
 // Frame origin and rms radius of every cluster; with near, also the
 // near-pair radius of the mixed mode's correction pass (2 or 4 kernels).
 cudaError_t launch_frame(const DevState &s, double near_frac, bool near, cudaStream_t st);
+// Smallest and largest mass of every cluster into diag[k][0], diag[k][1].
+cudaError_t launch_mass_range(const DevState &s, cudaStream_t st);
 cudaError_t launch_split(const DevState &s, cudaStream_t st);
 // One fused substep: optional kick v += wk dt_k (a_int + a_ext) from the
 // partial slots of decomposition d, then drift x += wd dt_k v, then

@@ -55,6 +55,7 @@ struct nb_ctx {
     bool batch = false;
     std::vector<int64_t> sizes;    // batch cluster sizes
     std::vector<double> eps_k, dts_k;
+    std::vector<double> mu_k;      // common mass per cluster (0: masses differ)
     int64_t n = 0;                 // bodies loaded (0: none)
     bool planned = false;
     bool split_stale = true;
@@ -134,6 +135,10 @@ int replan(nb_ctx *c, int64_t n)
     int rc = set_define(c->set, (int32_t)nk.size(), boff.data(), nk.data(), c->eps_k.data(),
                         c->dts_k.data());
     if (rc) return rc;
+    if (c->mu_k.size() == nk.size())
+        c->set.mu = c->mu_k;
+    else
+        c->set.mu.assign(nk.size(), 0.0);
     rc = plan_make(c->pool, c->set, c->p.precision, c->stream, c->plan);
     if (rc) return rc;
     free_graphs(c);
@@ -340,7 +345,24 @@ static int load_common(nb_ctx *c, int64_t n, const double *pos, const double *ve
         dm = sm;
     }
     NB_TRY(launch_unpack(view(c->pool, c->set, c->p.precision), dp, dv, dm, c->stream));
+    // clusters whose bodies all have one mass get the pair kernels' uniform-
+    // mass form; the plan follows the masses
+    NB_TRY(launch_mass_range(view(c->pool, c->set, c->p.precision), c->stream));
+    const int32_t K = c->set.K;
+    std::vector<double> range((size_t)K * DIAG_STRIDE);
+    NB_TRY(cudaMemcpyAsync(range.data(), c->set.diag, range.size() * sizeof(double),
+                           cudaMemcpyDeviceToHost, c->stream));
     NB_TRY(cudaStreamSynchronize(c->stream));
+    std::vector<double> mu((size_t)K);
+    for (int32_t k = 0; k < K; ++k) {
+        const double lo = range[(size_t)k * DIAG_STRIDE], hi = range[(size_t)k * DIAG_STRIDE + 1];
+        mu[k] = lo == hi && lo > 0 && std::isfinite(lo) ? lo : 0.0;
+    }
+    if (mu != c->mu_k) {
+        c->mu_k = mu;
+        int rc = replan(c, n);
+        if (rc) return rc;
+    }
     c->split_stale = true;
     return NB_OK;
 }

@@ -199,7 +199,10 @@ __global__ void near_rank_kernel(DevState s)
 }
 
 // One thread per body t: probe its 8 cells (first loads issued together),
-// then visit their bodies in cell order.
+// then visit their bodies in cell order.  UM: the pair kernel left the common
+// mass out of the pair term (multiplying its sums by it afterwards); the
+// correction repeats exactly that and scales by the cluster's mass.
+template <bool UM>
 __global__ void __launch_bounds__(256) near_correct_kernel(DevState s, uint32_t mask, int64_t H,
                                                            double G)
 {
@@ -254,7 +257,8 @@ __global__ void __launch_bounds__(256) near_correct_kernel(DevState s, uint32_t 
                 r2 = __fmaf_rn(ddz, ddz, r2);
                 if (!(r2 < th2)) continue;
                 const float ri = near_rsqrt(r2);
-                const float sf = __fmul_rn(__fmul_rn(mj, ri), __fmul_rn(ri, ri));
+                const float sf = UM ? __fmul_rn(ri, __fmul_rn(ri, ri))
+                                    : __fmul_rn(__fmul_rn(mj, ri), __fmul_rn(ri, ri));
                 // the same pair with the double-single coordinate difference
                 const float ex = __fadd_rn(ddx, __fsub_rn(Lj.x, lxi));
                 const float ey = __fadd_rn(ddy, __fsub_rn(Lj.y, lyi));
@@ -263,7 +267,8 @@ __global__ void __launch_bounds__(256) near_correct_kernel(DevState s, uint32_t 
                 e2 = __fmaf_rn(ey, ey, e2);
                 e2 = __fmaf_rn(ez, ez, e2);
                 const float re = near_rsqrt(e2);
-                const float se = __fmul_rn(__fmul_rn(mj, re), __fmul_rn(re, re));
+                const float se = UM ? __fmul_rn(re, __fmul_rn(re, re))
+                                    : __fmul_rn(__fmul_rn(mj, re), __fmul_rn(re, re));
                 ax += (double)__fmul_rn(ex, se) - (double)__fmul_rn(ddx, sf);
                 ay += (double)__fmul_rn(ey, se) - (double)__fmul_rn(ddy, sf);
                 az += (double)__fmul_rn(ez, se) - (double)__fmul_rn(ddz, sf);
@@ -271,9 +276,10 @@ __global__ void __launch_bounds__(256) near_correct_kernel(DevState s, uint32_t 
         }
     }
     const int64_t i = s.cl.boff[k] + t - s.cl.noff[k];
-    s.corr[i] = G * ax;
-    s.corr[s.cap + i] = G * ay;
-    s.corr[2 * s.cap + i] = G * az;
+    const double Gm = UM ? G * s.cl.mu[k] : G;
+    s.corr[i] = Gm * ax;
+    s.corr[s.cap + i] = Gm * ay;
+    s.corr[2 * s.cap + i] = Gm * az;
 }
 
 int64_t near_table_size(int64_t n)
@@ -283,7 +289,7 @@ int64_t near_table_size(int64_t n)
     return H;
 }
 
-cudaError_t launch_near_correct(const DevState &s, double G, cudaStream_t st)
+cudaError_t launch_near_correct(const DevState &s, double G, bool um, cudaStream_t st)
 {
     const int64_t H = near_table_size(s.n);
     if (H > s.ng_hcap) return cudaErrorInvalidValue;
@@ -301,7 +307,10 @@ cudaError_t launch_near_correct(const DevState &s, double G, cudaStream_t st)
     scan_add_kernel<<<nbh, 256, 0, st>>>(s.ng_start, s.ng_bsum, H, s.n);
     near_scatter_kernel<<<nbn, 256, 0, st>>>(s);
     near_rank_kernel<<<nbn, 256, 0, st>>>(s);
-    near_correct_kernel<<<nbn, 256, 0, st>>>(s, mask, H, G);
+    if (um)
+        near_correct_kernel<true><<<nbn, 256, 0, st>>>(s, mask, H, G);
+    else
+        near_correct_kernel<false><<<nbn, 256, 0, st>>>(s, mask, H, G);
     return cudaGetLastError();
 }
 

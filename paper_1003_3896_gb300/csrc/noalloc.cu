@@ -282,7 +282,7 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
         }
         // the mixed mode re-forms near pairs from the double-single difference
         if (pl.mode == PM_DS_NEAR) {
-            if (launch_near_correct(s, p->G, st) != cudaSuccess) {
+            if (launch_near_correct(s, p->G, false, st) != cudaSuccess) {
                 rc = NB_ECUDA;
                 break;
             }

@@ -89,6 +89,7 @@ struct ParamTab {
     int32_t K;
     int64_t uoff[KC + 1];
     int64_t boff[KC];
+    double mu[KC];
     int32_t nk[KC];
     int32_t ntiles[KC];
     float eps2f[KC];
@@ -157,8 +158,9 @@ struct IPairs {
 
 // One chunk of CH j bodies (local indices j0 ...) against the thread's 2P i
 // bodies (local indices ibase + k * TILE).  MASK zeroes the j == i term
-// (eps = 0, diagonal chunks).
-template <int P, int MODE, bool MASK>
+// (eps = 0, diagonal chunks).  UM (all masses of the cluster equal): the pair
+// term is d / r^3 without m_j, one multiply fewer; the caller scales by m.
+template <int P, int MODE, bool MASK, bool UM>
 __device__ __forceinline__ void chunk_pass(const float4 (*cb)[4], int j0, int ibase,
                                            IPairs<P> &ip, float eps2)
 {
@@ -194,7 +196,8 @@ __device__ __forceinline__ void chunk_pass(const float4 (*cb)[4], int j0, int ib
                 r2 = __ffma2_rn(dy, dy, r2);
                 r2 = __ffma2_rn(dz, dz, r2);
                 const float2 ri = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
-                float2 s = __fmul2_rn(__fmul2_rn(mm, ri), __fmul2_rn(ri, ri));
+                float2 s = UM ? __fmul2_rn(ri, __fmul2_rn(ri, ri))
+                              : __fmul2_rn(__fmul2_rn(mm, ri), __fmul2_rn(ri, ri));
                 if (MASK) {
                     const int j = j0 + jj;
                     if (j == ibase + 2 * p * TILE) s.x = 0.f;
@@ -217,7 +220,7 @@ __host__ __device__ constexpr int sp_min_blocks(int P) { return P == 1 ? 8 : (P 
 template <int KC>
 using TabOf = ParamTab<KC == 0 ? 1 : KC>;
 
-template <int P, int MODE, int KC>
+template <int P, int MODE, int KC, bool UM>
 __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
     const float4 *__restrict__ jd, const float4 *__restrict__ jl,
     const float *__restrict__ xh, const float *__restrict__ yh, const float *__restrict__ zh,
@@ -298,9 +301,9 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
             }
             const bool diag = mask_self && jc < ib0 + d.ipb && jc + CH > ib0;
             if (diag)
-                chunk_pass<P, MODE, true>(cb, jc, ibase, ip, eps2);
+                chunk_pass<P, MODE, true, UM>(cb, jc, ibase, ip, eps2);
             else
-                chunk_pass<P, MODE, false>(cb, jc, ibase, ip, eps2);
+                chunk_pass<P, MODE, false, UM>(cb, jc, ibase, ip, eps2);
             __syncwarp();
             if (((jc + CH - J0) & (TILE - 1)) == 0 || jc + CH >= J1) {
                 // every TILE j and at the segment's end: fold the tile sums
@@ -331,6 +334,7 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
             }
         }
 
+        const double Gm = UM ? G * (KC > 0 ? tab.mu[sg.k] : c.mu[sg.k]) : G;
 #pragma unroll
         for (int kk = 0; kk < I; ++kk) {
             const int i = ibase + kk * TILE;
@@ -338,8 +342,8 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
                 double *o = part + (sg.slot * 3) * cap + base + i;
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc)
-                    o[cc * cap] = G * ((double)acc_sh[cc * I + kk][tid] +
-                                       (double)acc_sh[(3 + cc) * I + kk][tid]);
+                    o[cc * cap] = Gm * ((double)acc_sh[cc * I + kk][tid] +
+                                        (double)acc_sh[(3 + cc) * I + kk][tid]);
             }
         }
         u += sg.t1 - sg.t0;
@@ -694,10 +698,11 @@ typedef void (*dp_kernel_t)(const double *, const double *, const double *, cons
 
 // I (bodies per thread) = 2P for the single-precision family.
 template <int KC>
-static sp_kernel_t<KC> sp_variant(int mode, int I)
+static sp_kernel_t<KC> sp_variant(int mode, int I, bool um = false)
 {
-#define NB_SP(M, II) \
-    if (mode == M && I == II) return pair_sp_kernel<II / 2, M, KC>;
+#define NB_SP(M, II)                                                      \
+    if (mode == M && I == II)                                             \
+        return um ? pair_sp_kernel<II / 2, M, KC, true> : pair_sp_kernel<II / 2, M, KC, false>;
     NB_SP(PM_DS_NEAR, 2) NB_SP(PM_DS_NEAR, 4) NB_SP(PM_DS_NEAR, 8)
     NB_SP(PM_DS_FULL, 2) NB_SP(PM_DS_FULL, 4)
     NB_SP(PM_FP32, 2) NB_SP(PM_FP32, 4) NB_SP(PM_FP32, 8)
@@ -714,7 +719,7 @@ template <int KC>
 static cudaError_t launch_sp(const DevState &s, const PairLaunch &pl, const HostTab &ht,
                              double G, cudaStream_t st)
 {
-    sp_kernel_t<KC> k = sp_variant<KC>(pl.mode, pl.I);
+    sp_kernel_t<KC> k = sp_variant<KC>(pl.mode, pl.I, pl.um && pl.mode != PM_DD);
     if (!k) return cudaErrorInvalidValue;
     TabOf<KC> t;
     std::memset(&t, 0, sizeof t);
@@ -727,6 +732,7 @@ static cudaError_t launch_sp(const DevState &s, const PairLaunch &pl, const Host
             t.nk[q] = (int32_t)ht.nk[q];
             t.ntiles[q] = ht.ntiles[q];
             t.eps2f[q] = ht.eps2f[q];
+            t.mu[q] = ht.mu ? ht.mu[q] : 0.0;
         }
         t.uoff[ht.K] = ht.uoff[ht.K];
     }

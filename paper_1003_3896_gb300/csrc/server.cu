@@ -35,6 +35,7 @@ struct Job {
     int64_t id = 0;
     nb_job_desc d{};
     std::vector<double> pos, vel, mass;   // initial conditions, then the result
+    double mu = 0;                        // the common mass of its bodies (0: they differ)
     int state = NB_JOB_QUEUED;
     int64_t steps_done = 0;
     double t_submit = 0, t_admit = 0, t_done = 0;
@@ -265,16 +266,18 @@ int launch_step(nb_server *s, Group &g)
     if (g.members.empty()) return NB_OK;
     if (g.dirty) {
         std::vector<int64_t> boff, nk;
-        std::vector<double> eps, dts;
+        std::vector<double> eps, dts, mu;
         for (int64_t id : g.members) {
             const Job &j = *s->jobs[id];
             boff.push_back(j.off);
             nk.push_back(j.d.n);
             eps.push_back(j.d.eps);
             dts.push_back(j.d.dt);
+            mu.push_back(j.mu);
         }
         int rc = set_define(g.set, (int32_t)nk.size(), boff.data(), nk.data(), eps.data(),
                             dts.data());
+        g.set.mu = mu;
         if (!rc) rc = plan_make(s->pool, g.set, g.precision, g.stream, g.plan);
         if (rc) return rc;
         g.dirty = false;
@@ -465,6 +468,9 @@ int nb_server_submit(nb_server *s, const nb_job_desc *d, const double *pos, cons
     j->pos.assign(pos, pos + 3 * d->n);
     j->vel.assign(vel, vel + 3 * d->n);
     j->mass.assign(mass, mass + d->n);
+    j->mu = mass[0] > 0 && std::isfinite(mass[0]) ? mass[0] : 0.0;
+    for (int64_t q = 1; q < d->n && j->mu > 0; ++q)
+        if (mass[q] != j->mu) j->mu = 0.0;
     std::lock_guard<std::mutex> lk(s->mu);
     if (!s->fatal.empty()) return set_error(NB_ECUDA, "server stopped: %s", s->fatal.c_str());
     j->id = s->next_id++;

@@ -148,6 +148,7 @@ static int time_plan(const Pool &P, const ClusterSet &C, const Plan &pl, const P
     ht.nk = C.nk.data();
     ht.ntiles = C.ntiles.data();
     ht.eps2f = C.eps2f.data();
+    ht.mu = C.mu.data();
     NB_TRY(launch_pair(s, pl.pl, ht, ph.G, st));
     NB_TRY(cudaEventRecord(e0, st));
     for (int r = 0; r < reps; ++r) NB_TRY(launch_pair(s, pl.pl, ht, ph.G, st));

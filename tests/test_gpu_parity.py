@@ -380,3 +380,25 @@ def test_mixed_with_escapers_stays_accurate_and_fast(nbs, orc):
         wall = time.perf_counter() - t0
     assert rel_rms(a, ref) <= TOL["ds"], rel_rms(a, ref)
     assert wall < 0.5, wall
+
+
+@pytest.mark.parametrize("prec", ["ds", "fp32", "ds_full"])
+def test_uniform_mass_form_matches_general_form(nbs, orc, prec):
+    """Equal masses take the pair kernels' uniform-mass form (m factored out
+    of the pair term); nudging one mass by 2^-40 forces the general form.
+    Both meet the oracle bar and agree with each other to it."""
+    n = 20000 if prec != "ds_full" else 4099
+    pos, vel, m = system(n, seed=41, offset=True)
+    m2 = m.copy()
+    m2[17] *= 1.0 + 2.0 ** -40
+    eps = ics.paper_softening(n)
+    out = []
+    for mm in (m, m2):
+        ref = orc.accel_int(pos, mm, 1.0, eps)
+        with nbs.Context(n, eps=eps, precision=prec) as c:
+            c.load(pos, vel, mm)
+            a = c.accel()
+        tol = 1e-4 if prec == "fp32" else TOL[prec]
+        assert rel_rms(a, ref) <= tol, rel_rms(a, ref)
+        out.append(a)
+    assert rel_rms(out[0], out[1]) <= (1e-4 if prec == "fp32" else TOL[prec])
