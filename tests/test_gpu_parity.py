@@ -402,3 +402,42 @@ def test_uniform_mass_form_matches_general_form(nbs, orc, prec):
         assert rel_rms(a, ref) <= tol, rel_rms(a, ref)
         out.append(a)
     assert rel_rms(out[0], out[1]) <= (1e-4 if prec == "fp32" else TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["ds", "ds_full", "fp32", "dd"])
+def test_single_body_every_precision(nbs, orc, prec):
+    """One body: no pair term (the frame has zero radius, the near pass has
+    nothing to find), the external field only; a step moves it like the
+    oracle's test particle."""
+    pos = np.array([[50.0, 0.2, -0.1]])
+    vel = np.array([[0.0, ics.VC_R50, 0.05]])
+    m = np.array([0.3])
+    p = orc.Params(eps=0.01, ext_on=True)
+    with nbs.Context(1, eps=0.01, precision=prec, ext_on=True) as c:
+        c.load(pos, vel, m)
+        a = c.accel()
+        c.step(6, 1 / 256, 3)
+        x, _ = c.get_state()
+    np.testing.assert_allclose(a, orc.accel(pos, m, p), rtol=1e-13)
+    rx, _ = orc.run(pos, vel, m, p, 6, 1 / 256, 3)
+    assert np.abs(x - rx).max() <= 1e-12
+
+
+def test_batch_mixing_uniform_and_spread_masses(nbs, orc):
+    """A set whose clusters mix equal and unequal masses falls back to the
+    general form for all of them and stays at the mixed bar."""
+    sizes = [700, 1300, 450]
+    cl = []
+    for k, n in enumerate(sizes):
+        sal = k == 1
+        pos, vel, m = ics.plummer(n, 70 + k, masses=ics.salpeter_masses(n, 70 + k) if sal else None)
+        cl.append((pos, vel, m, ics.paper_softening(n)))
+    with nbs.Context(sizes=sizes, precision="ds") as b:
+        b.set_cluster_params(eps=[c[3] for c in cl])
+        b.load(np.concatenate([c[0] for c in cl]), np.concatenate([c[1] for c in cl]),
+               np.concatenate([c[2] for c in cl]))
+        a = b.accel()
+    off = 0
+    for (p, _, mm, e), n in zip(cl, sizes):
+        assert rel_rms(a[off:off + n], orc.accel_int(p, mm, 1.0, e)) <= TOL["ds"]
+        off += n
