@@ -119,6 +119,7 @@ int set_create(ClusterSet &C, int32_t kcap, int64_t body_cap)
     A((void **)&C.ng_bucket, (size_t)body_cap * 4);
     A((void **)&C.ng_entry, (size_t)body_cap * 4);
     A((void **)&C.ng_rank, (size_t)body_cap * 4);
+    A((void **)&C.ng_reg, (size_t)body_cap * 8);
     A((void **)&C.ng_count, (size_t)C.ng_hcap * 4);
     A((void **)&C.ng_start, (size_t)(C.ng_hcap + 1) * 4);
     A((void **)&C.ng_bsum, (size_t)(C.ng_hcap / 1024 + 1) * 4);
@@ -143,7 +144,7 @@ void set_destroy(ClusterSet &C)
     void *ptrs[] = {C.dmem,     C.red,      C.ng_key,  C.ng_bucket, C.ng_entry,
                     C.ng_count, C.ng_start, C.ng_bsum, C.flag,      C.cid,
                     C.ng_pos,   C.ng_lo,    C.ng_spos, C.ng_slo,    C.ng_slot,
-                    C.ng_rank};
+                    C.ng_rank,  C.ng_reg};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     C = ClusterSet();
@@ -398,6 +399,7 @@ DevState view(const Pool &P, const ClusterSet &C, int precision)
     s.ng_slo = C.ng_slo;
     s.ng_slot = C.ng_slot;
     s.ng_rank = C.ng_rank;
+    s.ng_reg = C.ng_reg;
     s.flag = C.flag;
     if (precision != NB_DS) s.corr = nullptr;
     return s;

@@ -59,6 +59,7 @@ struct ClusterSet {
     int32_t *cid = nullptr;    // linear body -> cluster map
     float4 *ng_pos = nullptr, *ng_lo = nullptr, *ng_spos = nullptr, *ng_slo = nullptr;
     NgSlot *ng_slot = nullptr;
+    int2 *ng_reg = nullptr;
     Frame *frame = nullptr;    // [kcap]
     double *diag = nullptr;    // [kcap][DIAG_STRIDE]
     Clusters cl, cl_pot;       // device views (pair units / potential units)

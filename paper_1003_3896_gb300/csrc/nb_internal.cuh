@@ -100,6 +100,7 @@ struct DevState {
     // per linear body: table slot of its cell, arrival rank in the cell, and
     // (per cell-ordered position) the body index before ordering
     int *ng_bucket = nullptr, *ng_rank = nullptr, *ng_entry = nullptr;
+    int2 *ng_reg = nullptr;   // per linear body: its cluster's slot region (first, size)
     // compact copies per linear body (hi x, y, z, m) and (lo x, y, z, side
     // bits), and the same in cell order (lo.w = linear index)
     float4 *ng_pos = nullptr, *ng_lo = nullptr, *ng_spos = nullptr, *ng_slo = nullptr;
@@ -212,7 +213,7 @@ cudaError_t launch_pair(const DevState &s, const PairLaunch &pl, const HostTab &
 cudaError_t launch_potential(const DevState &s, const Decomp &d, cudaStream_t st);
 
 // ---- near-pair correction (near.cu) ----------------------------------------
-// Cell-table slots used for n bodies (power of two >= 2n).
+// Cell-table slots used for n bodies (four per body of every cluster).
 int64_t near_table_size(int64_t n);
 // corr_i = G sum over pairs closer than the cluster's near radius of the
 // double-single minus the float contribution (written to s.corr).

@@ -18,10 +18,13 @@
 // neighbour on the side of the cell half the body sits in, so each body looks
 // at 2 x 2 x 2 cells.  The 10% margin in CELL_SCALE absorbs the float rounding
 // of x / h for every cell coordinate the key can hold.  Occupied cells live
-// in an open-addressing table (linear probing, at most one cell per two
-// slots) whose slot records carry the cell's range in a cell-ordered copy of
+// in an open-addressing table (linear probing, at most one cell per four
+// slots, so that probes for the many empty neighbour cells end fast) whose
+// slot records carry the cell's range in a cell-ordered copy of
 // the bodies, so a probe costs one 16-byte load and never walks another
-// cell's bodies.  Near pairs are rare (a few tenths per body in a Plummer
+// cell's bodies.  Each cluster k owns the slots [4 noff[k], 4 noff[k+1]):
+// its bodies' probes stay in a region proportional to its size (cache
+// locality for ensembles of small clusters), and probing wraps inside it.  Near pairs are rare (a few tenths per body in a Plummer
 // sphere), so the pass is dominated by these probes.
 //
 // Deterministic: within a cell the bodies are ordered by linear index, and
@@ -53,10 +56,34 @@ __device__ __forceinline__ uint64_t cell_key(int32_t k, int cx, int cy, int cz)
            ((uint64_t)(cy + CELL_OFF) << CELL_BITS) | (uint64_t)(cz + CELL_OFF);
 }
 
-// Multiplicative (Fibonacci) hash of the key: the middle bits of key * 2^64/phi.
-__device__ __forceinline__ uint32_t slot_of(uint64_t key, uint32_t mask)
+// Region of cluster k's cells in the slot table.
+constexpr int SLOTS_PER_BODY = 4;
+
+struct Region {
+    int64_t base;   // first slot
+    uint32_t size;  // slots (SLOTS_PER_BODY n_k)
+};
+
+__device__ __forceinline__ Region region_of(const Clusters &c, int32_t k)
 {
-    return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 32) & mask;
+    Region r;
+    r.base = SLOTS_PER_BODY * c.noff[k];
+    r.size = (uint32_t)(SLOTS_PER_BODY * c.nk[k]);
+    return r;
+}
+
+// Multiplicative (Fibonacci) hash of the key (the middle bits of
+// key * 2^64/phi), reduced to the region by a multiply-shift.
+__device__ __forceinline__ int64_t slot_of(uint64_t key, const Region &r)
+{
+    const uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 32);
+    return r.base + (int64_t)(((uint64_t)h * r.size) >> 32);
+}
+
+// Next slot of the linear probe, wrapping inside the region.
+__device__ __forceinline__ int64_t next_slot(int64_t b, const Region &r)
+{
+    return b + 1 == r.base + r.size ? r.base : b + 1;
 }
 
 // Cell coordinate of v (clamped to the key's range) and the side, -1 or +1,
@@ -71,7 +98,7 @@ __device__ __forceinline__ int cell_coord(float v, float inv_h, int &side)
 
 // Per body: compact float copies, the cell key, insertion of the cell into
 // the slot table and the body's rank among its cell's arrivals.
-__global__ void near_cell_kernel(DevState s, uint32_t mask, int64_t H)
+__global__ void near_cell_kernel(DevState s)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= s.n) return;
@@ -93,13 +120,15 @@ __global__ void near_cell_kernel(DevState s, uint32_t mask, int64_t H)
     s.ng_lo[t] = make_float4(s.xl[i], s.yl[i], s.zl[i], __int_as_float(bits));
     const uint64_t key = cell_key(k, cx, cy, cz);
     s.ng_key[t] = key;
-    // the table has at least twice as many slots as bodies, so a free or
+    // the region has more slots than the cluster has bodies, so a free or
     // matching slot always exists; the bound only caps the loop
-    uint32_t b = slot_of(key, mask);
-    for (int64_t p = 0; p < H; ++p) {
+    const Region rg = region_of(s.cl, k);
+    s.ng_reg[t] = make_int2((int)rg.base, (int)rg.size);
+    int64_t b = slot_of(key, rg);
+    for (uint32_t p = 0; p < rg.size; ++p) {
         const unsigned long long prev = atomicCAS(&s.ng_slot[b].key, NG_EMPTY, key);
         if (prev == NG_EMPTY || prev == key) break;
-        b = (b + 1) & mask;
+        b = next_slot(b, rg);
     }
     s.ng_bucket[t] = (int)b;
     s.ng_rank[t] = atomicAdd(&s.ng_count[b], 1);
@@ -203,14 +232,14 @@ __global__ void near_rank_kernel(DevState s)
 // mass out of the pair term (multiplying its sums by it afterwards); the
 // correction repeats exactly that and scales by the cluster's mass.
 template <bool UM>
-__global__ void __launch_bounds__(256) near_correct_kernel(DevState s, uint32_t mask, int64_t H,
-                                                           double G)
+__global__ void __launch_bounds__(256) near_correct_kernel(DevState s, double G)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= s.n) return;
     const uint64_t kt = s.ng_key[t];
     const float4 P = s.ng_pos[t];
     const float4 Lo = s.ng_lo[t];
+    const int2 rr = s.ng_reg[t];   // the cluster's slot region, read with the key
     const int32_t k = (int32_t)(kt >> (3 * CELL_BITS));
     const int bits = __float_as_int(Lo.w);
     double ax = 0.0, ay = 0.0, az = 0.0;
@@ -220,14 +249,17 @@ __global__ void __launch_bounds__(256) near_correct_kernel(DevState s, uint32_t 
         const int cy = (int)((kt >> CELL_BITS) & cmask) - CELL_OFF;
         const int cz = (int)(kt & cmask) - CELL_OFF;
         const int sx = bits & 1 ? 1 : -1, sy = bits & 2 ? 1 : -1, sz = bits & 4 ? 1 : -1;
+        Region rg;
+        rg.base = rr.x;
+        rg.size = (uint32_t)rr.y;
         uint64_t key[8];
-        uint32_t slot[8];
+        int64_t slot[8];
         NgSlot v[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             key[q] = cell_key(k, cx + (q & 1 ? sx : 0), cy + (q & 2 ? sy : 0),
                               cz + (q & 4 ? sz : 0));
-            slot[q] = slot_of(key[q], mask);
+            slot[q] = slot_of(key[q], rg);
             v[q] = s.ng_slot[slot[q]];
         }
         const float eps2 = s.cl.eps2f[k];
@@ -237,9 +269,9 @@ __global__ void __launch_bounds__(256) near_correct_kernel(DevState s, uint32_t 
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             NgSlot c = v[q];
-            uint32_t b = slot[q];
-            for (int64_t p = 1; p < H && c.key != key[q] && c.key != NG_EMPTY; ++p) {
-                b = (b + 1) & mask;
+            int64_t b = slot[q];
+            for (uint32_t p = 1; p < rg.size && c.key != key[q] && c.key != NG_EMPTY; ++p) {
+                b = next_slot(b, rg);
                 c = s.ng_slot[b];
             }
             if (c.key != key[q]) continue;   // empty cell
@@ -284,16 +316,13 @@ __global__ void __launch_bounds__(256) near_correct_kernel(DevState s, uint32_t 
 
 int64_t near_table_size(int64_t n)
 {
-    int64_t H = 1024;
-    while (H < 2 * n) H <<= 1;
-    return H;
+    return SLOTS_PER_BODY * n;
 }
 
 cudaError_t launch_near_correct(const DevState &s, double G, bool um, cudaStream_t st)
 {
     const int64_t H = near_table_size(s.n);
     if (H > s.ng_hcap) return cudaErrorInvalidValue;
-    const uint32_t mask = (uint32_t)(H - 1);
     const unsigned nbn = (unsigned)((s.n + 255) / 256);
     const unsigned nbh = (unsigned)((H + 255) / 256);
     const int nscan = (int)((H + SCAN_B - 1) / SCAN_B);
@@ -301,16 +330,16 @@ cudaError_t launch_near_correct(const DevState &s, double G, bool um, cudaStream
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(s.ng_count, 0, (size_t)H * sizeof(int), st);
     if (e != cudaSuccess) return e;
-    near_cell_kernel<<<nbn, 256, 0, st>>>(s, mask, H);
+    near_cell_kernel<<<nbn, 256, 0, st>>>(s);
     scan_block_kernel<<<nscan, SCAN_T, 0, st>>>(s.ng_count, s.ng_start, s.ng_bsum, H);
     scan_top_kernel<<<1, SCAN_T, 0, st>>>(s.ng_bsum, nscan);
     scan_add_kernel<<<nbh, 256, 0, st>>>(s.ng_start, s.ng_bsum, H, s.n);
     near_scatter_kernel<<<nbn, 256, 0, st>>>(s);
     near_rank_kernel<<<nbn, 256, 0, st>>>(s);
     if (um)
-        near_correct_kernel<true><<<nbn, 256, 0, st>>>(s, mask, H, G);
+        near_correct_kernel<true><<<nbn, 256, 0, st>>>(s, G);
     else
-        near_correct_kernel<false><<<nbn, 256, 0, st>>>(s, mask, H, G);
+        near_correct_kernel<false><<<nbn, 256, 0, st>>>(s, G);
     return cudaGetLastError();
 }
 

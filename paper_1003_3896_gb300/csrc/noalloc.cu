@@ -32,7 +32,7 @@ namespace {
 constexpr int64_t NA_MAX_N = 16384;   // bodies per call, at most
 constexpr int64_t NA_SLOTS = 8;       // partial-sum slots per body
 constexpr int64_t NA_SEGS = (NA_MAX_N + SEG_BODIES - 1) / SEG_BODIES;
-constexpr int64_t NA_H = 32768;       // near_table_size(NA_MAX_N)
+constexpr int64_t NA_H = 65536;       // near_table_size(NA_MAX_N)
 
 constexpr int64_t align256(int64_t b) { return (b + 255) / 256 * 256; }
 constexpr int64_t OFF_D = 0;                                                // x y z m
@@ -42,7 +42,8 @@ constexpr int64_t OFF_P = OFF_J + align256(4 * NA_MAX_N * 16);              // p
 constexpr int64_t OFF_C = OFF_P + align256(NA_SLOTS * 3 * NA_MAX_N * 8);    // near-pair correction
 constexpr int64_t OFF_K = OFF_C + align256(3 * NA_MAX_N * 8);               // cell keys
 constexpr int64_t OFF_I = OFF_K + align256(NA_MAX_N * 8);                   // bucket, rank, entry
-constexpr int64_t OFF_Q = OFF_I + align256(3 * NA_MAX_N * 4);               // pos lo spos slo
+constexpr int64_t OFF_V = OFF_I + align256(3 * NA_MAX_N * 4);               // slot regions
+constexpr int64_t OFF_Q = OFF_V + align256(NA_MAX_N * 8);                   // pos lo spos slo
 constexpr int64_t OFF_S = OFF_Q + align256(4 * NA_MAX_N * 16);              // cell table
 constexpr int64_t OFF_H = OFF_S + align256(NA_H * (int64_t)sizeof(NgSlot));  // count, start, bsum
 constexpr int64_t OFF_T = OFF_H + align256((2 * NA_H + 1 + NA_H / 1024 + 1) * 4);  // tables
@@ -173,6 +174,7 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
         s.ng_bucket = reinterpret_cast<int *>(b + OFF_I);
         s.ng_rank = s.ng_bucket + N;
         s.ng_entry = s.ng_bucket + 2 * N;
+        s.ng_reg = reinterpret_cast<int2 *>(b + OFF_V);
         s.ng_pos = reinterpret_cast<float4 *>(b + OFF_Q);
         s.ng_lo = s.ng_pos + N;
         s.ng_spos = s.ng_pos + 2 * N;
