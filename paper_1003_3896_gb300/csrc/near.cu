@@ -166,25 +166,40 @@ __global__ void scan_block_kernel(const int *__restrict__ in, int *__restrict__ 
     if (threadIdx.x == SCAN_T - 1) bsum[blockIdx.x] = sh[SCAN_T - 1];
 }
 
-__global__ void scan_top_kernel(int *bsum, int nb)
+// Exclusive scan of the nb block totals in one pass of one block: each of
+// TOP_T threads sums its own run of ceil(nb / TOP_T) totals, the runs' sums
+// are scanned with warp shuffles, and each thread writes its run's prefixes.
+constexpr int TOP_T = 1024;
+
+__global__ void __launch_bounds__(TOP_T) scan_top_kernel(int *bsum, int nb)
 {
-    __shared__ int sh[SCAN_T];
-    int carry = 0;
-    for (int c0 = 0; c0 < nb; c0 += SCAN_T) {
-        const int idx = c0 + threadIdx.x;
-        const int v = idx < nb ? bsum[idx] : 0;
-        sh[threadIdx.x] = v;
-        __syncthreads();
-        for (int w = 1; w < SCAN_T; w <<= 1) {
-            const int t = threadIdx.x >= w ? sh[threadIdx.x - w] : 0;
-            __syncthreads();
-            sh[threadIdx.x] += t;
-            __syncthreads();
+    __shared__ int wsum[TOP_T / 32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int per = (nb + TOP_T - 1) / TOP_T;
+    const int lo = t * per, hi = lo + per < nb ? lo + per : nb;
+    int local = 0;
+    for (int i = lo; i < hi; ++i) local += bsum[i];
+    int x = local;   // inclusive scan over the warp
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int v = wsum[lane];
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, v, d);
+            if (lane >= d) v += y;
         }
-        if (idx < nb) bsum[idx] = carry + sh[threadIdx.x] - v;
-        const int tot = sh[SCAN_T - 1];
-        __syncthreads();
-        carry += tot;
+        wsum[lane] = v;
+    }
+    __syncthreads();
+    int run = x - local + (w > 0 ? wsum[w - 1] : 0);
+    for (int i = lo; i < hi; ++i) {
+        const int v = bsum[i];
+        bsum[i] = run;
+        run += v;
     }
 }
 
@@ -332,7 +347,7 @@ cudaError_t launch_near_correct(const DevState &s, double G, bool um, cudaStream
     if (e != cudaSuccess) return e;
     near_cell_kernel<<<nbn, 256, 0, st>>>(s);
     scan_block_kernel<<<nscan, SCAN_T, 0, st>>>(s.ng_count, s.ng_start, s.ng_bsum, H);
-    scan_top_kernel<<<1, SCAN_T, 0, st>>>(s.ng_bsum, nscan);
+    scan_top_kernel<<<1, TOP_T, 0, st>>>(s.ng_bsum, nscan);
     scan_add_kernel<<<nbh, 256, 0, st>>>(s.ng_start, s.ng_bsum, H, s.n);
     near_scatter_kernel<<<nbn, 256, 0, st>>>(s);
     near_rank_kernel<<<nbn, 256, 0, st>>>(s);
