@@ -491,3 +491,92 @@ def test_sampled_sum_matches_full_sum(orc):
     full = orc.accel_int(pos, m, 1.0, 0.01)
     idx = np.array([0, 5, 699, 350, 5])
     np.testing.assert_array_equal(orc.accel_int_at(pos, m, idx, 1.0, 0.01), full[idx])
+
+
+# ------------------------------------------- high-precision brute force
+
+def _dec_accel(pos, m, eps):
+    """a_i = sum_{j != i} m_j (x_j - x_i) / (r^2 + eps^2)^{3/2} (eq. 5) in
+    60-digit decimal arithmetic, from the exact values of the double inputs;
+    also the sum of the terms' magnitudes per body."""
+    from decimal import Decimal, getcontext
+    getcontext().prec = 60
+    P = [[Decimal(float(v)) for v in row] for row in pos]
+    M = [Decimal(float(v)) for v in m]
+    e2 = Decimal(float(eps)) ** 2
+    n = len(M)
+    out, mag = [], []
+    for i in range(n):
+        a = [Decimal(0)] * 3
+        s = Decimal(0)
+        for j in range(n):
+            if j == i:
+                continue
+            d = [P[j][c] - P[i][c] for c in range(3)]
+            r2 = sum(x * x for x in d) + e2
+            w = M[j] / (r2 * r2.sqrt())
+            for c in range(3):
+                a[c] += w * d[c]
+            s += abs(w) * r2.sqrt()
+        out.append([float(x) for x in a])
+        mag.append(float(s))
+    return np.array(out), np.array(mag)
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 8])
+@pytest.mark.parametrize("eps", [0.0, 0.01])
+def test_force_sum_against_high_precision_brute_force(orc, n, eps):
+    """The FP64 sum agrees with a 60-digit brute force of eq. 5 to within a
+    rounding bound: a few ulps per term times the sum of the terms' sizes."""
+    rng = np.random.default_rng(500 + n)
+    pos = rng.normal(size=(n, 3))
+    m = rng.uniform(0.1, 2.0, n)
+    ref, mag = _dec_accel(pos, m, eps)
+    got = orc.accel_int(pos, m, 1.0, eps)
+    err = np.linalg.norm(got - ref, axis=1)
+    bound = 8 * n * 2.0 ** -52 * mag
+    assert np.all(err <= bound), (err, bound)
+    # and well below the FP64 GPU bar of 1e-12 relative
+    assert np.linalg.norm(got - ref) <= 1e-15 * np.linalg.norm(ref) * max(1.0, mag.max() / np.abs(ref).max())
+
+
+def test_potential_energy_against_high_precision_brute_force(orc):
+    """W = -G sum_{i<j} m_i m_j / sqrt(r^2 + eps^2) (eq. 4) to 1e-15 relative."""
+    from decimal import Decimal, getcontext
+    getcontext().prec = 60
+    rng = np.random.default_rng(77)
+    n, eps = 7, 0.03
+    pos = rng.normal(size=(n, 3))
+    vel = np.zeros((n, 3))
+    m = rng.uniform(0.1, 2.0, n)
+    W = Decimal(0)
+    for i in range(n):
+        for j in range(i + 1, n):
+            r2 = sum((Decimal(float(pos[j, c])) - Decimal(float(pos[i, c]))) ** 2
+                     for c in range(3)) + Decimal(eps) ** 2
+            W -= Decimal(float(m[i])) * Decimal(float(m[j])) / r2.sqrt()
+    e = orc.energy(pos, vel, m, _params(orc, eps=eps))
+    assert abs(e.W - float(W)) <= 1e-15 * abs(float(W))
+
+
+def test_external_field_against_high_precision(orc):
+    """The disk + bulge + black hole acceleration (closed form of -grad Phi)
+    against the same closed form in 60-digit decimals, to 1e-15 relative."""
+    from decimal import Decimal, getcontext
+    getcontext().prec = 60
+    p = _params(orc, ext_on=True, Mbh=3.0, eps_bh=0.2)
+    D = lambda v: Decimal(float(v))
+    for x in ([50.0, 0.3, -0.2], [0.4, -0.1, 0.05], [7.0, 3.0, 1.5]):
+        X, Y, Z = (D(v) for v in x)
+        R2 = X * X + Y * Y
+        s = (Z * Z + D(p.bd) ** 2).sqrt()
+        Dd = (R2 + (D(p.ad) + s) ** 2)
+        kd = D(p.Md) / (Dd * Dd.sqrt())
+        rb2 = R2 + Z * Z + D(p.ab) ** 2
+        kb = D(p.Mb) / (rb2 * rb2.sqrt())
+        rh2 = R2 + Z * Z + D(p.eps_bh) ** 2
+        kh = D(p.Mbh) / (rh2 * rh2.sqrt())
+        want = np.array([float(-(kd + kb + kh) * X), float(-(kd + kb + kh) * Y),
+                         float(-(kd * (D(p.ad) + s) / s + kb + kh) * Z)])
+        got = orc.ext_accel(p, np.array(x))[0]
+        assert np.linalg.norm(got - want) <= 1e-15 * np.linalg.norm(want) * 4
