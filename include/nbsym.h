@@ -274,6 +274,19 @@ int nb_measure_peaks(int device, nb_peaks_t *out);
 int nb_accel_static(const nb_params *p, int64_t n, const double *d_pos,
                     const double *d_mass, double *d_acc_out);
 
+/* Accelerations of bodies [i0, i1) of a one-cluster context against all n
+ * (internal sum of eq. 5 in the context's precision, plus the external field
+ * when ext_on): the share one GPU computes in the paper's multi-GPU scheme
+ * (Sect. 4.2), where each GPU sums an i-range against all bodies.  The launch
+ * takes whole 128 I-body i-blocks and sums each one's j range in order in one
+ * block, so a body's result does not depend on the range it was computed in:
+ * split ranges concatenate bit for bit to the whole range (in every
+ * precision; across calls the mixed mode's near-pair correction is
+ * deterministic too).  Rows of acc_out: i1 - i0, host memory.  Synchronous.
+ * Errors: NB_EINVAL (NULL, bad range, more than one cluster), NB_ESTATE
+ * (nothing loaded), NB_ENONFINITE, NB_ECUDA. */
+int nb_accel_range(nb_ctx *ctx, int64_t i0, int64_t i1, double *acc_out);
+
 /* The N(N-1)/2 variant of the internal sum (Newton's third law: each
  * unordered pair evaluated once and its force added to both bodies), which
  * the paper rejects for its GPU (Sect. 4.2); provided to measure it here.

@@ -421,10 +421,12 @@ cudaError_t launch_kick_drift(const DevState &s, const Decomp &d, double wk, dou
     return cudaGetLastError();
 }
 
-__global__ void accel_out_kernel(DevState s, Decomp d, ExtField ext, double *__restrict__ out)
+__global__ void accel_out_kernel(DevState s, Decomp d, ExtField ext, double *__restrict__ out,
+                                 int64_t t0, int64_t t1)
 {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= s.n) return;
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t t = t0 + q;
+    if (t >= t1) return;
     const BodyRef r = body_at(s.cl, t);
     double ax, ay, az;
     sum_slots(s, d, r, ax, ay, az);
@@ -435,16 +437,22 @@ __global__ void accel_out_kernel(DevState s, Decomp d, ExtField ext, double *__r
         ay += ey;
         az += ez;
     }
-    out[3 * t] = ax;
-    out[3 * t + 1] = ay;
-    out[3 * t + 2] = az;
+    out[3 * q] = ax;
+    out[3 * q + 1] = ay;
+    out[3 * q + 2] = az;
     if (!isfinite(ax) || !isfinite(ay) || !isfinite(az)) atomicOr(s.flag, 1);
 }
 
 cudaError_t launch_accel_out(const DevState &s, const Decomp &d, const ExtField &ext,
                              double *out_aos, cudaStream_t st)
 {
-    accel_out_kernel<<<blocks_for(s.n, OT), OT, 0, st>>>(s, d, ext, out_aos);
+    return launch_accel_out_range(s, d, ext, out_aos, 0, s.n, st);
+}
+
+cudaError_t launch_accel_out_range(const DevState &s, const Decomp &d, const ExtField &ext,
+                                   double *out_aos, int64_t t0, int64_t t1, cudaStream_t st)
+{
+    accel_out_kernel<<<blocks_for(t1 - t0, OT), OT, 0, st>>>(s, d, ext, out_aos, t0, t1);
     return cudaGetLastError();
 }
 

@@ -127,6 +127,11 @@ struct Decomp {
     // j bodies per unit: TILE or a divisor of it down to 32 (finer units give
     // small clusters enough of them to fill the GPU)
     int32_t jt = TILE;
+    // rows: a unit is a whole i-block row (all its j, summed in order by one
+    // block), so every body's sum is the same whatever other rows share the
+    // launch; b0: first i-block of the launch (i-range launches)
+    int32_t rows = 0;
+    int64_t b0 = 0;
     int64_t W = 0;        // total units
     int64_t G = 1;        // persistent blocks (grid size), 1 <= G <= W
     int64_t slots = 1;    // max partial slots any i-block needs
@@ -141,7 +146,7 @@ struct Decomp {
     // units per i-block of a cluster of ntiles TILE-wide j-tiles
     __host__ __device__ int64_t units_per_iblock(int64_t ntiles) const
     {
-        return ntiles * (TILE / jt);
+        return rows ? 1 : ntiles * (TILE / jt);
     }
 };
 
@@ -150,7 +155,7 @@ struct Decomp {
 __device__ __forceinline__ void iblock_slots(const Decomp &d, const Clusters &c, int32_t k,
                                              int64_t li, int64_t &first, int64_t &count)
 {
-    const int64_t b = li / d.ipb;
+    const int64_t b = li / d.ipb - d.b0;
     const int64_t nt = d.units_per_iblock(c.ntiles[k]);
     const int64_t u0 = c.uoff[k] + b * nt;
     first = d.owner(u0);
@@ -205,7 +210,7 @@ bool pair_variant_exists(int mode, int I);
 // Decomposition of the pair work of clusters with host-side sizes nk and
 // tiles, given units per cluster (host arrays), i-block width, target grid.
 Decomp make_decomp(int64_t W, int64_t max_ntiles, int ipb, int64_t G, int64_t slot_cap,
-                   int jt = TILE);
+                   int jt = TILE, int rows = 0);
 cudaError_t launch_pair(const DevState &s, const PairLaunch &pl, const HostTab &ht, double G,
                         cudaStream_t st);
 // Potential sums phi_i = sum_{j != i} m_j / sqrt(r^2 + eps^2) (FP64) into
@@ -241,6 +246,9 @@ cudaError_t launch_kick_drift(const DevState &s, const Decomp &d, double wk, dou
                               int do_kick, int do_split, const ExtField &ext, cudaStream_t st);
 cudaError_t launch_accel_out(const DevState &s, const Decomp &d, const ExtField &ext,
                              double *out_aos, cudaStream_t st);
+// The same for linear bodies [t0, t1) only, row t - t0 of out_aos.
+cudaError_t launch_accel_out_range(const DevState &s, const Decomp &d, const ExtField &ext,
+                                   double *out_aos, int64_t t0, int64_t t1, cudaStream_t st);
 cudaError_t launch_energy_reduce(const DevState &s, const Decomp &d, const ExtField &ext,
                                  double G, cudaStream_t st);
 cudaError_t launch_torque(const DevState &s, const ExtField &ext, cudaStream_t st);

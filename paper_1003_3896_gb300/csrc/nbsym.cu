@@ -436,6 +436,48 @@ int nb_accel(nb_ctx *c, double *acc_out) { return accel_common(c, acc_out, true)
 
 int nb_accel_device(nb_ctx *c, double *d_acc_out) { return accel_common(c, d_acc_out, false); }
 
+int nb_accel_range(nb_ctx *c, int64_t i0, int64_t i1, double *acc_out)
+{
+    if (!c || !acc_out) return set_error(NB_EINVAL, "NULL argument");
+    if (c->n == 0) return set_error(NB_ESTATE, "nb_accel_range before nb_load");
+    if (c->set.K != 1) return set_error(NB_EINVAL, "nb_accel_range takes one cluster");
+    if (i0 < 0 || i1 > c->n || i0 >= i1)
+        return set_error(NB_EINVAL, "range [%lld, %lld) outside [0, %lld)", (long long)i0,
+                         (long long)i1, (long long)c->n);
+    DeviceGuard dg(c->p.device);
+    int rc = refresh_split(c);
+    if (rc) return rc;
+    // whole i-block rows of the range, one block per run of rows: each row's
+    // j sum is done in order by one block, as in any other range launch
+    const Plan &pl = c->plan;
+    PairLaunch rl = pl.pl;
+    const int ipb = TILE * rl.I;
+    const int64_t b0 = i0 / ipb, b1 = (i1 + ipb - 1) / ipb, W = b1 - b0;
+    int64_t G = (int64_t)c->pool.num_sms * rl.blocks_per_sm;
+    if (G > W) G = W;
+    rl.d = make_decomp(W, c->set.max_ntiles, ipb, G, c->pool.s.part_slots, TILE, 1);
+    rl.d.b0 = b0;
+    rl.d.mask_self = pl.pl.d.mask_self;
+    const DevState s = view(c->pool, c->set, pl);
+    const int64_t uoff[2] = {0, W};
+    HostTab ht;
+    ht.K = 1;
+    ht.uoff = uoff;
+    ht.boff = c->set.boff.data();
+    ht.nk = c->set.nk.data();
+    ht.ntiles = c->set.ntiles.data();
+    ht.eps2f = c->set.eps2f.data();
+    ht.mu = c->set.mu.data();
+    NB_TRY(launch_pair(s, rl, ht, c->phys.G, c->stream));
+    if (rl.mode == PM_DS_NEAR) NB_TRY(launch_near_correct(s, c->phys.G, rl.um, c->stream));
+    NB_TRY(cudaMemsetAsync(c->set.flag, 0, sizeof(int), c->stream));
+    double *out = c->pool.stage;   // 3 (i1 - i0) <= 7 cap doubles
+    NB_TRY(launch_accel_out_range(s, rl.d, c->phys.ext, out, i0, i1, c->stream));
+    NB_TRY(cudaMemcpyAsync(acc_out, out, sizeof(double) * 3 * (size_t)(i1 - i0),
+                           cudaMemcpyDeviceToHost, c->stream));
+    return check_flag(c, "nb_accel_range");
+}
+
 int nb_step(nb_ctx *c, int order, double dt, int64_t nsteps)
 {
     if (!c) return set_error(NB_EINVAL, "ctx is NULL");

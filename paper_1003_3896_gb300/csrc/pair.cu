@@ -34,11 +34,13 @@
 
 namespace nb {
 
-Decomp make_decomp(int64_t W, int64_t max_ntiles, int ipb, int64_t G, int64_t slot_cap, int jt)
+Decomp make_decomp(int64_t W, int64_t max_ntiles, int ipb, int64_t G, int64_t slot_cap, int jt,
+                   int rows)
 {
     Decomp d;
     d.ipb = ipb;
     d.jt = jt;
+    d.rows = rows;
     const int64_t max_units = d.units_per_iblock(max_ntiles);
     d.W = W > 0 ? W : 1;
     if (G > d.W) G = d.W;
@@ -79,7 +81,8 @@ struct Segment {
     int64_t base;     // first pool slot of the cluster
     int32_t nk;       // bodies of the cluster
     int32_t b;        // i-block
-    int32_t t0, t1;   // j tiles [t0, t1)
+    int32_t t0, t1;   // units [t0, t1) of the i-block
+    int32_t J0, J1;   // their j range
     int64_t slot;     // partial slot of this block for the i-block
 };
 
@@ -116,13 +119,16 @@ __device__ __forceinline__ Segment segment_at(const Decomp &d, const ParamTab<KC
     const int64_t u0 = t.uoff[s.k];
     const int32_t nt = (int32_t)d.units_per_iblock(t.ntiles[s.k]);
     const int64_t lu = u - u0;
-    s.b = (int32_t)(lu / nt);
-    s.t0 = (int32_t)(lu - (int64_t)s.b * nt);
+    const int64_t rb = lu / nt;
+    s.b = (int32_t)(d.b0 + rb);
+    s.t0 = (int32_t)(lu - rb * nt);
     const int64_t left = uend - u;
     s.t1 = (int64_t)s.t0 + left < nt ? (int32_t)(s.t0 + left) : nt;
+    s.J0 = d.rows ? 0 : s.t0 * d.jt;
+    s.J1 = d.rows ? t.ntiles[s.k] * TILE : s.t1 * d.jt;
     s.base = t.boff[s.k];
     s.nk = t.nk[s.k];
-    s.slot = g - d.owner(u0 + (int64_t)s.b * nt);
+    s.slot = g - d.owner(u0 + rb * nt);
     return s;
 }
 
@@ -134,13 +140,16 @@ __device__ __forceinline__ Segment segment_at(const Decomp &d, const Clusters &c
     const int64_t u0 = c.uoff[s.k];
     const int32_t nt = (int32_t)d.units_per_iblock(c.ntiles[s.k]);
     const int64_t lu = u - u0;
-    s.b = (int32_t)(lu / nt);
-    s.t0 = (int32_t)(lu - (int64_t)s.b * nt);
+    const int64_t rb = lu / nt;
+    s.b = (int32_t)(d.b0 + rb);
+    s.t0 = (int32_t)(lu - rb * nt);
     const int64_t left = uend - u;
     s.t1 = (int64_t)s.t0 + left < nt ? (int32_t)(s.t0 + left) : nt;
+    s.J0 = d.rows ? 0 : s.t0 * d.jt;
+    s.J1 = d.rows ? c.ntiles[s.k] * TILE : s.t1 * d.jt;
     s.base = c.boff[s.k];
     s.nk = (int32_t)c.nk[s.k];
-    s.slot = g - d.owner(u0 + (int64_t)s.b * nt);
+    s.slot = g - d.owner(u0 + rb * nt);
     return s;
 }
 
@@ -275,7 +284,7 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
 #pragma unroll
         for (int r = 0; r < 6 * I; ++r) acc_sh[r][tid] = 0.f;
 
-        const int J0 = sg.t0 * d.jt, J1 = sg.t1 * d.jt;
+        const int J0 = sg.J0, J1 = sg.J1;
         float4 pf[4];
         {
             const int j = J0 + lane;
@@ -538,7 +547,7 @@ __global__ void __launch_bounds__(TILE) pair_ff_kernel(
             q.zl[p] = make_float2(zl[ca], zl[cb2]);
             q.axh[p] = q.axl[p] = q.ayh[p] = q.ayl[p] = q.azh[p] = q.azl[p] = make_float2(0.f, 0.f);
         }
-        const int J0 = sg.t0 * d.jt, J1 = sg.t1 * d.jt;
+        const int J0 = sg.J0, J1 = sg.J1;
         float4 pf[4];
         {
             const int j = J0 + lane;
@@ -627,7 +636,7 @@ __global__ void __launch_bounds__(TILE) pair_fp64_kernel(
             zi[k] = z[ic];
             ax[k] = ay[k] = az[k] = 0.0;
         }
-        const int J0 = sg.t0 * d.jt, J1 = sg.t1 * d.jt;
+        const int J0 = sg.J0, J1 = sg.J1;
         for (int jglob = J0; jglob < J1; jglob += TILE) {
             const int w = J1 - jglob < TILE ? J1 - jglob : TILE;   // j bodies staged
             const int j = jglob + tid;

@@ -97,6 +97,7 @@ nb_clusters = _sig("nb_clusters", C.c_int64, _ctxp)
 nb_energy_clusters = _sig("nb_energy_clusters", C.c_int, _ctxp, C.POINTER(EnergyT))
 nb_accel_static = _sig("nb_accel_static", C.c_int, C.POINTER(Params), C.c_int64, _vp, _vp, _vp)
 nb_tune = _sig("nb_tune", C.c_int, _ctxp, C.c_int, C.POINTER(TuneT))
+nb_accel_range = _sig("nb_accel_range", C.c_int, _ctxp, C.c_int64, C.c_int64, _dp)
 nb_accel_symmetric = _sig("nb_accel_symmetric", C.c_int, _ctxp, _dp, C.POINTER(C.c_double))
 nb_tune_save = _sig("nb_tune_save", C.c_int, C.c_char_p)
 nb_tune_load = _sig("nb_tune_load", C.c_int64, C.c_char_p)
@@ -289,6 +290,12 @@ class Context:
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
         check(nb_set_precision(self._h, int(precision)))
+
+    def accel_range(self, i0: int, i1: int) -> np.ndarray:
+        """Accelerations of bodies [i0, i1) against all (nb_accel_range)."""
+        out = np.empty((max(int(i1) - int(i0), 1), 3))   # the library checks the range
+        check(nb_accel_range(self._h, int(i0), int(i1), _p(out)))
+        return out
 
     def accel_symmetric(self):
         """(accelerations, pair-kernel ms) from the N(N-1)/2 float variant."""
