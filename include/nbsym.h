@@ -41,7 +41,7 @@ typedef struct nb_ctx nb_ctx;
  *  NB_DS   -- mixed: pair arithmetic in single precision on coordinates
  *             taken relative to a reference point near the system, the
  *             coordinate difference of close pairs re-formed from
- *             double-single (hi + lo) coordinates, per-tile sums folded
+ *             double-single (hi + lo) coordinates, float partial sums folded
  *             into double-single accumulators (the paper's software
  *             double-single idea, Sect. 5.2).  On small sets (sum of N_k^2
  *             at most 2^27, e.g. one cluster of N <= 11585) the close-pair

@@ -319,12 +319,16 @@ int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan
         jt = tuned.jt;
     } else if (pl.pl.mode == PM_FP64) {
         I = 1;
-    } else if (mean < 16384) {
-        I = 2;
+    } else if (pl.pl.mode == PM_DD) {
+        I = 2;   // measured fastest at N = 262144
+    } else if (pl.pl.mode == PM_DS_FULL) {
+        I = mean < 16384 ? 2 : 4;
     } else {
-        // measured at N = 65536: mixed is fastest at 4 bodies per thread,
-        // pure float (fewer live registers) at 8
-        I = pl.pl.mode == PM_FP32 ? 8 : 4;
+        // float pairs (mixed and pure float): 8 bodies per thread measured
+        // fastest at N = 65536 and N = 262144 and on the 512-cluster
+        // ensemble (mean N 2519); small clusters keep 2 so the i-blocks
+        // stay narrow enough to give every resident block a unit
+        I = mean < 2048 ? 2 : 8;
     }
     if (!pair_variant_exists(pl.pl.mode, I))
         return set_error(NB_EINVAL, "no pair kernel with %d bodies per thread for this precision",

@@ -10,14 +10,14 @@
 //
 // Single-precision family (one template, three modes):
 //   PM_DS_NEAR  float pair arithmetic on coordinates relative to the cluster's
-//               frame origin, per-tile float sums folded into double-single
+//               frame origin, float partial sums over 256 j folded into double-single
 //               accumulators (Sect. 5.2's software double precision); pairs
 //               closer than the near radius are re-formed from the
 //               double-single coordinate difference (hi_j - hi_i) +
 //               (lo_j - lo_i) by the separate correction pass of near.cu.
 //   PM_DS_FULL  the double-single coordinate difference on every pair.
-//   PM_FP32     float coordinates and float accumulation throughout (per-tile
-//               float sums added in float).
+//   PM_FP32     float coordinates and float accumulation throughout (the
+//               256-j partial sums added in float).
 //
 // Data movement: no block-wide barrier.  Each warp streams its j bodies in
 // chunks of 32 through a warp-private shared-memory buffer: lane l loads body
@@ -155,6 +155,7 @@ __device__ __forceinline__ Segment segment_at(const Decomp &d, const Clusters &c
 
 constexpr int CH = 32;            // j bodies per warp chunk
 constexpr int WARPS = TILE / 32;  // warps per block
+constexpr int FOLD = 2 * TILE;    // j bodies per float partial sum before the fold
 
 // Thread-private i bodies, two per packed register pair: pair p holds bodies
 // k = 2p (.x) and k = 2p + 1 (.y), local body k = ib0 + tid + k * TILE.
@@ -162,19 +163,22 @@ template <int P>
 struct IPairs {
     float2 nx[P], ny[P], nz[P];     // negated hi coordinates
     float2 nlx[P], nly[P], nlz[P];  // negated lo coordinates (full double-single mode)
-    float2 ax[P], ay[P], az[P];     // float sums of the current 128-j tile
+    float2 ax[P], ay[P], az[P];     // float sums of the current FOLD j bodies
 };
 
 // One chunk of CH j bodies (local indices j0 ...) against the thread's 2P i
 // bodies (local indices ibase + k * TILE).  MASK zeroes the j == i term
 // (eps = 0, diagonal chunks).  UM (all masses of the cluster equal): the pair
 // term is d / r^3 without m_j, one multiply fewer; the caller scales by m.
+// At P = 4 the chunk stays a loop of four groups of 8 j: fully unrolled, the
+// kernel's code outgrows the instruction cache and runs 30% slower.
 template <int P, int MODE, bool MASK, bool UM>
 __device__ __forceinline__ void chunk_pass(const float4 (*cb)[4], int j0, int ibase,
                                            IPairs<P> &ip, float eps2)
 {
     const float2 e2 = make_float2(eps2, eps2);
-#pragma unroll
+    constexpr int GU = P >= 4 ? 1 : CH / 8;
+#pragma unroll GU
     for (int g = 0; g < CH / 8; ++g) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -314,9 +318,9 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
             else
                 chunk_pass<P, MODE, false, UM>(cb, jc, ibase, ip, eps2);
             __syncwarp();
-            if (((jc + CH - J0) & (TILE - 1)) == 0 || jc + CH >= J1) {
-                // every TILE j and at the segment's end: fold the tile sums
-                // into the running sums
+            if (((jc + CH - J0) & (FOLD - 1)) == 0 || jc + CH >= J1) {
+                // every FOLD j and at the segment's end: fold the float
+                // partial sums into the running sums
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
 #pragma unroll
