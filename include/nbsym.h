@@ -303,11 +303,13 @@ int nb_accel_symmetric(nb_ctx *ctx, double *acc_out, double *pair_ms);
 /* ---- autotuner (no counterpart in the paper: the paper fixes one block
  * shape for its GPU, Sect. 4.2) ---------------------------------------------
  * The launch shape of the pair kernel is (bodies per thread I, j-tile width
- * jt, resident blocks per SM b): one work unit is an i-block of 128 * I
- * bodies against a j-range of jt bodies (128, 64 or 32: narrower ranges give
- * small clusters enough units to fill the GPU); b sets the persistent grid
- * (b * SMs blocks, at most the unit count) and so how finely units are cut
- * into per-block runs.  nb_tune times every shape this build compiled for
+ * jt, blocks per SM b): one work unit is an i-block of 128 * I bodies against
+ * a j-range of jt bodies (128, 64 or 32: narrower ranges give small clusters
+ * enough units to fill the GPU); b sets the grid (b * SMs blocks, at most the
+ * unit count) and so how finely units are cut into per-block runs.  Up to
+ * the occupancy limit the grid is resident at once; above it (up to 6 times
+ * that limit) it runs in waves, which evens out SMs whose resident blocks
+ * progress at different rates.  nb_tune times every shape this build compiled for
  * the context's current precision on its loaded state (reps launches each,
  * CUDA events on the context's stream), switches the context to the fastest
  * and records it in a process-wide table keyed by the workload's shape (SM
@@ -318,10 +320,11 @@ int nb_accel_symmetric(nb_ctx *ctx, double *acc_out, double *pair_ms);
 typedef struct {
     int precision;           /* enum nb_precision tuned */
     int bodies_per_thread;   /* chosen I */
-    int blocks_per_sm;       /* chosen b */
+    int blocks_per_sm;       /* chosen b (grid per SM; above the occupancy
+                                limit the grid runs in waves) */
     int j_tile;              /* chosen j bodies per unit: 128, 64 or 32 */
     int candidates;          /* shapes timed */
-    int64_t grid;            /* persistent blocks of the chosen shape */
+    int64_t grid;            /* blocks of the chosen shape */
     double pair_ms;          /* mean pair-launch time of the chosen shape */
     double default_ms;       /* the same for the shape chosen without tuning */
 } nb_tune_t;
@@ -343,7 +346,7 @@ int nb_tune_save(const char *path);
 int64_t nb_tune_load(const char *path);
 
 /* The pair-kernel shape of the context's current plan: bodies per thread,
- * resident blocks per SM, j bodies per unit, persistent grid (any out pointer
+ * blocks per SM, j bodies per unit, grid (any out pointer
  * may be NULL).  Errors: NB_EINVAL (NULL ctx), NB_ESTATE (nothing loaded). */
 int nb_pair_shape(nb_ctx *ctx, int *bodies_per_thread, int *blocks_per_sm, int *j_tile,
                   int64_t *grid);

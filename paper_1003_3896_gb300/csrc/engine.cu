@@ -38,11 +38,14 @@ int pool_create(Pool &P, int device, int64_t cap)
         return set_error(NB_ECUDA, "cudaDeviceGetAttribute failed");
     DevState &s = P.s;
     s.cap = cap;
-    // partial-sum slots: an i-block needs about G_max * ipb / n + 2 of them;
-    // memory stays near 24 * (G_max * 512 + 2 cap) bytes whatever cap is
-    const int64_t gmax = (int64_t)P.num_sms * 8;
-    int64_t slots = 2 + (gmax * 512 + cap - 1) / cap;
-    if (slots > 24) slots = 24;
+    // partial-sum slots: an i-block needs about G * ipb / n + 2 of them,
+    // where G * ipb <= SMs * MAX_WAVES * (resident blocks * i-block width)
+    // and the last factor is at most 3072 for every compiled variant (8 x
+    // 256, 6 x 512, 3 x 1024); memory stays near 24 * (that + 2 cap) bytes
+    // whatever cap is.  make_decomp shrinks a grid that would need more.
+    const int64_t giw = (int64_t)P.num_sms * MAX_WAVES * 3072;
+    int64_t slots = 2 + (giw + cap - 1) / cap;
+    if (slots > 64) slots = 64;
     s.part_slots = slots;
     s.red_len = 0;
     bool ok = true;
@@ -334,10 +337,12 @@ int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan
         return set_error(NB_EINVAL, "no pair kernel with %d bodies per thread for this precision",
                          I);
     pl.pl.I = I;
-    const int occ = pair_occupancy(pl.pl.mode, I);
-    pl.pl.blocks_per_sm = bps > 0 && bps < occ ? bps : occ;
-    if (pl.pl.blocks_per_sm < 1) pl.pl.blocks_per_sm = 1;
+    int occ = pair_occupancy(pl.pl.mode, I);
+    if (occ < 1) occ = 1;
+    pl.pl.blocks_per_sm = bps > 0 ? (bps < MAX_WAVES * occ ? bps : MAX_WAVES * occ)
+                                  : DEFAULT_WAVES * occ;
     const int64_t want = (int64_t)P.num_sms * pl.pl.blocks_per_sm;
+    const int64_t resident = (int64_t)P.num_sms * occ;
     if (jt == 0) {
         // full-width j-tiles, halved while the units are too few to give
         // every resident block one (small clusters)
@@ -345,7 +350,7 @@ int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan
         for (int32_t k = 0; k < C.K; ++k)
             w_full += ((C.nk[k] + TILE * I - 1) / (TILE * I)) * ((C.nk[k] + TILE - 1) / TILE);
         jt = TILE;
-        while (jt > 32 && w_full * (TILE / jt) < want) jt /= 2;
+        while (jt > 32 && w_full * (TILE / jt) < resident) jt /= 2;
     }
     int rc = set_layout(C, TILE * I, st, jt);
     if (rc) return rc;

@@ -82,8 +82,16 @@ struct Plan {
 };
 // Launch shape of the pair kernel: I bodies per thread (i-block width
 // TILE * I), jt j bodies per unit (TILE, TILE / 2 or TILE / 4) and
-// blocks_per_sm resident blocks (grid = blocks_per_sm * SMs, at most the
-// unit count).
+// blocks_per_sm, the grid per SM (grid = blocks_per_sm * SMs, at most the
+// unit count).  Up to the occupancy limit the grid is resident at once;
+// above it the grid runs in waves (at most MAX_WAVES), the hardware handing
+// each further block to whichever SM frees a slot.  Resident blocks of one SM
+// do not progress at one rate (the warp scheduler favours the oldest), so a
+// single resident wave of equal unit runs ends with SMs holding one slow
+// block; waves even that out, while every block's units and partial slot
+// stay fixed by its index (results stay bit-reproducible).
+constexpr int MAX_WAVES = 6;
+constexpr int DEFAULT_WAVES = 4;
 struct PairShape {
     int I = 0;
     int blocks_per_sm = 0;

@@ -363,11 +363,27 @@ __device__ __forceinline__ void sum_slots(const DevState &s, const Decomp &d, co
     iblock_slots(d, s.cl, r.k, r.li, first, count);
     (void)first;
     ax = ay = az = 0.0;
-    for (int64_t k = 0; k < count; ++k) {
-        const double *p = s.part + (k * 3) * s.cap + r.gi;
-        ax += p[0];
-        ay += p[s.cap];
-        az += p[2 * s.cap];
+    // slots in order, loaded eight at a time so the loads are in flight
+    // together (a grid run in waves gives an i-block tens of slots)
+    for (int64_t k0 = 0; k0 < count; k0 += 8) {
+        double bx[8], by[8], bz[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            bx[q] = by[q] = bz[q] = 0.0;
+            if (k0 + q < count) {
+                const double *p = s.part + ((k0 + q) * 3) * s.cap + r.gi;
+                bx[q] = p[0];
+                by[q] = p[s.cap];
+                bz[q] = p[2 * s.cap];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (k0 + q < count) {
+                ax += bx[q];
+                ay += by[q];
+                az += bz[q];
+            }
     }
     if (s.corr) {
         ax += s.corr[r.gi];
@@ -477,7 +493,15 @@ __global__ void energy_partial_kernel(DevState s, Decomp d, ExtField ext)
         int64_t first, count;
         iblock_slots(d, s.cl, k, r.li, first, count);
         double phi = 0.0;
-        for (int64_t q = 0; q < count; ++q) phi += s.part[(q * 3) * s.cap + i];
+        for (int64_t q0 = 0; q0 < count; q0 += 8) {
+            double bp[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                bp[q] = q0 + q < count ? s.part[((q0 + q) * 3) * s.cap + i] : 0.0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q0 + q < count) phi += bp[q];
+        }
         v[0] += 0.5 * m * (vx * vx + vy * vy + vz * vz);
         v[1] += m * phi;
         if (ext.on) v[2] += m * field_phi(ext, x, y, z);

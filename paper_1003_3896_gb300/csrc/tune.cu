@@ -3,9 +3,10 @@
 // The shape of one pair-force launch is (I, jt, b): I bodies per thread,
 // which sets the width TILE * I of the i-block a work unit covers; jt, the
 // j bodies of a unit (TILE, TILE / 2 or TILE / 4), which sets how many units
-// a small cluster has; and b resident blocks per SM, which sets the persistent
-// grid G = b * SMs (at most the unit count) and so how finely the units are
-// cut into per-block runs.  The best shape depends on the arithmetic
+// a small cluster has; and b blocks per SM, which sets the grid G = b * SMs
+// (at most the unit count) and so how finely the units are cut into
+// per-block runs: up to the occupancy limit one resident wave, above it
+// several waves of shorter runs.  The best shape depends on the arithmetic
 // (registers per thread), on N (small clusters need more, smaller units to
 // fill 152 SMs) and on the cluster mix of a batch, so it is measured rather
 // than modelled: every variant the library has compiled is timed on the
@@ -19,6 +20,7 @@
 // results of two shapes can differ at the rounding level (within the
 // precision's tolerance); with one shape they are bit-reproducible.
 #include <cstdio>
+#include <initializer_list>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -176,6 +178,7 @@ int tune_pair(const Pool &P, ClusterSet &C, int precision, const Phys &ph, cudaS
     rep.precision = precision;
     PairShape best{0, 0, 0};
     double best_ms = 0;
+    int64_t best_gw = 0;
     std::vector<int64_t> seen;   // (I, grid, jt) already timed
     do {
         // the shape the planner would pick without a tuned entry
@@ -193,8 +196,14 @@ int tune_pair(const Pool &P, ClusterSet &C, int precision, const Phys &ph, cudaS
             for (int32_t k = 0; k < C.K; ++k)
                 w_full += ((C.nk[k] + TILE * I - 1) / (TILE * I)) * ((C.nk[k] + TILE - 1) / TILE);
             const bool scarce = w_full < 2 * (int64_t)P.num_sms * occ;
+            // grids of 1 to MAX_WAVES resident waves, and single waves a
+            // little below the occupancy limit
+            int bs[8], nb = 0;
+            for (int w : {MAX_WAVES, DEFAULT_WAVES, 2}) bs[nb++] = w * occ;
+            for (int b = occ; b >= 1 && b > occ - 4; --b) bs[nb++] = b;
             for (int jt = TILE; rc == NB_OK && jt >= (scarce ? 32 : TILE); jt /= 2)
-            for (int b = occ; b >= 1 && b > occ - 4; --b) {
+            for (int q = 0; q < nb; ++q) {
+                const int b = bs[q];
                 const PairShape s{I, b, jt};
                 Plan pl;
                 rc = plan_make(P, C, precision, st, pl, &s, false);
@@ -208,9 +217,16 @@ int tune_pair(const Pool &P, ClusterSet &C, int precision, const Phys &ph, cudaS
                 rc = time_plan(P, C, pl, ph, st, reps, e0, e1, &ms);
                 if (rc) break;
                 ++rep.candidates;
-                if (best.I == 0 || ms < best_ms) {
+                // more blocks x i-block width means more partial slots for
+                // the kick to sum: such a shape has to win by 0.5%, one with
+                // fewer may lose by as much
+                const double tie = 1.005;
+                const int64_t gw = pl.pl.d.G * I;
+                if (best.I == 0 || ms * (gw > best_gw ? tie : 1.0) <
+                                       best_ms * (gw < best_gw ? tie : 1.0)) {
                     best = s;
                     best_ms = ms;
+                    best_gw = gw;
                     rep.grid = pl.pl.d.G;
                 }
             }
