@@ -486,8 +486,9 @@ int enq_step(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph,
         NB_TRY(launch_frame(s, ph.near_frac, near, st));
         count(kernels, near ? 4 : 2);
     }
-    // drift of the first leapfrog's half step (and the split it feeds)
-    NB_TRY(launch_kick_drift(s, pl.pl.d, 0.0, 0.5 * wk[0] * h, 0, sp ? 1 : 0, ph.ext, st));
+    // drift of the first leapfrog's half step (and the split it feeds, mass
+    // words included: the later splits of the step rewrite coordinates only)
+    NB_TRY(launch_kick_drift(s, pl.pl.d, 0.0, 0.5 * wk[0] * h, 0, sp ? 2 : 0, ph.ext, st));
     count(kernels, 1);
     for (int k = 0; k < K; ++k) {
         // adjacent half drifts of consecutive leapfrogs merge

@@ -11,6 +11,7 @@
 // Reductions run per segment (a run of one cluster's bodies), then one block
 // per cluster adds its segments in a fixed tree order.
 #include "nb_internal.cuh"
+#include "split.cuh"
 
 namespace nb {
 
@@ -315,27 +316,34 @@ cudaError_t launch_frame(const DevState &s, double near_frac, bool near, cudaStr
 
 // hi = fl32(x - c), lo = fl32((x - c) - hi): the double-single representation
 // of Sect. 5.2, taken relative to the cluster's frame origin.
+// MASS: also write the mass words of the j-stream copies (m and its float
+// rounding residue); the kick's per-substep splits leave them as the step's
+// first split wrote them (masses never change).
+template <bool MASS>
 __device__ __forceinline__ void split_one(const DevState &s, const Frame &f, int64_t i,
                                           double x, double y, double z)
 {
-    const double rx = x - f.cx, ry = y - f.cy, rz = z - f.cz;
-    const float hx = __double2float_rn(rx), hy = __double2float_rn(ry),
-                hz = __double2float_rn(rz);
+    float hx, hy, hz, lx, ly, lz;
+    split_ds(x - f.cx, hx, lx);
+    split_ds(y - f.cy, hy, ly);
+    split_ds(z - f.cz, hz, lz);
     s.xh[i] = hx;
     s.yh[i] = hy;
     s.zh[i] = hz;
-    const float lx = __double2float_rn(rx - (double)hx);
-    const float ly = __double2float_rn(ry - (double)hy);
-    const float lz = __double2float_rn(rz - (double)hz);
     s.xl[i] = lx;
     s.yl[i] = ly;
     s.zl[i] = lz;
-    const float m = s.mf[i];
-    const float ml = __double2float_rn(s.m[i] - (double)m);   // mass lo part (float-float mode)
     s.jd[2 * i] = make_float4(hx, hx, hy, hy);
-    s.jd[2 * i + 1] = make_float4(hz, hz, m, m);
     s.jl[2 * i] = make_float4(lx, lx, ly, ly);
-    s.jl[2 * i + 1] = make_float4(lz, lz, ml, ml);
+    if (MASS) {
+        const float m = s.mf[i];
+        const float ml = __double2float_rn(s.m[i] - (double)m);   // mass lo part (float-float)
+        s.jd[2 * i + 1] = make_float4(hz, hz, m, m);
+        s.jl[2 * i + 1] = make_float4(lz, lz, ml, ml);
+    } else {
+        *reinterpret_cast<float2 *>(&s.jd[2 * i + 1]) = make_float2(hz, hz);
+        *reinterpret_cast<float2 *>(&s.jl[2 * i + 1]) = make_float2(lz, lz);
+    }
 }
 
 __global__ void split_kernel(DevState s)
@@ -345,7 +353,7 @@ __global__ void split_kernel(DevState s)
     const BodyRef r = body_at(s.cl, t);
     const int64_t i = r.gi;
     s.mf[i] = __double2float_rn(s.m[i]);
-    split_one(s, s.cl.frame[r.k], i, s.x[i], s.y[i], s.z[i]);
+    split_one<true>(s, s.cl.frame[r.k], i, s.x[i], s.y[i], s.z[i]);
 }
 
 cudaError_t launch_split(const DevState &s, cudaStream_t st)
@@ -427,7 +435,10 @@ __global__ void kick_drift_kernel(DevState s, Decomp d, double wk, double wd, in
     s.x[i] = x;
     s.y[i] = y;
     s.z[i] = z;
-    if (do_split) split_one(s, s.cl.frame[r.k], i, x, y, z);
+    if (do_split == 2)
+        split_one<true>(s, s.cl.frame[r.k], i, x, y, z);
+    else if (do_split)
+        split_one<false>(s, s.cl.frame[r.k], i, x, y, z);
 }
 
 cudaError_t launch_kick_drift(const DevState &s, const Decomp &d, double wk, double wd,

@@ -140,9 +140,21 @@ struct Decomp {
     // decision a launch-wide constant
     int32_t mask_self = 0;
 
-    __host__ __device__ int64_t U(int64_t g) const { return (g * W) / G; }
+    // 1 when (W + 1) (G + 1) < 2^32: U and owner then divide in 32 bits (a
+    // 64-bit division costs tens of instructions, on the kick's hot path)
+    int32_t narrow = 0;
+    __host__ __device__ int64_t U(int64_t g) const
+    {
+        if (narrow) return (int64_t)(((uint32_t)g * (uint32_t)W) / (uint32_t)G);
+        return (g * W) / G;
+    }
     // largest g with U(g) <= u
-    __host__ __device__ int64_t owner(int64_t u) const { return ((u + 1) * G + W - 1) / W - 1; }
+    __host__ __device__ int64_t owner(int64_t u) const
+    {
+        if (narrow)
+            return (int64_t)(((uint32_t)(u + 1) * (uint32_t)G + (uint32_t)W - 1u) / (uint32_t)W) - 1;
+        return ((u + 1) * G + W - 1) / W - 1;
+    }
     // units per i-block of a cluster of ntiles TILE-wide j-tiles
     __host__ __device__ int64_t units_per_iblock(int64_t ntiles) const
     {
@@ -155,7 +167,7 @@ struct Decomp {
 __device__ __forceinline__ void iblock_slots(const Decomp &d, const Clusters &c, int32_t k,
                                              int64_t li, int64_t &first, int64_t &count)
 {
-    const int64_t b = li / d.ipb - d.b0;
+    const int64_t b = (li >> (__ffs(d.ipb) - 1)) - d.b0;   // ipb = TILE * I, a power of two
     const int64_t nt = d.units_per_iblock(c.ntiles[k]);
     const int64_t u0 = c.uoff[k] + b * nt;
     first = d.owner(u0);
@@ -240,8 +252,9 @@ cudaError_t launch_frame(const DevState &s, double near_frac, bool near, cudaStr
 cudaError_t launch_mass_range(const DevState &s, cudaStream_t st);
 cudaError_t launch_split(const DevState &s, cudaStream_t st);
 // One fused substep: optional kick v += wk dt_k (a_int + a_ext) from the
-// partial slots of decomposition d, then drift x += wd dt_k v, then
-// (optionally) refresh the float planes.
+// partial slots of decomposition d, then drift x += wd dt_k v, then refresh
+// the float planes: do_split 0 no, 1 coordinates only, 2 coordinates and the
+// j-stream mass words (needed once after any load; masses never change).
 cudaError_t launch_kick_drift(const DevState &s, const Decomp &d, double wk, double wd,
                               int do_kick, int do_split, const ExtField &ext, cudaStream_t st);
 cudaError_t launch_accel_out(const DevState &s, const Decomp &d, const ExtField &ext,

@@ -52,6 +52,7 @@ Decomp make_decomp(int64_t W, int64_t max_ntiles, int ipb, int64_t G, int64_t sl
         G = G - G / 8 - 1;
         if (G < 1) G = 1;
     }
+    d.narrow = (double)(d.W + 1) * (double)(d.G + 1) < 4294967296.0 ? 1 : 0;
     return d;
 }
 

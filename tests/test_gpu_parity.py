@@ -228,6 +228,29 @@ def test_deterministic_and_resumable(nbs):
         np.testing.assert_array_equal(v2, v_full)
 
 
+def test_many_slot_reduction_is_deterministic(nbs, orc):
+    """Grids run in waves give an i-block tens of partial slots, summed in
+    slot order by whichever block finishes the i-block last: repeated
+    evaluations (different arrival orders) must agree bit for bit, and the
+    sum must match the oracle."""
+    n = 32768
+    pos, vel, m = system(n, seed=23, offset=True)
+    eps = ics.paper_softening(n)
+    idx = np.arange(0, n, 97)
+    ref = orc.accel_int_at(pos, m, idx, 1.0, eps)
+    ext = orc.ext_accel(ext_params(orc, eps, True), pos[idx])
+    for prec in ("ds", "fp64", "dd"):
+        with nbs.Context(n, eps=eps, precision=prec, ext_on=True) as c:
+            c.load(pos, vel, m)
+            shape = c.pair_shape()
+            assert shape["grid"] > 3 * 152, shape   # more than one resident wave
+            a = [c.accel() for _ in range(4)]
+        for q in a[1:]:
+            np.testing.assert_array_equal(q, a[0])
+        err = rel_rms(a[0][idx] - ext, ref)
+        assert err <= TOL[prec], (prec, err)
+
+
 def test_state_errors(nbs):
     with nbs.Context(10, eps=0.01) as c:
         with pytest.raises(nbs.NBError) as e:

@@ -1,0 +1,109 @@
+"""The double-single split taken from the bits of a double (csrc/split.cuh)
+against the plain conversions hi = RN_float(r), lo = RN_float(r - hi), bit for
+bit, on the GPU: random doubles over the whole fast-path exponent range and
+both fallbacks, round-to-even ties of either parity, roundings that carry into
+the exponent, signed zeros, subnormals, infinities and NaN."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                    "paper_1003_3896_gb300", "csrc")
+
+SRC = r"""
+#include <cstdio>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#include <cuda_runtime.h>
+#include "split.cuh"
+
+__global__ void check(const double *r, int n, unsigned long long *bad, int *first)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    float hi, lo;
+    nb::split_ds(r[t], hi, lo);
+    const float h0 = __double2float_rn(r[t]);
+    const float l0 = __double2float_rn(r[t] - (double)h0);
+    const bool same_h = __float_as_int(hi) == __float_as_int(h0) || (h0 != h0 && hi != hi);
+    const bool same_l = __float_as_int(lo) == __float_as_int(l0) || (l0 != l0 && lo != lo);
+    if (!(same_h && same_l)) {
+        atomicAdd(bad, 1ull);
+        atomicMin(first, t);
+    }
+}
+
+static double from_bits(uint64_t b) { double d; std::memcpy(&d, &b, 8); return d; }
+
+int main()
+{
+    std::vector<double> v;
+    uint64_t s = 0x9E3779B97F4A7C15ull;
+    auto next = [&]() { s ^= s << 13; s ^= s >> 7; s ^= s << 17; return s; };
+    // random mantissas over exponents 900 .. 1150 (fast path is 953 .. 1123)
+    for (int e = 900; e <= 1150; ++e)
+        for (int k = 0; k < 4000; ++k) {
+            const uint64_t m = next() & 0xFFFFFFFFFFFFFull;
+            const uint64_t sign = (next() & 1) << 63;
+            v.push_back(from_bits(sign | ((uint64_t)e << 52) | m));
+        }
+    // ties (low 29 bits exactly half) with odd and even kept bit, carries
+    for (int e : {953, 1000, 1023, 1050, 1123}) {
+        for (int k = 0; k < 2000; ++k) {
+            uint64_t m = next() & 0xFFFFFFFFFFFFFull;
+            m = (m & ~0x1FFFFFFFull) | 0x10000000ull;
+            v.push_back(from_bits(((uint64_t)e << 52) | m));
+            v.push_back(from_bits((1ull << 63) | ((uint64_t)e << 52) | m));
+        }
+        v.push_back(from_bits(((uint64_t)e << 52) | 0xFFFFFFFFFFFFFull));
+        v.push_back(from_bits(((uint64_t)e << 52) | 0xFFFFFF0000000ull | 0x10000000ull));
+        v.push_back(from_bits(((uint64_t)e << 52) | 0xFFFFFFE000000ull | 0x10000000ull));
+        v.push_back(from_bits((1ull << 63) | ((uint64_t)e << 52) | 0xFFFFFFFFFFFFFull));
+    }
+    // zeros, subnormals, tiny, huge, infinities, NaN
+    for (uint64_t b : {0ull, 1ull << 63, 1ull, 0x000FFFFFFFFFFFFFull, 0x0010000000000000ull,
+                       0x7FEFFFFFFFFFFFFFull, 0x7FF0000000000000ull, 0xFFF0000000000000ull,
+                       0x7FF8000000000000ull})
+        v.push_back(from_bits(b));
+    const int n = (int)v.size();
+    double *d_r = nullptr;
+    unsigned long long *d_bad = nullptr;
+    int *d_first = nullptr;
+    if (cudaMalloc(&d_r, sizeof(double) * n) || cudaMalloc(&d_bad, 8) || cudaMalloc(&d_first, 4))
+        return 2;
+    const int big = n;
+    cudaMemcpy(d_r, v.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
+    cudaMemset(d_bad, 0, 8);
+    cudaMemcpy(d_first, &big, 4, cudaMemcpyHostToDevice);
+    check<<<(n + 255) / 256, 256>>>(d_r, n, d_bad, d_first);
+    unsigned long long bad = 0;
+    int first = 0;
+    if (cudaMemcpy(&bad, d_bad, 8, cudaMemcpyDeviceToHost) ||
+        cudaMemcpy(&first, d_first, 4, cudaMemcpyDeviceToHost))
+        return 3;
+    std::printf("checked %d mismatches %llu first %d\n", n, bad, first);
+    if (bad) {
+        uint64_t b;
+        std::memcpy(&b, &v[first], 8);
+        std::printf("first mismatch bits %016llx\n", (unsigned long long)b);
+    }
+    return bad ? 1 : 0;
+}
+"""
+
+
+def test_split_matches_plain_conversions(tmp_path):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    src = tmp_path / "split_check.cu"
+    src.write_text(SRC)
+    exe = tmp_path / "split_check"
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-std=c++17",
+                    "-I", CSRC, str(src), "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "mismatches 0" in r.stdout
