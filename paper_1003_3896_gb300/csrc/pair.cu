@@ -374,7 +374,11 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
 // float-float), m / r^3 and the sums are all float-float.  Against a plain FP64
 // sum it agrees to ~1e-14 relative (the 48-bit coordinates alone account for
 // that), so it stands in for the FP64 pipe, which on this GPU runs at 1/77 of
-// the FP32 rate.
+// the FP32 rate.  The sums of r^2 + eps^2, whose terms are all non-negative,
+// order their operands with max / min (ALU pipe) and use Dekker's three-
+// operation sum; signed sums keep Knuth's six (ordering them by magnitude
+// costs more issue slots than it saves).  UM (all masses of the cluster
+// equal): 1 / r^3 without m, the caller scales by m.
 
 __device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __fadd2_rn(a, f2neg(b)); }
@@ -392,6 +396,17 @@ __device__ __forceinline__ void fast_two_sum2(float2 a, float2 b, float2 &s, flo
 {
     s = __fadd2_rn(a, b);
     e = f2sub(b, f2sub(s, a));
+}
+
+// s + e = a + b exactly for a, b >= 0: the larger operand first (max / min
+// run on the ALU pipe, which this kernel leaves idle), then Dekker's fast
+// two-sum, three FMA-pipe operations instead of Knuth's six.
+__device__ __forceinline__ void pos_two_sum2(float2 a, float2 b, float2 &s, float2 &e)
+{
+    const float2 hi = make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y));
+    const float2 lo = make_float2(fminf(a.x, b.x), fminf(a.y, b.y));
+    s = __fadd2_rn(a, b);
+    e = f2sub(lo, f2sub(s, hi));
 }
 
 // (ah + al) - (bh + bl), normalised.
@@ -429,7 +444,7 @@ struct FFI {
     float2 axh[P], axl[P], ayh[P], ayl[P], azh[P], azl[P];   // running sums
 };
 
-template <int P, bool MASK>
+template <int P, bool MASK, bool UM>
 __device__ __forceinline__ void chunk_pass_ff(const float4 (*cb)[4], int j0, int ibase,
                                               FFI<P> &q, float2 e2h, float2 e2l)
 {
@@ -452,30 +467,35 @@ __device__ __forceinline__ void chunk_pass_ff(const float4 (*cb)[4], int j0, int
             ff_sq(dxh, dxl, px, ex);
             ff_sq(dyh, dyl, py, ey);
             ff_sq(dzh, dzl, pz, ez);
-            float2 s1, t1, s2, t2, s3, t3;
-            two_sum2(px, py, s1, t1);
-            two_sum2(s1, pz, s2, t2);
-            two_sum2(s2, e2h, s3, t3);
+            float2 s1, t1, s2, t2, s3, t3;   // all terms >= 0
+            pos_two_sum2(px, py, s1, t1);
+            pos_two_sum2(s1, pz, s2, t2);
+            pos_two_sum2(s2, e2h, s3, t3);
             float2 err = __fadd2_rn(__fadd2_rn(__fadd2_rn(ex, ey), __fadd2_rn(ez, e2l)),
                                     __fadd2_rn(__fadd2_rn(t1, t2), t3));
             float2 rh, rl;
             fast_two_sum2(s3, err, rh, rl);
             // 1 / sqrt(r^2): float estimate, one Newton step in float-float
             const float2 y0 = make_float2(rsqrt_mufu(rh.x), rsqrt_mufu(rh.y));
-            const float2 th = __fmul2_rn(y0, y0);
-            const float2 tl = __ffma2_rn(y0, y0, f2neg(th));
-            const float2 pp = __fmul2_rn(rh, th);
-            float2 pe = __ffma2_rn(rh, th, f2neg(pp));
-            pe = __ffma2_rn(rh, tl, pe);
-            pe = __ffma2_rn(rl, th, pe);
-            const float2 v = f2sub(f2sub(one, pp), pe);   // 1 - r^2 y0^2 (1 - pp exact)
+            // v = 1 - (rh + rl) y0^2: w + wl = rh y0 exactly, and 1 - w y0
+            // is small (y0 is good to ~2^-22), so one FMA forms it to ~2^-46
+            const float2 w = __fmul2_rn(rh, y0);
+            const float2 wl = __ffma2_rn(rh, y0, f2neg(w));
+            float2 v = __ffma2_rn(f2neg(w), y0, one);
+            v = __ffma2_rn(f2neg(wl), y0, v);
+            v = __ffma2_rn(f2neg(__fmul2_rn(rl, y0)), y0, v);
             float2 yh, yl;
             fast_two_sum2(y0, __fmul2_rn(__fmul2_rn(half, y0), v), yh, yl);
-            // s = m / r^3
-            float2 p2, e2, p3, e3, sh, sl;
+            // s = m / r^3 (UM: 1 / r^3, the caller scales by m)
+            float2 p2, e2, sh, sl;
             ff_sq(yh, yl, p2, e2);
-            ff_mul(p2, e2, yh, yl, p3, e3);
-            ff_mul(mjh, mjl, p3, e3, sh, sl);
+            if (UM) {
+                ff_mul(p2, e2, yh, yl, sh, sl);
+            } else {
+                float2 p3, e3;
+                ff_mul(p2, e2, yh, yl, p3, e3);
+                ff_mul(mjh, mjl, p3, e3, sh, sl);
+            }
             if (MASK) {
                 const int j = j0 + jj;
                 if (j == ibase + 2 * p * TILE) sh.x = sl.x = 0.f;
@@ -499,7 +519,7 @@ __device__ __forceinline__ void chunk_pass_ff(const float4 (*cb)[4], int j0, int
     }
 }
 
-template <int P, int KC>
+template <int P, int KC, bool UM>
 __global__ void __launch_bounds__(TILE) pair_ff_kernel(
     const float4 *__restrict__ jd, const float4 *__restrict__ jl,
     const float *__restrict__ xh, const float *__restrict__ yh, const float *__restrict__ zh,
@@ -574,9 +594,9 @@ __global__ void __launch_bounds__(TILE) pair_ff_kernel(
             }
             const bool diag = mask_self && jc < ib0 + d.ipb && jc + CH > ib0;
             if (diag)
-                chunk_pass_ff<P, true>(cb, jc, ibase, q, e2h, e2l);
+                chunk_pass_ff<P, true, UM>(cb, jc, ibase, q, e2h, e2l);
             else
-                chunk_pass_ff<P, false>(cb, jc, ibase, q, e2h, e2l);
+                chunk_pass_ff<P, false, UM>(cb, jc, ibase, q, e2h, e2l);
             __syncwarp();
 #pragma unroll
             for (int p = 0; p < P; ++p) {
@@ -590,14 +610,15 @@ __global__ void __launch_bounds__(TILE) pair_ff_kernel(
                     make_float2(0.f, 0.f);
             }
         }
+        const double Gm = UM ? G * (KC > 0 ? tab.mu[sg.k] : c.mu[sg.k]) : G;
 #pragma unroll
         for (int k = 0; k < I; ++k) {
             const int i = ibase + k * TILE;
             if (i < n) {
                 double *o = part + (sg.slot * 3) * cap + base + i;
-                o[0] = G * dax[k];
-                o[cap] = G * day[k];
-                o[2 * cap] = G * daz[k];
+                o[0] = Gm * dax[k];
+                o[cap] = Gm * day[k];
+                o[2 * cap] = Gm * daz[k];
             }
         }
         u += sg.t1 - sg.t0;
@@ -721,8 +742,10 @@ static sp_kernel_t<KC> sp_variant(int mode, int I, bool um = false)
     NB_SP(PM_DS_FULL, 2) NB_SP(PM_DS_FULL, 4)
     NB_SP(PM_FP32, 2) NB_SP(PM_FP32, 4) NB_SP(PM_FP32, 8)
 #undef NB_SP
-    if (mode == PM_DD && I == 2) return pair_ff_kernel<1, KC>;
-    if (mode == PM_DD && I == 4) return pair_ff_kernel<2, KC>;
+    if (mode == PM_DD && I == 2)
+        return um ? pair_ff_kernel<1, KC, true> : pair_ff_kernel<1, KC, false>;
+    if (mode == PM_DD && I == 4)
+        return um ? pair_ff_kernel<2, KC, true> : pair_ff_kernel<2, KC, false>;
     return nullptr;
 }
 
@@ -733,7 +756,7 @@ template <int KC>
 static cudaError_t launch_sp(const DevState &s, const PairLaunch &pl, const HostTab &ht,
                              double G, cudaStream_t st)
 {
-    sp_kernel_t<KC> k = sp_variant<KC>(pl.mode, pl.I, pl.um && pl.mode != PM_DD);
+    sp_kernel_t<KC> k = sp_variant<KC>(pl.mode, pl.I, pl.um);
     if (!k) return cudaErrorInvalidValue;
     TabOf<KC> t;
     std::memset(&t, 0, sizeof t);
