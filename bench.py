@@ -119,6 +119,23 @@ PAIR_TRAFFIC = {"source_sha256": "067ee3fc3700ecbf", "n": 65536, "precision": "d
                 "bodies_per_thread": 8, "blocks_per_sm": 12, "bytes_per_launch": 3183360.0}
 
 
+# The paper's own throughput (Table 3, GFLOPS at 20 flops per pair, leapfrog)
+# on its hardware, quoted beside the headline as context, not as a target:
+# NBSympleC runs the pair sum on one Tesla C1060, NBSympleE on two, hosted by
+# two quad-core 2.00 GHz Xeons (Sect. 4.1); per Sect. 5.1 the two-GPU version
+# takes about a minute per leapfrog step at N = 1,536,000.
+PAPER_CONTEXT = {
+    "source": "paper Table 3 (GFLOPS, 20 flops per pair, leapfrog) and Sect. 5.1",
+    "hardware": "Tesla C1060 (1 GPU: NBSympleC; 2 GPUs: NBSympleE), host 2x quad-core "
+                "Xeon 2.00 GHz, 2010",
+    "n": [480, 30720, 1536000],
+    "sp_gflops_1gpu": [5.97, 409.0, 423.0], "dp_gflops_1gpu": [3.36, 21.9, 22.0],
+    "sp_gflops_2gpu": [11.29, 797.0, 846.0], "dp_gflops_2gpu": [3.37, 43.8, 44.0],
+    "two_gpu_leapfrog_step_s_at_n_1536000": 60.0,
+    "note": "other hardware: context only",
+}
+
+
 def pair_traffic(n: int, precision: str, shape: dict):
     import hashlib
     path = os.path.join(ROOT, "paper_1003_3896_gb300", "csrc", "pair.cu")
@@ -395,6 +412,7 @@ def main():
                 "d2h_bytes_per_step": n * 6 * 8, "steps": e2e_steps},
         "gpu_launches": prof["kernel_launches"],
         "clocks": clocks, "wall_s_timed": wall,
+        "paper_context": PAPER_CONTEXT,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pos, m, eps)
