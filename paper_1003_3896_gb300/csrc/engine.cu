@@ -118,18 +118,14 @@ int set_create(ClusterSet &C, int32_t kcap, int64_t body_cap)
         }
     };
     A((void **)&C.red, (size_t)C.scap * 16 * 8);
-    A((void **)&C.ng_key, (size_t)body_cap * 8);
     A((void **)&C.ng_bucket, (size_t)body_cap * 4);
     A((void **)&C.ng_entry, (size_t)body_cap * 4);
     A((void **)&C.ng_rank, (size_t)body_cap * 4);
-    A((void **)&C.ng_reg, (size_t)body_cap * 8);
     A((void **)&C.ng_count, (size_t)C.ng_hcap * 4);
     A((void **)&C.ng_start, (size_t)(C.ng_hcap + 1) * 4);
     A((void **)&C.ng_bsum, (size_t)(C.ng_hcap / 1024 + 1) * 4);
     A((void **)&C.flag, sizeof(int));
     A((void **)&C.cid, (size_t)body_cap * 4);
-    A((void **)&C.ng_pos, (size_t)body_cap * 16);
-    A((void **)&C.ng_lo, (size_t)body_cap * 16);
     A((void **)&C.ng_spos, (size_t)body_cap * 16);
     A((void **)&C.ng_slo, (size_t)body_cap * 16);
     A((void **)&C.ng_slot, (size_t)C.ng_hcap * sizeof(NgSlot));
@@ -144,10 +140,9 @@ int set_create(ClusterSet &C, int32_t kcap, int64_t body_cap)
 
 void set_destroy(ClusterSet &C)
 {
-    void *ptrs[] = {C.dmem,     C.red,      C.ng_key,  C.ng_bucket, C.ng_entry,
-                    C.ng_count, C.ng_start, C.ng_bsum, C.flag,      C.cid,
-                    C.ng_pos,   C.ng_lo,    C.ng_spos, C.ng_slo,    C.ng_slot,
-                    C.ng_rank,  C.ng_reg};
+    void *ptrs[] = {C.dmem,     C.red,      C.ng_bucket, C.ng_entry, C.ng_count,
+                    C.ng_start, C.ng_bsum,  C.flag,      C.cid,      C.ng_spos,
+                    C.ng_slo,   C.ng_slot,  C.ng_rank};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     C = ClusterSet();
@@ -395,20 +390,16 @@ DevState view(const Pool &P, const ClusterSet &C, int precision)
     s.diag = C.diag;
     s.red = C.red;
     s.red_len = C.scap * 16;
-    s.ng_key = C.ng_key;
     s.ng_bucket = C.ng_bucket;
     s.ng_entry = C.ng_entry;
     s.ng_count = C.ng_count;
     s.ng_start = C.ng_start;
     s.ng_bsum = C.ng_bsum;
     s.ng_hcap = C.ng_hcap;
-    s.ng_pos = C.ng_pos;
-    s.ng_lo = C.ng_lo;
     s.ng_spos = C.ng_spos;
     s.ng_slo = C.ng_slo;
     s.ng_slot = C.ng_slot;
     s.ng_rank = C.ng_rank;
-    s.ng_reg = C.ng_reg;
     s.flag = C.flag;
     if (precision != NB_DS) s.corr = nullptr;
     return s;

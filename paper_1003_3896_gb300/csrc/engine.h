@@ -53,13 +53,11 @@ struct ClusterSet {
     // per-set scratch, so sets in one pool can run concurrently on different
     // streams: near-pair hash grid over the set's linear bodies and the flag
     int64_t body_cap = 0, ng_hcap = 0;
-    uint64_t *ng_key = nullptr;
     int *ng_bucket = nullptr, *ng_rank = nullptr, *ng_entry = nullptr, *ng_count = nullptr,
         *ng_start = nullptr, *ng_bsum = nullptr, *flag = nullptr;
     int32_t *cid = nullptr;    // linear body -> cluster map
-    float4 *ng_pos = nullptr, *ng_lo = nullptr, *ng_spos = nullptr, *ng_slo = nullptr;
+    float4 *ng_spos = nullptr, *ng_slo = nullptr;
     NgSlot *ng_slot = nullptr;
-    int2 *ng_reg = nullptr;
     Frame *frame = nullptr;    // [kcap]
     double *diag = nullptr;    // [kcap][DIAG_STRIDE]
     Clusters cl, cl_pot;       // device views (pair units / potential units)

@@ -96,14 +96,11 @@ struct DevState {
     int64_t part_slots = 0;
     // near-pair correction of the mixed mode (nullptr corr: not applied)
     double *corr = nullptr;     // [3][cap]
-    uint64_t *ng_key = nullptr; // cell key per linear body
     // per linear body: table slot of its cell, arrival rank in the cell, and
     // (per cell-ordered position) the body index before ordering
     int *ng_bucket = nullptr, *ng_rank = nullptr, *ng_entry = nullptr;
-    int2 *ng_reg = nullptr;   // per linear body: its cluster's slot region (first, size)
-    // compact copies per linear body (hi x, y, z, m) and (lo x, y, z, side
-    // bits), and the same in cell order (lo.w = linear index)
-    float4 *ng_pos = nullptr, *ng_lo = nullptr, *ng_spos = nullptr, *ng_slo = nullptr;
+    // cell-ordered copies (hi x, y, z, m) and (lo x, y, z, linear index)
+    float4 *ng_spos = nullptr, *ng_slo = nullptr;
     NgSlot *ng_slot = nullptr;                       // cell table [H]
     int *ng_count = nullptr, *ng_start = nullptr;    // per slot (start: H + 1)
     int *ng_bsum = nullptr;                          // scan block totals

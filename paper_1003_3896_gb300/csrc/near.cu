@@ -47,7 +47,6 @@ constexpr int CELL_OFF = 1 << (CELL_BITS - 1);
 constexpr int CELL_MAX = CELL_OFF - 2;        // |cell| <= CELL_MAX, neighbours <= CELL_OFF - 1
 constexpr float CELL_SCALE = 2.2f;            // h / d_th
 constexpr unsigned long long NG_EMPTY = ~0ull;
-constexpr int NO_GRID = 8;                    // side bits: body not in the grid (d_th = 0)
 
 __device__ __forceinline__ uint64_t cell_key(int32_t k, int cx, int cy, int cz)
 {
@@ -96,8 +95,8 @@ __device__ __forceinline__ int cell_coord(float v, float inv_h, int &side)
     return (int)fminf(fmaxf(f, -(float)CELL_MAX), (float)CELL_MAX);
 }
 
-// Per body: compact float copies, the cell key, insertion of the cell into
-// the slot table and the body's rank among its cell's arrivals.
+// Per body: the cell key, insertion of the cell into the slot table and the
+// body's rank among its cell's arrivals.
 __global__ void near_cell_kernel(DevState s)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -105,25 +104,18 @@ __global__ void near_cell_kernel(DevState s)
     const int32_t k = cluster_of(s.cl, t);
     const int64_t i = s.cl.boff[k] + t - s.cl.noff[k];
     const float dth = s.cl.frame[k].dth;
-    const float x = s.xh[i], y = s.yh[i], z = s.zh[i];
-    s.ng_pos[t] = make_float4(x, y, z, s.mf[i]);
     if (!(dth > 0.f)) {   // no pair can pass the test r^2 + eps^2 < eps^2
-        s.ng_key[t] = cell_key(k, 0, 0, 0);
-        s.ng_lo[t] = make_float4(s.xl[i], s.yl[i], s.zl[i], __int_as_float(NO_GRID));
         s.ng_bucket[t] = -1;
         return;
     }
     const float ih = 1.0f / (CELL_SCALE * dth);
     int sx, sy, sz;
-    const int cx = cell_coord(x, ih, sx), cy = cell_coord(y, ih, sy), cz = cell_coord(z, ih, sz);
-    const int bits = (sx > 0 ? 1 : 0) | (sy > 0 ? 2 : 0) | (sz > 0 ? 4 : 0);
-    s.ng_lo[t] = make_float4(s.xl[i], s.yl[i], s.zl[i], __int_as_float(bits));
+    const int cx = cell_coord(s.xh[i], ih, sx), cy = cell_coord(s.yh[i], ih, sy),
+              cz = cell_coord(s.zh[i], ih, sz);
     const uint64_t key = cell_key(k, cx, cy, cz);
-    s.ng_key[t] = key;
     // the region has more slots than the cluster has bodies, so a free or
     // matching slot always exists; the bound only caps the loop
     const Region rg = region_of(s.cl, k);
-    s.ng_reg[t] = make_int2((int)rg.base, (int)rg.size);
     int64_t b = slot_of(key, rg);
     for (uint32_t p = 0; p < rg.size; ++p) {
         const unsigned long long prev = atomicCAS(&s.ng_slot[b].key, NG_EMPTY, key);
@@ -203,11 +195,13 @@ __global__ void __launch_bounds__(TOP_T) scan_top_kernel(int *bsum, int nb)
     }
 }
 
-__global__ void scan_add_kernel(int *out, const int *bsum, int64_t H, int64_t n)
+// Adds the block offsets; out[H] = the number of bodies in the grid (fewer
+// than n when a cluster has no near radius, e.g. a single body).
+__global__ void scan_add_kernel(int *out, const int *bsum, const int *count, int64_t H)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < H) out[i] += bsum[i / SCAN_B];
-    if (i == 0) out[H] = (int)n;
+    if (i == H - 1) out[H] = out[i] + count[i];
 }
 
 // Bodies into their cell's range, in arrival order.
@@ -221,52 +215,57 @@ __global__ void near_scatter_kernel(DevState s)
 }
 
 // Final place of each body in its cell = number of cell members with a
-// smaller linear index; writes the cell-ordered copies (lo.w = t) and, from
-// the cell's first body, the slot's range.
+// smaller linear index; writes the cell-ordered copies of its float planes
+// (lo.w = t) and, from the cell's first body, the slot's range.  Bodies
+// outside the grid get their (zero) correction here.
 __global__ void near_rank_kernel(DevState s)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= s.n) return;
     const int b = s.ng_bucket[t];
-    if (b < 0) return;
+    const int32_t k = cluster_of(s.cl, t);
+    const int64_t i = s.cl.boff[k] + t - s.cl.noff[k];
+    if (b < 0) {   // not in the grid (no near radius): no correction
+        s.corr[i] = 0.0;
+        s.corr[s.cap + i] = 0.0;
+        s.corr[2 * s.cap + i] = 0.0;
+        return;
+    }
     const int lo = s.ng_start[b], hi = s.ng_start[b + 1];
     int r = 0;
     for (int e = lo; e < hi; ++e) r += s.ng_entry[e] < (int)t ? 1 : 0;
-    s.ng_spos[lo + r] = s.ng_pos[t];
-    float4 l = s.ng_lo[t];
-    l.w = __int_as_float((int)t);
-    s.ng_slo[lo + r] = l;
+    s.ng_spos[lo + r] = make_float4(s.xh[i], s.yh[i], s.zh[i], s.mf[i]);
+    s.ng_slo[lo + r] = make_float4(s.xl[i], s.yl[i], s.zl[i], __int_as_float((int)t));
     if (r == 0) {
         s.ng_slot[b].start = lo;
         s.ng_slot[b].end = hi;
     }
 }
 
-// One thread per body t: probe its 8 cells (first loads issued together),
-// then visit their bodies in cell order.  UM: the pair kernel left the common
+// One thread per body in cell order (entry e of the cell-ordered copies), so
+// that the threads of a warp share cells, probes and member lists: probe its
+// 8 cells (first loads issued together), then visit their bodies in cell
+// order.  The cell and side are recomputed from the copy's float position
+// with the cell kernel's arithmetic.  Bodies outside the grid got a zero
+// correction from near_rank_kernel.  UM: the pair kernel left the common
 // mass out of the pair term (multiplying its sums by it afterwards); the
 // correction repeats exactly that and scales by the cluster's mass.
 template <bool UM>
 __global__ void __launch_bounds__(256) near_correct_kernel(DevState s, double G)
 {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= s.n) return;
-    const uint64_t kt = s.ng_key[t];
-    const float4 P = s.ng_pos[t];
-    const float4 Lo = s.ng_lo[t];
-    const int2 rr = s.ng_reg[t];   // the cluster's slot region, read with the key
-    const int32_t k = (int32_t)(kt >> (3 * CELL_BITS));
-    const int bits = __float_as_int(Lo.w);
+    const int64_t e0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e0 >= s.ng_start[SLOTS_PER_BODY * s.n]) return;   // bodies in the grid
+    const float4 P = s.ng_spos[e0];
+    const float4 Lo = s.ng_slo[e0];
+    const int t = __float_as_int(Lo.w);
+    const int32_t k = cluster_of(s.cl, t);
     double ax = 0.0, ay = 0.0, az = 0.0;
-    if (!(bits & NO_GRID)) {
-        const int cmask = (1 << CELL_BITS) - 1;
-        const int cx = (int)((kt >> (2 * CELL_BITS)) & cmask) - CELL_OFF;
-        const int cy = (int)((kt >> CELL_BITS) & cmask) - CELL_OFF;
-        const int cz = (int)(kt & cmask) - CELL_OFF;
-        const int sx = bits & 1 ? 1 : -1, sy = bits & 2 ? 1 : -1, sz = bits & 4 ? 1 : -1;
-        Region rg;
-        rg.base = rr.x;
-        rg.size = (uint32_t)rr.y;
+    {
+        const float ih = 1.0f / (CELL_SCALE * s.cl.frame[k].dth);
+        int sx, sy, sz;
+        const int cx = cell_coord(P.x, ih, sx), cy = cell_coord(P.y, ih, sy),
+                  cz = cell_coord(P.z, ih, sz);
+        const Region rg = region_of(s.cl, k);
         uint64_t key[8];
         int64_t slot[8];
         NgSlot v[8];
@@ -293,7 +292,7 @@ __global__ void __launch_bounds__(256) near_correct_kernel(DevState s, double G)
             for (int e = c.start; e < c.end; ++e) {
                 const float4 Pj = s.ng_spos[e];
                 const float4 Lj = s.ng_slo[e];
-                if (__float_as_int(Lj.w) == (int)t) continue;
+                if (__float_as_int(Lj.w) == t) continue;
                 // the pair kernel's float contribution, operation for operation
                 const float mj = Pj.w;
                 const float ddx = __fadd_rn(Pj.x, -xi);
@@ -348,7 +347,7 @@ cudaError_t launch_near_correct(const DevState &s, double G, bool um, cudaStream
     near_cell_kernel<<<nbn, 256, 0, st>>>(s);
     scan_block_kernel<<<nscan, SCAN_T, 0, st>>>(s.ng_count, s.ng_start, s.ng_bsum, H);
     scan_top_kernel<<<1, TOP_T, 0, st>>>(s.ng_bsum, nscan);
-    scan_add_kernel<<<nbh, 256, 0, st>>>(s.ng_start, s.ng_bsum, H, s.n);
+    scan_add_kernel<<<nbh, 256, 0, st>>>(s.ng_start, s.ng_bsum, s.ng_count, H);
     near_scatter_kernel<<<nbn, 256, 0, st>>>(s);
     near_rank_kernel<<<nbn, 256, 0, st>>>(s);
     if (um)

@@ -40,11 +40,9 @@ constexpr int64_t OFF_F = OFF_D + align256(4 * NA_MAX_N * 8);               // 7
 constexpr int64_t OFF_J = OFF_F + align256(7 * NA_MAX_N * 4);               // jd, jl
 constexpr int64_t OFF_P = OFF_J + align256(4 * NA_MAX_N * 16);              // partial slots
 constexpr int64_t OFF_C = OFF_P + align256(NA_SLOTS * 3 * NA_MAX_N * 8);    // near-pair correction
-constexpr int64_t OFF_K = OFF_C + align256(3 * NA_MAX_N * 8);               // cell keys
-constexpr int64_t OFF_I = OFF_K + align256(NA_MAX_N * 8);                   // bucket, rank, entry
-constexpr int64_t OFF_V = OFF_I + align256(3 * NA_MAX_N * 4);               // slot regions
-constexpr int64_t OFF_Q = OFF_V + align256(NA_MAX_N * 8);                   // pos lo spos slo
-constexpr int64_t OFF_S = OFF_Q + align256(4 * NA_MAX_N * 16);              // cell table
+constexpr int64_t OFF_I = OFF_C + align256(3 * NA_MAX_N * 8);               // bucket, rank, entry
+constexpr int64_t OFF_Q = OFF_I + align256(3 * NA_MAX_N * 4);               // spos slo
+constexpr int64_t OFF_S = OFF_Q + align256(2 * NA_MAX_N * 16);              // cell table
 constexpr int64_t OFF_H = OFF_S + align256(NA_H * (int64_t)sizeof(NgSlot));  // count, start, bsum
 constexpr int64_t OFF_T = OFF_H + align256((2 * NA_H + 1 + NA_H / 1024 + 1) * 4);  // tables
 // tables of the single cluster: boff nk noff[2] uoff[2] eps2d dts (int64/double),
@@ -170,15 +168,11 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
         s.part = reinterpret_cast<double *>(b + OFF_P);
         s.part_slots = NA_SLOTS;
         s.corr = reinterpret_cast<double *>(b + OFF_C);
-        s.ng_key = reinterpret_cast<uint64_t *>(b + OFF_K);
         s.ng_bucket = reinterpret_cast<int *>(b + OFF_I);
         s.ng_rank = s.ng_bucket + N;
         s.ng_entry = s.ng_bucket + 2 * N;
-        s.ng_reg = reinterpret_cast<int2 *>(b + OFF_V);
-        s.ng_pos = reinterpret_cast<float4 *>(b + OFF_Q);
-        s.ng_lo = s.ng_pos + N;
-        s.ng_spos = s.ng_pos + 2 * N;
-        s.ng_slo = s.ng_pos + 3 * N;
+        s.ng_spos = reinterpret_cast<float4 *>(b + OFF_Q);
+        s.ng_slo = s.ng_spos + N;
         s.ng_slot = reinterpret_cast<NgSlot *>(b + OFF_S);
         s.ng_count = reinterpret_cast<int *>(b + OFF_H);
         s.ng_start = s.ng_count + NA_H;

@@ -67,6 +67,29 @@ def test_batch_accel_matches_oracle_and_alone(nbs, orc, prec):
         off += n
 
 
+def test_batch_near_pass_with_single_body_clusters(nbs, orc):
+    """Single-body clusters have no near radius and stay out of the cell grid,
+    so fewer than N bodies are in it; in a set large enough for the near-pair
+    pass (sum of N_k^2 above 2^27) every other cluster must still match the
+    oracle to the mixed tolerance and the single bodies feel no force."""
+    sizes = [1, 12000, 1, 3000]
+    cl = clusters(sizes, base_seed=300)
+    pos, vel, m = concat(cl)
+    with nbs.Context(sizes=sizes, precision="ds") as b:
+        b.set_cluster_params(eps=[c[3] for c in cl])
+        b.load(pos, vel, m)
+        a = b.accel()
+    off = 0
+    for (p, v, mm, e), n in zip(cl, sizes):
+        got = a[off:off + n]
+        if n == 1:
+            assert np.all(got == 0)
+        else:
+            err = rel_rms(got, orc.accel_int(p, mm, 1.0, e))
+            assert err <= 1e-6, (n, err)
+        off += n
+
+
 @pytest.mark.parametrize("prec", ["fp64", "ds"])
 def test_batch_steps_equal_alone_runs(nbs, orc, prec):
     """Four SI6A steps of the whole ensemble with per-cluster softening and
