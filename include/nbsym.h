@@ -264,7 +264,7 @@ int nb_measure_peaks(int device, nb_peaks_t *out);
  * before reading d_acc_out.  No non-finite check is made.
  *
  * Limit: 1 <= n <= 16384.  All working memory sits in one static device
- * array of about 7.9 MB that every GPU loading the library keeps until the
+ * array of about 7.3 MB that every GPU loading the library keeps until the
  * process exits.  The first call on a device looks up that array's address
  * (cudaGetSymbolAddress) and must come before any stream capture.  Calls
  * share the array: calls whose work overlaps on the GPU race, so serialise

@@ -121,9 +121,7 @@ int set_create(ClusterSet &C, int32_t kcap, int64_t body_cap)
     A((void **)&C.ng_bucket, (size_t)body_cap * 4);
     A((void **)&C.ng_entry, (size_t)body_cap * 4);
     A((void **)&C.ng_rank, (size_t)body_cap * 4);
-    A((void **)&C.ng_count, (size_t)C.ng_hcap * 4);
-    A((void **)&C.ng_start, (size_t)(C.ng_hcap + 1) * 4);
-    A((void **)&C.ng_bsum, (size_t)(C.ng_hcap / 1024 + 1) * 4);
+    A((void **)&C.ng_total, sizeof(int));
     A((void **)&C.flag, sizeof(int));
     A((void **)&C.cid, (size_t)body_cap * 4);
     A((void **)&C.ng_spos, (size_t)body_cap * 16);
@@ -140,9 +138,8 @@ int set_create(ClusterSet &C, int32_t kcap, int64_t body_cap)
 
 void set_destroy(ClusterSet &C)
 {
-    void *ptrs[] = {C.dmem,     C.red,      C.ng_bucket, C.ng_entry, C.ng_count,
-                    C.ng_start, C.ng_bsum,  C.flag,      C.cid,      C.ng_spos,
-                    C.ng_slo,   C.ng_slot,  C.ng_rank};
+    void *ptrs[] = {C.dmem,    C.red,   C.ng_bucket, C.ng_entry, C.ng_total, C.flag,
+                    C.cid,     C.ng_spos, C.ng_slo,  C.ng_slot,  C.ng_rank};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     C = ClusterSet();
@@ -392,9 +389,7 @@ DevState view(const Pool &P, const ClusterSet &C, int precision)
     s.red_len = C.scap * 16;
     s.ng_bucket = C.ng_bucket;
     s.ng_entry = C.ng_entry;
-    s.ng_count = C.ng_count;
-    s.ng_start = C.ng_start;
-    s.ng_bsum = C.ng_bsum;
+    s.ng_total = C.ng_total;
     s.ng_hcap = C.ng_hcap;
     s.ng_spos = C.ng_spos;
     s.ng_slo = C.ng_slo;
@@ -412,7 +407,7 @@ void count(int64_t *k, int64_t v)
 {
     if (k) *k += v;
 }
-constexpr int64_t NEAR_KERNELS = 7;   // launch_near_correct (memsets not counted)
+constexpr int64_t NEAR_KERNELS = 5;   // launch_near_correct (memsets not counted)
 }  // namespace
 
 int enq_split(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph,

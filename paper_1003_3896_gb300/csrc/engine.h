@@ -53,8 +53,8 @@ struct ClusterSet {
     // per-set scratch, so sets in one pool can run concurrently on different
     // streams: near-pair hash grid over the set's linear bodies and the flag
     int64_t body_cap = 0, ng_hcap = 0;
-    int *ng_bucket = nullptr, *ng_rank = nullptr, *ng_entry = nullptr, *ng_count = nullptr,
-        *ng_start = nullptr, *ng_bsum = nullptr, *flag = nullptr;
+    int *ng_bucket = nullptr, *ng_rank = nullptr, *ng_entry = nullptr, *ng_total = nullptr,
+        *flag = nullptr;
     int32_t *cid = nullptr;    // linear body -> cluster map
     float4 *ng_spos = nullptr, *ng_slo = nullptr;
     NgSlot *ng_slot = nullptr;

@@ -102,8 +102,7 @@ struct DevState {
     // cell-ordered copies (hi x, y, z, m) and (lo x, y, z, linear index)
     float4 *ng_spos = nullptr, *ng_slo = nullptr;
     NgSlot *ng_slot = nullptr;                       // cell table [H]
-    int *ng_count = nullptr, *ng_start = nullptr;    // per slot (start: H + 1)
-    int *ng_bsum = nullptr;                          // scan block totals
+    int *ng_total = nullptr;                         // bodies placed in the grid
     int64_t ng_hcap = 0;                             // slots allocated
     double *red = nullptr;      // reduction partials [segment][16]
     int64_t red_len = 0;

@@ -27,10 +27,15 @@
 // locality for ensembles of small clusters), and probing wraps inside it.  Near pairs are rare (a few tenths per body in a Plummer
 // sphere), so the pass is dominated by these probes.
 //
+// Pass: clear the table (one memset), insert cells and count arrivals, let
+// each cell's first arrival claim its range of the cell-ordered copies (one
+// atomic add on a running total), scatter, order each cell by body index and
+// write the copies, correct.
+//
 // Deterministic: within a cell the bodies are ordered by linear index, and
 // every body visits its 8 cells in a fixed order, so the FP64 correction sums
-// do not depend on timing (which slot a cell lands in may vary; the sums do
-// not depend on it).
+// do not depend on timing (which slot a cell lands in, and where its range
+// lands, may vary; the sums do not depend on either).
 #include "nb_internal.cuh"
 
 namespace nb {
@@ -101,6 +106,7 @@ __global__ void near_cell_kernel(DevState s)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= s.n) return;
+    if (t == 0) *s.ng_total = 0;   // read only by the claim pass, which follows
     const int32_t k = cluster_of(s.cl, t);
     const int64_t i = s.cl.boff[k] + t - s.cl.noff[k];
     const float dth = s.cl.frame[k].dth;
@@ -123,85 +129,55 @@ __global__ void near_cell_kernel(DevState s)
         b = next_slot(b, rg);
     }
     s.ng_bucket[t] = (int)b;
-    s.ng_rank[t] = atomicAdd(&s.ng_count[b], 1);
+    // the slot's end counts arrivals from -1 (the empty record) until the
+    // claim pass turns it into the range end
+    s.ng_rank[t] = atomicAdd(&s.ng_slot[b].end, 1) + 1;
 }
 
-// Exclusive scan of ng_count[0, H) into ng_start: per-block scan of 1024
-// entries, then a single block scans the block totals, then a fix-up pass.
-constexpr int SCAN_T = 256, SCAN_E = 4, SCAN_B = SCAN_T * SCAN_E;
+// After all insertions: the first arrival of each cell claims the cell's
+// range of the cell-ordered copies.  A block sums its claims (warp-shuffle
+// scan, then across the warps) and takes one range of the running total with
+// a single atomic add; a claim per atomic on one address would serialise.
+// Ranges land in the order the blocks claim them; only their contents,
+// ordered by body index, enter the sums.  The slot keeps [start, end).
+constexpr int CLAIM_T = 256;
 
-__global__ void scan_block_kernel(const int *__restrict__ in, int *__restrict__ out,
-                                  int *__restrict__ bsum, int64_t H)
+__global__ void __launch_bounds__(CLAIM_T) near_claim_kernel(DevState s)
 {
-    __shared__ int sh[SCAN_T];
-    const int64_t base = blockIdx.x * (int64_t)SCAN_B + threadIdx.x * SCAN_E;
-    int v[SCAN_E], run = 0;
-#pragma unroll
-    for (int k = 0; k < SCAN_E; ++k) {
-        v[k] = base + k < H ? in[base + k] : 0;
-        run += v[k];
+    __shared__ int wsum[CLAIM_T / 32];
+    __shared__ int base;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int b = -1, cnt = 0;
+    if (t < s.n) {
+        b = s.ng_bucket[t];
+        if (b >= 0 && s.ng_rank[t] == 0)
+            cnt = s.ng_slot[b].end + 1;   // arrivals counted from -1
+        else
+            b = -1;
     }
-    sh[threadIdx.x] = run;
-    __syncthreads();
-    for (int w = 1; w < SCAN_T; w <<= 1) {
-        const int t = threadIdx.x >= w ? sh[threadIdx.x - w] : 0;
-        __syncthreads();
-        sh[threadIdx.x] += t;
-        __syncthreads();
-    }
-    int acc = sh[threadIdx.x] - run;
-#pragma unroll
-    for (int k = 0; k < SCAN_E; ++k) {
-        if (base + k < H) out[base + k] = acc;
-        acc += v[k];
-    }
-    if (threadIdx.x == SCAN_T - 1) bsum[blockIdx.x] = sh[SCAN_T - 1];
-}
-
-// Exclusive scan of the nb block totals in one pass of one block: each of
-// TOP_T threads sums its own run of ceil(nb / TOP_T) totals, the runs' sums
-// are scanned with warp shuffles, and each thread writes its run's prefixes.
-constexpr int TOP_T = 1024;
-
-__global__ void __launch_bounds__(TOP_T) scan_top_kernel(int *bsum, int nb)
-{
-    __shared__ int wsum[TOP_T / 32];
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const int per = (nb + TOP_T - 1) / TOP_T;
-    const int lo = t * per, hi = lo + per < nb ? lo + per : nb;
-    int local = 0;
-    for (int i = lo; i < hi; ++i) local += bsum[i];
-    int x = local;   // inclusive scan over the warp
+    int x = cnt;   // inclusive scan over the warp
     for (int d = 1; d < 32; d <<= 1) {
         const int y = __shfl_up_sync(0xffffffffu, x, d);
         if (lane >= d) x += y;
     }
     if (lane == 31) wsum[w] = x;
     __syncthreads();
-    if (w == 0) {
-        int v = wsum[lane];
-        for (int d = 1; d < 32; d <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, v, d);
-            if (lane >= d) v += y;
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int q = 0; q < CLAIM_T / 32; ++q) {
+            const int v = wsum[q];
+            wsum[q] = run;
+            run += v;
         }
-        wsum[lane] = v;
+        base = run > 0 ? atomicAdd(s.ng_total, run) : 0;
     }
     __syncthreads();
-    int run = x - local + (w > 0 ? wsum[w - 1] : 0);
-    for (int i = lo; i < hi; ++i) {
-        const int v = bsum[i];
-        bsum[i] = run;
-        run += v;
+    if (b >= 0) {
+        const int st = base + wsum[w] + x - cnt;
+        s.ng_slot[b].start = st;
+        s.ng_slot[b].end = st + cnt;
     }
-}
-
-// Adds the block offsets; out[H] = the number of bodies in the grid (fewer
-// than n when a cluster has no near radius, e.g. a single body).
-__global__ void scan_add_kernel(int *out, const int *bsum, const int *count, int64_t H)
-{
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < H) out[i] += bsum[i / SCAN_B];
-    if (i == H - 1) out[H] = out[i] + count[i];
 }
 
 // Bodies into their cell's range, in arrival order.
@@ -211,7 +187,7 @@ __global__ void near_scatter_kernel(DevState s)
     if (t >= s.n) return;
     const int b = s.ng_bucket[t];
     if (b < 0) return;
-    s.ng_entry[s.ng_start[b] + s.ng_rank[t]] = (int)t;
+    s.ng_entry[s.ng_slot[b].start + s.ng_rank[t]] = (int)t;
 }
 
 // Final place of each body in its cell = number of cell members with a
@@ -231,15 +207,11 @@ __global__ void near_rank_kernel(DevState s)
         s.corr[2 * s.cap + i] = 0.0;
         return;
     }
-    const int lo = s.ng_start[b], hi = s.ng_start[b + 1];
+    const int lo = s.ng_slot[b].start, hi = s.ng_slot[b].end;
     int r = 0;
     for (int e = lo; e < hi; ++e) r += s.ng_entry[e] < (int)t ? 1 : 0;
     s.ng_spos[lo + r] = make_float4(s.xh[i], s.yh[i], s.zh[i], s.mf[i]);
     s.ng_slo[lo + r] = make_float4(s.xl[i], s.yl[i], s.zl[i], __int_as_float((int)t));
-    if (r == 0) {
-        s.ng_slot[b].start = lo;
-        s.ng_slot[b].end = hi;
-    }
 }
 
 // One thread per body in cell order (entry e of the cell-ordered copies), so
@@ -254,7 +226,7 @@ template <bool UM>
 __global__ void __launch_bounds__(256) near_correct_kernel(DevState s, double G)
 {
     const int64_t e0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e0 >= s.ng_start[SLOTS_PER_BODY * s.n]) return;   // bodies in the grid
+    if (e0 >= *s.ng_total) return;   // bodies in the grid
     const float4 P = s.ng_spos[e0];
     const float4 Lo = s.ng_slo[e0];
     const int t = __float_as_int(Lo.w);
@@ -338,16 +310,11 @@ cudaError_t launch_near_correct(const DevState &s, double G, bool um, cudaStream
     const int64_t H = near_table_size(s.n);
     if (H > s.ng_hcap) return cudaErrorInvalidValue;
     const unsigned nbn = (unsigned)((s.n + 255) / 256);
-    const unsigned nbh = (unsigned)((H + 255) / 256);
-    const int nscan = (int)((H + SCAN_B - 1) / SCAN_B);
+    // empty records: key all ones, start = end = -1
     cudaError_t e = cudaMemsetAsync(s.ng_slot, 0xff, (size_t)H * sizeof(NgSlot), st);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(s.ng_count, 0, (size_t)H * sizeof(int), st);
-    if (e != cudaSuccess) return e;
     near_cell_kernel<<<nbn, 256, 0, st>>>(s);
-    scan_block_kernel<<<nscan, SCAN_T, 0, st>>>(s.ng_count, s.ng_start, s.ng_bsum, H);
-    scan_top_kernel<<<1, TOP_T, 0, st>>>(s.ng_bsum, nscan);
-    scan_add_kernel<<<nbh, 256, 0, st>>>(s.ng_start, s.ng_bsum, s.ng_count, H);
+    near_claim_kernel<<<nbn, CLAIM_T, 0, st>>>(s);
     near_scatter_kernel<<<nbn, 256, 0, st>>>(s);
     near_rank_kernel<<<nbn, 256, 0, st>>>(s);
     if (um)

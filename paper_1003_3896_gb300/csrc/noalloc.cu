@@ -43,8 +43,8 @@ constexpr int64_t OFF_C = OFF_P + align256(NA_SLOTS * 3 * NA_MAX_N * 8);    // n
 constexpr int64_t OFF_I = OFF_C + align256(3 * NA_MAX_N * 8);               // bucket, rank, entry
 constexpr int64_t OFF_Q = OFF_I + align256(3 * NA_MAX_N * 4);               // spos slo
 constexpr int64_t OFF_S = OFF_Q + align256(2 * NA_MAX_N * 16);              // cell table
-constexpr int64_t OFF_H = OFF_S + align256(NA_H * (int64_t)sizeof(NgSlot));  // count, start, bsum
-constexpr int64_t OFF_T = OFF_H + align256((2 * NA_H + 1 + NA_H / 1024 + 1) * 4);  // tables
+constexpr int64_t OFF_H = OFF_S + align256(NA_H * (int64_t)sizeof(NgSlot));  // grid total
+constexpr int64_t OFF_T = OFF_H + align256(4);                               // tables
 // tables of the single cluster: boff nk noff[2] uoff[2] eps2d dts (int64/double),
 // seg_lo[S] seg_hi[S], then ntiles eps2f seg_k[S] seg_off[2] flag (32-bit)
 constexpr int64_t T64 = 8 + 2 * NA_SEGS;
@@ -174,9 +174,7 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
         s.ng_spos = reinterpret_cast<float4 *>(b + OFF_Q);
         s.ng_slo = s.ng_spos + N;
         s.ng_slot = reinterpret_cast<NgSlot *>(b + OFF_S);
-        s.ng_count = reinterpret_cast<int *>(b + OFF_H);
-        s.ng_start = s.ng_count + NA_H;
-        s.ng_bsum = s.ng_start + NA_H + 1;
+        s.ng_total = reinterpret_cast<int *>(b + OFF_H);
         s.ng_hcap = NA_H;
         TablePtrs t;
         int64_t *t64 = reinterpret_cast<int64_t *>(b + OFF_T);
