@@ -10,14 +10,14 @@
 //
 // Single-precision family (one template, three modes):
 //   PM_DS_NEAR  float pair arithmetic on coordinates relative to the cluster's
-//               frame origin, float partial sums over 256 j folded into double-single
+//               frame origin, float partial sums over 512 j folded into double-single
 //               accumulators (Sect. 5.2's software double precision); pairs
 //               closer than the near radius are re-formed from the
 //               double-single coordinate difference (hi_j - hi_i) +
 //               (lo_j - lo_i) by the separate correction pass of near.cu.
 //   PM_DS_FULL  the double-single coordinate difference on every pair.
 //   PM_FP32     float coordinates and float accumulation throughout (the
-//               256-j partial sums added in float).
+//               512-j partial sums added in float).
 //
 // Data movement: no block-wide barrier.  Each warp streams its j bodies in
 // chunks of 32 through a warp-private shared-memory buffer: lane l loads body
@@ -156,7 +156,7 @@ __device__ __forceinline__ Segment segment_at(const Decomp &d, const Clusters &c
 
 constexpr int CH = 32;            // j bodies per warp chunk
 constexpr int WARPS = TILE / 32;  // warps per block
-constexpr int FOLD = 2 * TILE;    // j bodies per float partial sum before the fold
+constexpr int FOLD = 4 * TILE;    // j bodies per float partial sum before the fold
 
 // Thread-private i bodies, two per packed register pair: pair p holds bodies
 // k = 2p (.x) and k = 2p + 1 (.y), local body k = ib0 + tid + k * TILE.
