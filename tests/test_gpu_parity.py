@@ -251,6 +251,31 @@ def test_many_slot_reduction_is_deterministic(nbs, orc):
         assert err <= TOL[prec], (prec, err)
 
 
+def test_cuda_path_matches_golden_fixture(nbs):
+    """Accelerations, energy and 4-step states of the seeded 16-body cluster
+    at R = 50 in the field against the oracle's values stored in
+    tests/golden/oracle_plummer16_orbit.txt (no oracle build needed)."""
+    from golden.fixture import load
+    g = load("oracle_plummer16_orbit.txt")
+    G, eps, Md, ad, bd, Mb, ab, dt, steps = g["params"][0]
+    m, pos, vel = g["mass"][0], g["pos"], g["vel"]
+    pos_tol = {"fp64": 1e-10, "dd": 1e-10, "ds": 1e-6}
+    for prec in ("fp64", "dd", "ds"):
+        with nbs.Context(pos.shape[0], eps=eps, precision=prec, ext_on=True, G=G) as c:
+            c.load(pos, vel, m)
+            a = c.accel()
+            e = c.energy()
+        assert rel_rms(a, g["acc"]) <= TOL[prec], (prec, rel_rms(a, g["acc"]))
+        assert abs(e.E - g["energy"][0][3]) <= 1e-12 * abs(g["energy"][0][3]), prec
+        for order in (6, 2):
+            with nbs.Context(pos.shape[0], eps=eps, precision=prec, ext_on=True, G=G) as c:
+                c.load(pos, vel, m)
+                c.step(order, dt, int(steps))
+                x, v = c.get_state()
+            err = float(np.abs(x - g[f"pos_order{order}"]).max())
+            assert err <= pos_tol[prec], (prec, order, err)
+
+
 def test_state_errors(nbs):
     with nbs.Context(10, eps=0.01) as c:
         with pytest.raises(nbs.NBError) as e:

@@ -580,3 +580,46 @@ def test_external_field_against_high_precision(orc):
                          float(-(kd * (D(p.ad) + s) / s + kb + kh) * Z)])
         got = orc.ext_accel(p, np.array(x))[0]
         assert np.linalg.norm(got - want) <= 1e-15 * np.linalg.norm(want) * 4
+
+
+# ------------------------------------------------------------ golden fixtures
+
+def _golden(name):
+    from golden.fixture import load
+    return load(name)
+
+
+def test_oracle_reproduces_its_fixture(orc):
+    """The oracle against the fixture tests/golden/make_golden.py wrote from it
+    (a seeded 16-body cluster at R = 50 in the field): a change to the
+    oracle's arithmetic shows here and must come with its reason."""
+    g = _golden("oracle_plummer16_orbit.txt")
+    G, eps, Md, ad, bd, Mb, ab, dt, steps = g["params"][0]
+    p = orc.Params(G=G, eps=eps, ext_on=True, Md=Md, ad=ad, bd=bd, Mb=Mb, ab=ab)
+    m, pos, vel = g["mass"][0], g["pos"], g["vel"]
+    a = orc.accel(pos, m, p)
+    np.testing.assert_allclose(a, g["acc"], rtol=1e-13, atol=1e-15 * np.abs(g["acc"]).max())
+    e = orc.energy(pos, vel, m, p)
+    np.testing.assert_allclose([e.K, e.W, e.W_ext, e.E, *e.P, *e.L], g["energy"][0],
+                               rtol=1e-13, atol=1e-16)
+    for order in (6, 2):
+        x, v = orc.run(pos, vel, m, p, order, dt, int(steps))
+        np.testing.assert_allclose(x, g[f"pos_order{order}"], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(v, g[f"vel_order{order}"], rtol=0, atol=1e-12)
+
+
+def test_paper_context_matches_the_printed_tables():
+    """The paper's figures quoted in the benchmark lines (context) equal the
+    transcription of its Tables 3 and 8 in tests/golden/paper_tables.txt."""
+    import bench
+    import bench_workloads
+    t = _golden("paper_tables.txt")
+    n = [int(v) for v in t["table3_n"][0]]
+    assert bench.PAPER_CONTEXT["n"] == n
+    for key in ("sp_gflops_1gpu", "dp_gflops_1gpu", "sp_gflops_2gpu", "dp_gflops_2gpu"):
+        row = "table3_" + key.replace("_gflops", "")
+        assert bench.PAPER_CONTEXT[key] == list(t[row][0]), key
+    assert [bench_workloads.PAPER_TABLE3_SP[k] for k in n] == list(t["table3_sp_1gpu"][0])
+    assert [bench_workloads.PAPER_TABLE3_DP[k] for k in n] == list(t["table3_dp_1gpu"][0])
+    for q, de, dl in t["table8"]:
+        assert bench_workloads.PAPER_TABLE8[q] == (de, dl), q
