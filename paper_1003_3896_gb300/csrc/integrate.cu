@@ -16,9 +16,20 @@
 namespace nb {
 
 constexpr int RT = 256;   // threads per reduction block
-constexpr int OT = 256;   // threads per block of the per-body kernels
+constexpr int OT = 256;   // threads per block of the per-body kernels, at most
 
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// Threads per block of a per-body kernel over n bodies: OT, or fewer (a
+// multiple of 32) when n is small, so the blocks spread over at least ~300
+// SMs' worth of slots; these kernels carry FP64 arithmetic and dependent
+// loads, and a small system on a few SMs waits on one SM's FP64 pipe.
+static inline int ot_for(int64_t n)
+{
+    int t = 32;
+    while (t < OT && (int64_t)t * 304 < n) t *= 2;
+    return t;
+}
 
 struct BodyRef {
     int32_t k;     // cluster
@@ -142,20 +153,20 @@ __global__ void cluster_map_kernel(Clusters c, int32_t *cid, int64_t n)
 cudaError_t launch_cluster_map(const Clusters &c, int32_t *cid, int64_t n, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    cluster_map_kernel<<<blocks_for(n, OT), OT, 0, st>>>(c, cid, n);
+    cluster_map_kernel<<<blocks_for(n, ot_for(n)), ot_for(n), 0, st>>>(c, cid, n);
     return cudaGetLastError();
 }
 
 cudaError_t launch_unpack(const DevState &s, const double *pos, const double *vel,
                           const double *mass, cudaStream_t st)
 {
-    unpack_kernel<<<blocks_for(s.n, OT), OT, 0, st>>>(s, pos, vel, mass);
+    unpack_kernel<<<blocks_for(s.n, ot_for(s.n)), ot_for(s.n), 0, st>>>(s, pos, vel, mass);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pack(const DevState &s, double *pos, double *vel, cudaStream_t st)
 {
-    pack_kernel<<<blocks_for(s.n, OT), OT, 0, st>>>(s, pos, vel);
+    pack_kernel<<<blocks_for(s.n, ot_for(s.n)), ot_for(s.n), 0, st>>>(s, pos, vel);
     return cudaGetLastError();
 }
 
@@ -191,10 +202,11 @@ __global__ void frame_final_kernel(DevState s, double near_frac)
         const int k = blockIdx.x;
         Frame f;
         const double M = v[0];
-        f.cx = M > 0 ? v[1] / M : 0.0;
-        f.cy = M > 0 ? v[2] / M : 0.0;
-        f.cz = M > 0 ? v[3] / M : 0.0;
-        const double r2 = M > 0 ? v[4] / M - (f.cx * f.cx + f.cy * f.cy + f.cz * f.cz) : 0.0;
+        const double iM = M > 0 ? 1.0 / M : 0.0;   // one division, four products
+        f.cx = v[1] * iM;
+        f.cy = v[2] * iM;
+        f.cz = v[3] * iM;
+        const double r2 = M > 0 ? v[4] * iM - (f.cx * f.cx + f.cy * f.cy + f.cz * f.cz) : 0.0;
         f.r2rms = r2 > 0 ? r2 : 0.0;
         // no near-pair radius yet (set by frame_scale_kernel when the plan
         // runs the near-pair pass)
@@ -358,7 +370,7 @@ __global__ void split_kernel(DevState s)
 
 cudaError_t launch_split(const DevState &s, cudaStream_t st)
 {
-    split_kernel<<<blocks_for(s.n, OT), OT, 0, st>>>(s);
+    split_kernel<<<blocks_for(s.n, ot_for(s.n)), ot_for(s.n), 0, st>>>(s);
     return cudaGetLastError();
 }
 
@@ -444,7 +456,8 @@ __global__ void kick_drift_kernel(DevState s, Decomp d, double wk, double wd, in
 cudaError_t launch_kick_drift(const DevState &s, const Decomp &d, double wk, double wd,
                               int do_kick, int do_split, const ExtField &ext, cudaStream_t st)
 {
-    kick_drift_kernel<<<blocks_for(s.n, OT), OT, 0, st>>>(s, d, wk, wd, do_kick, do_split, ext);
+    const int t = ot_for(s.n);
+    kick_drift_kernel<<<blocks_for(s.n, t), t, 0, st>>>(s, d, wk, wd, do_kick, do_split, ext);
     return cudaGetLastError();
 }
 
@@ -479,7 +492,8 @@ cudaError_t launch_accel_out(const DevState &s, const Decomp &d, const ExtField 
 cudaError_t launch_accel_out_range(const DevState &s, const Decomp &d, const ExtField &ext,
                                    double *out_aos, int64_t t0, int64_t t1, cudaStream_t st)
 {
-    accel_out_kernel<<<blocks_for(t1 - t0, OT), OT, 0, st>>>(s, d, ext, out_aos, t0, t1);
+    const int t = ot_for(t1 - t0);
+    accel_out_kernel<<<blocks_for(t1 - t0, t), t, 0, st>>>(s, d, ext, out_aos, t0, t1);
     return cudaGetLastError();
 }
 

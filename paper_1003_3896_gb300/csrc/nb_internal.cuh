@@ -262,7 +262,7 @@ cudaError_t launch_energy_reduce(const DevState &s, const Decomp &d, const ExtFi
                                  double G, cudaStream_t st);
 cudaError_t launch_torque(const DevState &s, const ExtField &ext, cudaStream_t st);
 
-constexpr int SEG_BODIES = 2048;   // bodies per reduction segment
+constexpr int SEG_BODIES = 512;    // bodies per reduction segment (one block each)
 constexpr int DIAG_STRIDE = 16;    // doubles per cluster in diag
 
 }  // namespace nb
