@@ -222,16 +222,24 @@ __global__ void near_rank_kernel(DevState s)
 // correction from near_rank_kernel.  UM: the pair kernel left the common
 // mass out of the pair term (multiplying its sums by it afterwards); the
 // correction repeats exactly that and scales by the cluster's mass.
+constexpr int NC_T = 256;   // threads per block of the correction
+
 template <bool UM>
-__global__ void __launch_bounds__(256) near_correct_kernel(DevState s, double G)
+__global__ void __launch_bounds__(NC_T) near_correct_kernel(DevState s, double G)
 {
-    const int64_t e0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    // per thread: the ranges of its 8 probed cells (empty: start = end), so
+    // that one flat loop walks all its candidates; a loop per cell would
+    // run as long as the warp's longest member list for every cell
+    __shared__ int2 rng[8][NC_T];
+    const int tid = threadIdx.x;
+    const int64_t e0 = blockIdx.x * (int64_t)blockDim.x + tid;
     if (e0 >= *s.ng_total) return;   // bodies in the grid
     const float4 P = s.ng_spos[e0];
     const float4 Lo = s.ng_slo[e0];
     const int t = __float_as_int(Lo.w);
     const int32_t k = cluster_of(s.cl, t);
     double ax = 0.0, ay = 0.0, az = 0.0;
+    int total = 0;
     {
         const float ih = 1.0f / (CELL_SCALE * s.cl.frame[k].dth);
         int sx, sy, sz;
@@ -248,10 +256,6 @@ __global__ void __launch_bounds__(256) near_correct_kernel(DevState s, double G)
             slot[q] = slot_of(key[q], rg);
             v[q] = s.ng_slot[slot[q]];
         }
-        const float eps2 = s.cl.eps2f[k];
-        const float th2 = s.cl.frame[k].th2;
-        const float xi = P.x, yi = P.y, zi = P.z;
-        const float lxi = Lo.x, lyi = Lo.y, lzi = Lo.z;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             NgSlot c = v[q];
@@ -260,38 +264,51 @@ __global__ void __launch_bounds__(256) near_correct_kernel(DevState s, double G)
                 b = next_slot(b, rg);
                 c = s.ng_slot[b];
             }
-            if (c.key != key[q]) continue;   // empty cell
-            for (int e = c.start; e < c.end; ++e) {
-                const float4 Pj = s.ng_spos[e];
-                const float4 Lj = s.ng_slo[e];
-                if (__float_as_int(Lj.w) == t) continue;
-                // the pair kernel's float contribution, operation for operation
-                const float mj = Pj.w;
-                const float ddx = __fadd_rn(Pj.x, -xi);
-                const float ddy = __fadd_rn(Pj.y, -yi);
-                const float ddz = __fadd_rn(Pj.z, -zi);
-                float r2 = __fmaf_rn(ddx, ddx, eps2);
-                r2 = __fmaf_rn(ddy, ddy, r2);
-                r2 = __fmaf_rn(ddz, ddz, r2);
-                if (!(r2 < th2)) continue;
-                const float ri = near_rsqrt(r2);
-                const float sf = UM ? __fmul_rn(ri, __fmul_rn(ri, ri))
-                                    : __fmul_rn(__fmul_rn(mj, ri), __fmul_rn(ri, ri));
-                // the same pair with the double-single coordinate difference
-                const float ex = __fadd_rn(ddx, __fsub_rn(Lj.x, lxi));
-                const float ey = __fadd_rn(ddy, __fsub_rn(Lj.y, lyi));
-                const float ez = __fadd_rn(ddz, __fsub_rn(Lj.z, lzi));
-                float e2 = __fmaf_rn(ex, ex, eps2);
-                e2 = __fmaf_rn(ey, ey, e2);
-                e2 = __fmaf_rn(ez, ez, e2);
-                const float re = near_rsqrt(e2);
-                const float se = UM ? __fmul_rn(re, __fmul_rn(re, re))
-                                    : __fmul_rn(__fmul_rn(mj, re), __fmul_rn(re, re));
-                ax += (double)__fmul_rn(ex, se) - (double)__fmul_rn(ddx, sf);
-                ay += (double)__fmul_rn(ey, se) - (double)__fmul_rn(ddy, sf);
-                az += (double)__fmul_rn(ez, se) - (double)__fmul_rn(ddz, sf);
-            }
+            const bool hit = c.key == key[q];
+            rng[q][tid] = hit ? make_int2(c.start, c.end) : make_int2(0, 0);
+            total += hit ? c.end - c.start : 0;
         }
+    }
+    const float eps2 = s.cl.eps2f[k];
+    const float th2 = s.cl.frame[k].th2;
+    const float xi = P.x, yi = P.y, zi = P.z;
+    const float lxi = Lo.x, lyi = Lo.y, lzi = Lo.z;
+    // candidates in cell order 0..7, each cell's members in body order
+    int q = 0;
+    int2 r = rng[0][tid];
+    int e = r.x;
+    for (int it = 0; it < total; ++it, ++e) {
+        while (e >= r.y) {
+            r = rng[++q][tid];
+            e = r.x;
+        }
+        const float4 Pj = s.ng_spos[e];
+        const float4 Lj = s.ng_slo[e];
+        // the pair kernel's float contribution, operation for operation
+        const float mj = Pj.w;
+        const float ddx = __fadd_rn(Pj.x, -xi);
+        const float ddy = __fadd_rn(Pj.y, -yi);
+        const float ddz = __fadd_rn(Pj.z, -zi);
+        float r2 = __fmaf_rn(ddx, ddx, eps2);
+        r2 = __fmaf_rn(ddy, ddy, r2);
+        r2 = __fmaf_rn(ddz, ddz, r2);
+        if (__float_as_int(Lj.w) == t || !(r2 < th2)) continue;
+        const float ri = near_rsqrt(r2);
+        const float sf = UM ? __fmul_rn(ri, __fmul_rn(ri, ri))
+                            : __fmul_rn(__fmul_rn(mj, ri), __fmul_rn(ri, ri));
+        // the same pair with the double-single coordinate difference
+        const float ex = __fadd_rn(ddx, __fsub_rn(Lj.x, lxi));
+        const float ey = __fadd_rn(ddy, __fsub_rn(Lj.y, lyi));
+        const float ez = __fadd_rn(ddz, __fsub_rn(Lj.z, lzi));
+        float e2 = __fmaf_rn(ex, ex, eps2);
+        e2 = __fmaf_rn(ey, ey, e2);
+        e2 = __fmaf_rn(ez, ez, e2);
+        const float re = near_rsqrt(e2);
+        const float se = UM ? __fmul_rn(re, __fmul_rn(re, re))
+                            : __fmul_rn(__fmul_rn(mj, re), __fmul_rn(re, re));
+        ax += (double)__fmul_rn(ex, se) - (double)__fmul_rn(ddx, sf);
+        ay += (double)__fmul_rn(ey, se) - (double)__fmul_rn(ddy, sf);
+        az += (double)__fmul_rn(ez, se) - (double)__fmul_rn(ddz, sf);
     }
     const int64_t i = s.cl.boff[k] + t - s.cl.noff[k];
     const double Gm = UM ? G * s.cl.mu[k] : G;
@@ -318,9 +335,9 @@ cudaError_t launch_near_correct(const DevState &s, double G, bool um, cudaStream
     near_scatter_kernel<<<nbn, 256, 0, st>>>(s);
     near_rank_kernel<<<nbn, 256, 0, st>>>(s);
     if (um)
-        near_correct_kernel<true><<<nbn, 256, 0, st>>>(s, G);
+        near_correct_kernel<true><<<(unsigned)((s.n + NC_T - 1) / NC_T), NC_T, 0, st>>>(s, G);
     else
-        near_correct_kernel<false><<<nbn, 256, 0, st>>>(s, G);
+        near_correct_kernel<false><<<(unsigned)((s.n + NC_T - 1) / NC_T), NC_T, 0, st>>>(s, G);
     return cudaGetLastError();
 }
 
