@@ -159,8 +159,8 @@ int nb_create(const nb_params *p, int64_t n_capacity, nb_ctx **out);
  * fixed sizes sizes[0..n_clusters-1] (each >= 1; 1 <= n_clusters <= 2^19,
  * sum <= 2^26).  Each cluster obeys eq. 3 on its own: bodies of different
  * clusters never interact.  Every force evaluation of the whole ensemble is
- * one persistent kernel launch whose blocks share the pair work of all
- * clusters evenly, and a step of every cluster is one CUDA graph.  nb_load
+ * one kernel launch whose blocks share the pair work of all clusters
+ * evenly, and a step of every cluster is one CUDA graph.  nb_load
  * then takes the clusters' bodies concatenated in cluster order (n = sum of
  * sizes); nb_accel / nb_get_state return them in that order; every cluster
  * starts with softening p->eps and step scale 1 (nb_set_cluster_params).
@@ -367,7 +367,7 @@ void nb_destroy(nb_ctx *ctx);
  * order when a resident-job slot is free and the state pool (sized from the
  * HBM budget) has a contiguous range for the job's bodies.  Resident jobs are
  * grouped by (precision, order); each group advances one step at a time with
- * one persistent launch per force evaluation covering all its jobs, on its
+ * one pair-kernel launch per force evaluation covering all its jobs, on its
  * own stream, so groups overlap on the device.  Jobs join and leave a group
  * between two of its steps (continuous batching).  Each job is an independent
  * system (eq. 3) with its own softening and step; the field parameters are

@@ -110,14 +110,15 @@ struct DevState {
     int *flag = nullptr;        // non-finite flag
 };
 
-// Persistent ("stream-K") decomposition of the pair work of a cluster set.
-// A unit is (cluster k, i-block b, j-range t of jt bodies); units are
-// numbered cluster by cluster, u = uoff[k] + b * units_per_iblock(ntiles[k])
-// + t, W units in all.  Persistent block g owns the contiguous units
-// [U(g), U(g+1)), U(g) = floor(g W / G); every unit is jt x TILE*I pairs, so
-// blocks get equal work whatever the cluster sizes.  Each (cluster, i-block, block g) segment writes its own partial
-// slot g - gfirst; consumers add an i-block's slots in slot order, so results
-// do not depend on timing.
+// Stream-K-style decomposition of the pair work of a cluster set.  A unit is
+// (cluster k, i-block b, j-range t of jt bodies); units are numbered cluster
+// by cluster, u = uoff[k] + b * units_per_iblock(ntiles[k]) + t, W units in
+// all.  Block g of the grid (resident at once, or run in waves when G exceeds
+// the resident blocks) owns the contiguous units [U(g), U(g+1)),
+// U(g) = floor(g W / G); every unit is jt x TILE*I pairs, so blocks get equal
+// work whatever the cluster sizes.  Each (cluster, i-block, block g) segment
+// writes its own partial slot g - gfirst; consumers add an i-block's slots in
+// slot order, so results do not depend on timing.
 struct Decomp {
     int32_t ipb = TILE;   // bodies per i-block = TILE * I
     // j bodies per unit: TILE or a divisor of it down to 32 (finer units give
@@ -129,7 +130,7 @@ struct Decomp {
     int32_t rows = 0;
     int64_t b0 = 0;
     int64_t W = 0;        // total units
-    int64_t G = 1;        // persistent blocks (grid size), 1 <= G <= W
+    int64_t G = 1;        // blocks (grid size), 1 <= G <= W
     int64_t slots = 1;    // max partial slots any i-block needs
     // 1 when some cluster has eps = 0: the j == i term is then masked in every
     // cluster (for eps > 0 it is exactly zero anyway), which keeps the

@@ -1,10 +1,10 @@
 // pair.cu -- all-pairs softened gravity (eq. 5; eq. 2 when eps = 0) on sm_103a.
 //
-// Every kernel here walks the same persistent decomposition (Decomp) of the
-// pair work of a set of independent clusters: a grid of G blocks, one
-// contiguous run of (cluster, i-block, j-tile) units per block, so every SM
-// gets the same amount of work whatever the cluster sizes are (one cluster,
-// or an ensemble of uneven clusters in one launch).  Each thread owns I
+// Every kernel here walks the same decomposition (Decomp) of the pair work of
+// a set of independent clusters: a grid of G blocks (one resident wave or
+// several), one contiguous run of (cluster, i-block, j-tile) units per block,
+// so every block gets the same amount of work whatever the cluster sizes are
+// (one cluster, or an ensemble of uneven clusters in one launch).  Each thread owns I
 // i-bodies and keeps their sums in registers; every pair of each cluster's
 // N x N array is evaluated, as in the paper (Sect. 4.2), not N(N-1)/2.
 //

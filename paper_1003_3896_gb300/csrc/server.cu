@@ -7,7 +7,7 @@
 // initial conditions are then uploaded into that range.  Resident jobs are
 // grouped by (precision, order); each group is one cluster set of the engine
 // (one cluster per job, with the job's softening and step length), advanced
-// one step at a time by one persistent launch per force evaluation on the
+// one step at a time by one pair-kernel launch per force evaluation on the
 // group's own stream, so the groups' work overlaps on the device.  Between two
 // steps of a group, finished jobs leave it (their state is copied back and
 // their pool range freed) and newly admitted jobs join it.  A job whose state

@@ -5,7 +5,7 @@
 // frame-centred coordinates).
 //
 // Work: tile pairs (I, J), I <= J, of 64 x 64 bodies over the upper triangle,
-// split into equal contiguous runs, one per persistent block.  A block of 128
+// split into equal contiguous runs, one per resident block.  A block of 128
 // threads is a 16 x 8 grid; thread (a, b) keeps bodies I*64 + 4a .. 4a + 3 and
 // J*64 + 8b .. 8b + 7 in registers and evaluates their 32 pairs, so a pair
 // costs 16 FMA-pipe operations for two interactions (differences, r^2, r^-3,
