@@ -149,3 +149,32 @@ def test_batch_rejects_bad_shapes(nbs):
         assert e.value.code == nbs.NB_EINVAL
         with pytest.raises(nbs.NBError):
             b.set_cluster_params(eps=[0.1, -1.0])
+
+
+def test_c4_full_ensemble_sampled(nbs, orc):
+    """The benchmark's ensemble at full size (512 Plummer clusters, N_k
+    log-uniform in [256, 8192], 1.29M bodies, paper softening per cluster) in
+    the launch configuration the benchmark times: accelerations of sampled
+    bodies of the smallest, largest and 18 other clusters against the oracle,
+    each cluster to the mixed tolerance."""
+    sizes = ics.ensemble_sizes(512, 256, 8192, seed=0)
+    cl = [ics.henon_plummer(int(n), k) for k, n in enumerate(sizes)]
+    eps = [ics.paper_softening(int(n)) for n in sizes]
+    pos, vel, m = (np.concatenate([c[i] for c in cl]) for i in range(3))
+    with nbs.Context(sizes=sizes, precision="ds") as b:
+        b.set_cluster_params(eps=eps)
+        b.load(pos, vel, m)
+        shape = b.pair_shape()
+        a = b.accel()
+    assert shape["grid"] > 3 * 152, shape   # the grid runs in waves, as in the benchmark
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    rng = np.random.default_rng(4)
+    pick = {int(np.argmin(sizes)), int(np.argmax(sizes))}
+    pick |= set(int(k) for k in rng.choice(len(sizes), 18, replace=False))
+    for k in sorted(pick):
+        n = int(sizes[k])
+        idx = np.unique(rng.choice(n, min(n, 64), replace=False))
+        ref = orc.accel_int_at(cl[k][0], cl[k][2], idx, 1.0, eps[k])
+        got = a[off[k]:off[k + 1]][idx]
+        err = rel_rms(got, ref)
+        assert err <= 1e-6, (k, n, err)
