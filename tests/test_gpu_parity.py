@@ -489,3 +489,20 @@ def test_batch_mixing_uniform_and_spread_masses(nbs, orc):
     for (p, _, mm, e), n in zip(cl, sizes):
         assert rel_rms(a[off:off + n], orc.accel_int(p, mm, 1.0, e)) <= TOL["ds"]
         off += n
+
+
+def test_largest_benchmarked_system_sampled(nbs, orc):
+    """The largest system the benchmark runs (the paper's N = 1,536,000
+    uniform sphere of Table 3, paper softening): 64 sampled bodies against
+    the oracle in the mixed and pure-float modes."""
+    n = 1536000
+    pos, vel, m = ics.uniform_sphere(n, 0, q_vir=0.3)
+    eps = ics.paper_softening(n)
+    idx = _sample(n, 64, 5)
+    ref = orc.accel_int_at(pos, m, idx, 1.0, eps)
+    with nbs.Context(n, eps=eps, precision="ds") as c:
+        c.load(pos, vel, m)
+        for prec, tol in (("ds", TOL["ds"]), ("fp32", TOL["fp32"])):
+            c.set_precision(prec)
+            err = rel_rms(c.accel()[idx], ref)
+            assert err <= tol, (prec, err)
