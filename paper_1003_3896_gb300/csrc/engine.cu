@@ -132,6 +132,13 @@ int set_create(ClusterSet &C, int32_t kcap, int64_t body_cap)
         set_destroy(C);
         return set_error(NB_ENOMEM, "cluster tables: device allocation failed");
     }
+    if (cudaStreamCreateWithFlags(&C.side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&C.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&C.join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        set_destroy(C);
+        return set_error(NB_ECUDA, "cluster tables: stream or event creation failed");
+    }
     cudaMemset(C.dmem, 0, bytes);
     return NB_OK;
 }
@@ -142,6 +149,9 @@ void set_destroy(ClusterSet &C)
                     C.cid,     C.ng_spos, C.ng_slo,  C.ng_slot,  C.ng_rank};
     for (void *q : ptrs)
         if (q) cudaFree(q);
+    if (C.fork) cudaEventDestroy(C.fork);
+    if (C.join) cudaEventDestroy(C.join);
+    if (C.side) cudaStreamDestroy(C.side);
     C = ClusterSet();
 }
 
@@ -441,13 +451,22 @@ int enq_force(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph
     ht.ntiles = C.ntiles.data();
     ht.eps2f = C.eps2f.data();
     ht.mu = C.mu.data();
+    // the near-pair pass (mixed mode) forks onto the set's side stream and
+    // runs beside the pair kernel: both read only the float planes, and they
+    // write different buffers (corr, part), so the overlap cannot change a
+    // result; the join orders it before whatever follows on st
+    const bool near = pl.pl.mode == PM_DS_NEAR;
+    if (near) {
+        NB_TRY(cudaEventRecord(C.fork, st));
+        NB_TRY(cudaStreamWaitEvent(C.side, C.fork, 0));
+        NB_TRY(launch_near_correct(s, ph.G, pl.pl.um, C.side));
+        NB_TRY(cudaEventRecord(C.join, C.side));
+        count(kernels, NEAR_KERNELS);
+    }
     NB_TRY(launch_pair(s, pl.pl, ht, ph.G, st));
     if (ev1) NB_TRY(cudaEventRecordWithFlags(ev1, st, evf));
     count(kernels, 1);
-    if (pl.pl.mode == PM_DS_NEAR) {
-        NB_TRY(launch_near_correct(s, ph.G, pl.pl.um, st));
-        count(kernels, NEAR_KERNELS);
-    }
+    if (near) NB_TRY(cudaStreamWaitEvent(st, C.join, 0));
     return NB_OK;
 }
 

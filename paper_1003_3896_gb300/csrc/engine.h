@@ -61,6 +61,10 @@ struct ClusterSet {
     Frame *frame = nullptr;    // [kcap]
     double *diag = nullptr;    // [kcap][DIAG_STRIDE]
     Clusters cl, cl_pot;       // device views (pair units / potential units)
+    // side stream and fork / join events: the near-pair pass runs beside the
+    // pair kernel (it reads only the float planes, and writes only corr)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 int set_create(ClusterSet &C, int32_t kcap, int64_t body_cap);
 void set_destroy(ClusterSet &C);
