@@ -172,8 +172,12 @@ struct IPairs {
 // (eps = 0, diagonal chunks).  UM (all masses of the cluster equal): the pair
 // term is d / r^3 without m_j, one multiply fewer; the caller scales by m.
 // At P = 4 the chunk stays a loop of four groups of 8 j: fully unrolled, the
-// kernel's code outgrows the instruction cache and runs 30% slower.
-template <int P, int MODE, bool MASK, bool UM>
+// kernel's code outgrows the instruction cache and runs 30% slower.  PA: the
+// packed pairs evaluated, the first PA of P (a partly filled i-block leaves
+// the others as padding for every lane of the warp; a variant per count keeps
+// each loop fully unrolled, where a runtime bound inside it cost more than the
+// padding).
+template <int P, int MODE, bool MASK, bool UM, int PA = P>
 __device__ __forceinline__ void chunk_pass(const float4 (*cb)[4], int j0, int ibase,
                                            IPairs<P> &ip, float eps2)
 {
@@ -197,7 +201,7 @@ __device__ __forceinline__ void chunk_pass(const float4 (*cb)[4], int j0, int ib
                 lzz = make_float2(D.x, D.y);
             }
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
+            for (int p = 0; p < PA; ++p) {
                 float2 dx = __fadd2_rn(xx, ip.nx[p]);
                 float2 dy = __fadd2_rn(yy, ip.ny[p]);
                 float2 dz = __fadd2_rn(zz, ip.nz[p]);
@@ -290,6 +294,12 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
         for (int r = 0; r < 6 * I; ++r) acc_sh[r][tid] = 0.f;
 
         const int J0 = sg.J0, J1 = sg.J1;
+        // packed pairs of this warp holding at least one body of the cluster
+        // (warp-uniform): its lanes' bodies are ib0 + 32 w + lane + k TILE
+        const int lw = ib0 + 32 * w;
+        int kmax = n > lw ? (n - lw + TILE - 1) / TILE : 0;
+        if (kmax > I) kmax = I;
+        const int pact = (kmax + 1) / 2;
         float4 pf[4];
         {
             const int j = J0 + lane;
@@ -314,10 +324,27 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
                 }
             }
             const bool diag = mask_self && jc < ib0 + d.ipb && jc + CH > ib0;
-            if (diag)
-                chunk_pass<P, MODE, true, UM>(cb, jc, ibase, ip, eps2);
-            else
-                chunk_pass<P, MODE, false, UM>(cb, jc, ibase, ip, eps2);
+            if (pact >= P) {
+                if (diag)
+                    chunk_pass<P, MODE, true, UM>(cb, jc, ibase, ip, eps2);
+                else
+                    chunk_pass<P, MODE, false, UM>(cb, jc, ibase, ip, eps2);
+            } else if (P > 1 && pact == (P > 1 ? P - 1 : 1)) {
+                if (diag)
+                    chunk_pass<P, MODE, true, UM, (P > 1 ? P - 1 : 1)>(cb, jc, ibase, ip, eps2);
+                else
+                    chunk_pass<P, MODE, false, UM, (P > 1 ? P - 1 : 1)>(cb, jc, ibase, ip, eps2);
+            } else if (P > 2 && pact == (P > 2 ? P - 2 : 1)) {
+                if (diag)
+                    chunk_pass<P, MODE, true, UM, (P > 2 ? P - 2 : 1)>(cb, jc, ibase, ip, eps2);
+                else
+                    chunk_pass<P, MODE, false, UM, (P > 2 ? P - 2 : 1)>(cb, jc, ibase, ip, eps2);
+            } else if (P > 3 && pact == 1) {
+                if (diag)
+                    chunk_pass<P, MODE, true, UM, 1>(cb, jc, ibase, ip, eps2);
+                else
+                    chunk_pass<P, MODE, false, UM, 1>(cb, jc, ibase, ip, eps2);
+            }
             __syncwarp();
             if (((jc + CH - J0) & (FOLD - 1)) == 0 || jc + CH >= J1) {
                 // every FOLD j and at the segment's end: fold the float
