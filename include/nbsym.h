@@ -93,7 +93,11 @@ typedef struct {
     double Mb, ab;     /* bulge mass, scale (ab > 0) */
     int device;        /* CUDA device ordinal */
     void *stream;      /* cudaStream_t to run on; NULL: the context creates
-                          and owns a non-blocking stream */
+                          and owns a non-blocking stream.  The context also
+                          owns a second stream on which the NB_DS near-pair
+                          pass runs beside the pair kernel; every call joins
+                          it back into this stream (events, captured into the
+                          step graphs), so work is ordered on this stream */
     double near_frac;  /* NB_DS only: pairs closer than near_frac * R_rms /
                           N^{1/3} (R_rms = mass-weighted rms radius about the
                           centre of mass, so the radius scales with the mean
