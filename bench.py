@@ -137,20 +137,25 @@ PAPER_CONTEXT = {
 }
 
 
-def pair_source_digest() -> str | None:
-    """Digest of pair.cu's code with comments and whitespace removed, so the
-    recorded traffic stays valid across comment edits and lapses with any
-    change of the kernel's code."""
+def code_digest(text: str) -> str:
+    """First 16 hex digits of the SHA-256 of C/C++ source with its comments
+    and whitespace removed: equal across comment and layout edits, different
+    for any change of the code."""
     import hashlib
     import re
-    path = os.path.join(ROOT, "paper_1003_3896_gb300", "csrc", "pair.cu")
-    try:
-        text = open(path).read()
-    except OSError:
-        return None
     text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
     text = re.sub(r"//[^\n]*", " ", text)
     return hashlib.sha256(" ".join(text.split()).encode()).hexdigest()[:16]
+
+
+def pair_source_digest() -> str | None:
+    """code_digest of pair.cu: the recorded traffic stays valid across
+    comment edits and lapses with any change of the kernel's code."""
+    path = os.path.join(ROOT, "paper_1003_3896_gb300", "csrc", "pair.cu")
+    try:
+        return code_digest(open(path).read())
+    except OSError:
+        return None
 
 
 def pair_traffic(n: int, precision: str, shape: dict):

@@ -114,3 +114,16 @@ def test_tuning_table_files_without_gpu(lib, tmp_path):
     assert nbsym.nb_tune_save(None) == nbsym.NB_EINVAL
     assert nbsym.nb_tune(None, 2, None) == nbsym.NB_EINVAL
     assert nbsym.nb_pair_shape(None, None, None, None, None) == nbsym.NB_EINVAL
+
+
+def test_traffic_record_keys_on_code_not_comments():
+    """The benchmark reports the captured DRAM traffic of the pair kernel only
+    while pair.cu's code is the captured code: comment and layout edits keep
+    the digest, any code edit changes it (and the bench then reports null)."""
+    import bench
+    src = "int f(int a) {\n    return a + 1;   // one\n}\n/* block\n comment */\n"
+    same = "int f(int a)\n{\n  return a + 1;   // another comment\n}\n"
+    other = "int f(int a) {\n    return a + 2;\n}\n"
+    assert bench.code_digest(src) == bench.code_digest(same)
+    assert bench.code_digest(src) != bench.code_digest(other)
+    assert len(bench.pair_source_digest()) == 16
