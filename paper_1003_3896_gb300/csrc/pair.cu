@@ -4,9 +4,12 @@
 // a set of independent clusters: a grid of G blocks (one resident wave or
 // several), one contiguous run of (cluster, i-block, j-tile) units per block,
 // so every block gets the same amount of work whatever the cluster sizes are
-// (one cluster, or an ensemble of uneven clusters in one launch).  Each thread owns I
-// i-bodies and keeps their sums in registers; every pair of each cluster's
-// N x N array is evaluated, as in the paper (Sect. 4.2), not N(N-1)/2.
+// (one cluster, or an ensemble of uneven clusters in one launch).  Each thread
+// owns I i-bodies and keeps their sums in registers; every pair of each
+// cluster's N x N array is evaluated, as in the paper (Sect. 4.2), not
+// N(N-1)/2.  Clusters of equal masses leave m out of the pair term (scaled in
+// afterwards), and in partly filled i-blocks a warp evaluates only the packed
+// i-pairs that hold bodies.
 //
 // Single-precision family (one template, three modes):
 //   PM_DS_NEAR  float pair arithmetic on coordinates relative to the cluster's
