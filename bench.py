@@ -213,6 +213,9 @@ def shard_clusters(sizes, world: int):
     return [np.array(sorted(o), dtype=np.int64) for o in out]
 
 
+FP64_PEAK_TFLOPS = 1.25   # GB300 nominal dense FP64
+
+
 def fp32_peak_tflops(sms: int, mhz: float) -> float:
     """FP32 FMA peak from unit counts: 128 FP32 lanes per SM, 2 flops per FMA."""
     return sms * 128 * 2 * mhz * 1e6 / 1e12
@@ -404,8 +407,20 @@ def main():
     clocks = clk.summary()
     peaks = nbsym.measure_peaks(local)
     achieved = FLOPS_PER_PAIR * prof["interactions"] / (prof["pair_ms"] * 1e-3) / 1e12
-    peak = fp32_peak_tflops(sms, 2070.0)
     sustained_mhz = clocks.get("sm_mhz") or 2070.0
+    kernel = {"fp64": "pair_fp64_kernel", "dd": "pair_ff_kernel"}.get(args.precision,
+                                                                       "pair_sp_kernel")
+    if args.precision == "fp64":
+        # the FP64 pipe: its nominal dense rate for this GPU, and the DFMA
+        # rate measured in the same run
+        peak, peak_basis = FP64_PEAK_TFLOPS, "nominal FP64 of GB300 (1.25 TFLOP/s)"
+        frac_clock = achieved / peak * 2070.0 / sustained_mhz
+        frac_meas = achieved / peaks["dfma_tflops"]
+    else:
+        peak = fp32_peak_tflops(sms, 2070.0)
+        peak_basis = f"{sms} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max clock)"
+        frac_clock = achieved / fp32_peak_tflops(sms, sustained_mhz)
+        frac_meas = achieved / max(peaks["ffma_tflops"], peaks["ffma2_tflops"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
@@ -416,11 +431,11 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": pair_traffic(n, args.precision, shape),
                      "traffic_unit": "bytes per launch (dram read + write)",
-                     "kernel": f"pair_sp_kernel ({args.precision})",
-                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max clock)",
-                     "frac_at_sampled_clock": achieved / fp32_peak_tflops(sms, sustained_mhz),
-                     "frac_of_measured_fp32": achieved / max(peaks["ffma_tflops"],
-                                                             peaks["ffma2_tflops"]),
+                     "kernel": f"{kernel} ({args.precision})",
+                     "peak_basis": peak_basis,
+                     "frac_at_sampled_clock": frac_clock,
+                     ("frac_of_measured_fp64" if args.precision == "fp64"
+                      else "frac_of_measured_fp32"): frac_meas,
                      "measured_peaks": peaks,
                      "pair_kernel_ms_mean": prof["pair_ms"] / max(1, prof["pair_launches"]),
                      "pair_launches": prof["pair_launches"]},
