@@ -63,7 +63,9 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(),
+                                 f"nbsym_clocks_rank{index}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
