@@ -23,6 +23,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "nbody_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
+CFLAGS = ["-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+          "-fPIC", "-shared"]
 
 
 def build(force: bool = False) -> str:
@@ -30,8 +32,7 @@ def build(force: bool = False) -> str:
     if (not force and os.path.exists(_LIB)
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
-    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
-           "-fopenmp", "-fPIC", "-shared", "-o", _LIB + ".tmp", _SRC, "-lm"]
+    cmd = ["gcc", *CFLAGS, "-o", _LIB + ".tmp", _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(_LIB + ".tmp", _LIB)
     return _LIB
@@ -71,7 +72,14 @@ def _load():
     if _lib is not None:
         return _lib
     build()
-    lib = C.CDLL(_LIB)
+    _lib = _bind(C.CDLL(_LIB))
+    return _lib
+
+
+def _bind(lib):
+    """Declare the argument and result types of the oracle's C entry points on
+    a loaded copy of the library (the tests also bind copies built from
+    deliberately altered sources, to check that the pins reject them)."""
     dp = C.POINTER(C.c_double)
     pp = C.POINTER(_Params)
     i64 = C.c_int64
@@ -90,7 +98,6 @@ def _load():
     lib.orc_run.restype = C.c_int
     lib.orc_set_threads.argtypes = [C.c_int]
     lib.orc_max_threads.restype = C.c_int
-    _lib = lib
     return lib
 
 

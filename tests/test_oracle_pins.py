@@ -202,6 +202,43 @@ def test_ext_symmetries(orc):
     np.testing.assert_allclose(orc.ext_accel(p, xm)[0], a * [1, 1, -1], rtol=1e-14)
 
 
+def test_ext_field_scaling_laws(orc):
+    """Phi and a_ext are linear in G and, jointly, in the three masses;
+    stretching every length (the point and a_d, b_d, a_b, eps_bh) by l divides
+    Phi by l and a_ext by l^2. A dropped G, or a scale entering unsquared,
+    breaks one of these."""
+    base = dict(ext_on=True, Mbh=4.0, eps_bh=0.3)
+    p = _params(orc, **base)
+    lam, g = 2.5, 1.9
+    big = _params(orc, ext_on=True, eps_bh=p.eps_bh, G=g, Md=3 * p.Md, Mb=3 * p.Mb,
+                  Mbh=3 * p.Mbh)
+    far = _params(orc, ext_on=True, Mbh=p.Mbh, eps_bh=lam * p.eps_bh, ad=lam * p.ad,
+                  bd=lam * p.bd, ab=lam * p.ab)
+    for x in ([50.0, 0.3, -0.2], [0.4, -0.1, 0.05], [7.0, 3.0, 1.5], [0.0, 0.0, 0.0]):
+        x = np.array(x)
+        phi, a = orc.ext_phi(p, x), orc.ext_accel(p, x)[0]
+        assert abs(orc.ext_phi(big, x) - 3 * g * phi) <= 1e-14 * abs(phi) * 3 * g
+        np.testing.assert_allclose(orc.ext_accel(big, x)[0], 3 * g * a,
+                                   rtol=1e-14, atol=1e-15 * np.abs(a).max() * 3 * g)
+        assert abs(orc.ext_phi(far, lam * x) - phi / lam) <= 1e-14 * abs(phi)
+        np.testing.assert_allclose(orc.ext_accel(far, lam * x)[0], a / lam ** 2,
+                                   rtol=1e-14, atol=1e-15 * np.abs(a).max())
+
+
+def test_total_acceleration_is_internal_plus_field(orc):
+    """Eq. 3: the right-hand side is the pair sum plus the field term; a lone
+    body feels the field alone."""
+    p = _params(orc, ext_on=True, eps=0.05, G=1.3, Mbh=2.0, eps_bh=0.1)
+    one = np.array([[3.0, -1.0, 0.7]])
+    np.testing.assert_array_equal(orc.accel(one, [2.0], p), orc.ext_accel(p, one))
+    pos, _, m = ics.plummer(40, seed=12)
+    pos = pos + np.array([4.0, 1.0, 0.5])
+    want = orc.accel_int(pos, m, 1.3, 0.05) + orc.ext_accel(p, pos)
+    np.testing.assert_allclose(orc.accel(pos, m, p), want, rtol=1e-15, atol=1e-16)
+    off = _params(orc, ext_on=False, eps=0.05, G=1.3, Mbh=2.0, eps_bh=0.1)
+    np.testing.assert_array_equal(orc.accel(pos, m, off), orc.accel_int(pos, m, 1.3, 0.05))
+
+
 def test_circular_speed_constant(orc):
     """VC_R50 and VC_R10 (input module constants) equal sqrt(R |a_R|) at
     R = 50 and R = 10, z = 0."""
