@@ -269,7 +269,8 @@ def run_reference(args, rank, world):
     value = args.steps * k * n / tot / 1e9
     cores = oracle.max_threads()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
-            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "n_gpus": args.gpus, "device": "host cores (no GPU work)",
+            "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(args, 1),
