@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "engine.h"
+#include "range_alloc.h"
 
 using namespace nb;
 
@@ -56,39 +57,6 @@ struct Group {
     bool inflight = false;
     std::vector<int64_t> stepping;        // members of the step in flight
     int64_t step_pairs = 0;               // interactions of that step
-};
-
-// First-fit allocator of ranges of pool slots.
-struct RangeAlloc {
-    std::map<int64_t, int64_t> free_;     // start -> length
-    explicit RangeAlloc(int64_t cap = 0) { if (cap > 0) free_[0] = cap; }
-    int64_t alloc(int64_t n)
-    {
-        for (auto it = free_.begin(); it != free_.end(); ++it)
-            if (it->second >= n) {
-                const int64_t off = it->first, len = it->second;
-                free_.erase(it);
-                if (len > n) free_[off + n] = len - n;
-                return off;
-            }
-        return -1;
-    }
-    void release(int64_t off, int64_t n)
-    {
-        auto it = free_.emplace(off, n).first;
-        auto nx = std::next(it);
-        if (nx != free_.end() && it->first + it->second == nx->first) {
-            it->second += nx->second;
-            free_.erase(nx);
-        }
-        if (it != free_.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) {
-                pv->second += it->second;
-                free_.erase(it);
-            }
-        }
-    }
 };
 
 // Bytes of device memory the pool and the group scratch use per body slot.
