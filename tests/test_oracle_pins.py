@@ -317,6 +317,36 @@ def test_si6a_weights_consistency(orc):
     assert abs(s5) < 1e-12
 
 
+@pytest.mark.parametrize("order", [2, 6])
+def test_free_body_moves_in_a_straight_line(orc, order):
+    """A lone body with no field feels no force, so every scheme moves it by
+    t v exactly up to rounding: the drift weights of a step sum to one (for
+    SI6A, w0 + 2(w1 + w2 + w3) = 1) and no kick changes v."""
+    x0 = np.array([[3.0, -2.0, 0.5]])
+    v0 = np.array([[0.25, 1.5, -0.75]])
+    h, n = 1 / 64, 128
+    x, v = orc.run(x0, v0, [1.0], _params(orc, eps=0.1), order, h, n)
+    np.testing.assert_array_equal(v, v0)
+    np.testing.assert_allclose(x, x0 + n * h * v0, rtol=0, atol=1e-13)
+
+
+def test_degenerate_sizes_and_arguments(orc):
+    """No bodies: empty accelerations and zero diagnostics; zero steps leave the
+    state as it is; an order other than 2 or 6 is refused."""
+    p = _params(orc, eps=0.1, ext_on=True)
+    z = np.zeros((0, 3))
+    assert orc.accel(z, np.zeros(0), p).shape == (0, 3)
+    e = orc.energy(z, z, np.zeros(0), p)
+    assert (e.K, e.W, e.W_ext, e.E) == (0.0, 0.0, 0.0, 0.0)
+    assert not e.P.any() and not e.L.any()
+    pos, vel, m = ics.plummer(8, seed=13)
+    x, v = orc.run(pos, vel, m, p, 6, 0.01, 0)
+    np.testing.assert_array_equal(x, pos)
+    np.testing.assert_array_equal(v, vel)
+    with pytest.raises(ValueError):
+        orc.run(pos, vel, m, p, 4, 0.01, 1)
+
+
 def _energy_drift(orc, order, nsteps):
     pos, vel, m = ics.kepler_pair(0.5, 0.5, 1.0, 0.5)
     p = _params(orc, eps=0.0)
