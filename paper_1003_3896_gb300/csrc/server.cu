@@ -107,8 +107,7 @@ int upload(nb_server *s, Job &j)
 {
     const int64_t n = j.d.n;
     const int64_t off = j.off;
-    const int64_t nk = n, eps0 = 0;
-    (void)eps0;
+    const int64_t nk = n;
     const double e = j.d.eps, one = 1.0;
     int rc = set_define(s->io, 1, &off, &nk, &e, &one);
     if (!rc) rc = set_layout(s->io, TILE, s->io_stream);
