@@ -2,6 +2,9 @@
 
 Each prints one labelled JSON line; the headline line (``c2``) stays in
 bench.py.  Inputs are seeded and synthetic (paper_1003_3896_gb300.ics).
+With ``--impl reference`` each instead times the CPU oracle on the same
+workload's inputs and metric (run_reference); the serving workload has no
+counterpart there.
 
   c1  N = 1024 Plummer in Henon units, eps = 1e-3, FP64, leapfrog DKD,
       dt = 1/1024, 64 steps: latency per step and |dE/E| against the oracle's
@@ -398,10 +401,131 @@ def sym(args, nbsym, torch):
             "note": "interactions counted as N^2 for both, so the rates compare time"}
 
 
+def _timed_steps(args, fn) -> float:
+    """args.warmup untimed calls of fn, then the seconds args.steps calls take."""
+    for _ in range(args.warmup):
+        fn()
+    wall = 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        fn()
+        wall += time.perf_counter() - t0
+    return wall
+
+
+def run_reference(args):
+    """Reference arm of a secondary workload: the CPU oracle as it stands, on
+    the host cores, timed on that workload's own inputs and metric.  Each step
+    is a bounded sample: the whole 64-step run for c1, whole clusters (in
+    index order) for c4, otherwise a sample of target bodies against all N
+    sources (eq. 5, FP64).  The serving workload (c5) has no counterpart: the
+    oracle has no serving loop.  Under torchrun rank 0 alone runs."""
+    import bench
+    import oracle
+    world, rank, _ = bench.rank_env()
+    if rank != 0:
+        return 0
+    w = args.workload
+    if w == "c5":
+        print(json.dumps({"impl": "reference", "workload": "c5",
+                          "unavailable": "the CPU oracle has no serving loop: the p50/p99 "
+                                         "latency of a job stream is defined for the GPU "
+                                         "server only"}), flush=True)
+        return 0
+    oracle.build()
+    rng = np.random.default_rng(1)
+    pairs_per_step = None
+
+    def targets(pos, m, eps, k):
+        nonlocal pairs_per_step
+        n = m.size
+        k = min(k, n)
+        idx = np.sort(rng.choice(n, k, replace=False))
+        pairs_per_step = k * n
+        return (lambda: oracle.accel_int_at(pos, m, idx, 1.0, eps),
+                f"per step {k} target bodies x {n} sources (eq. 5, FP64)")
+
+    hib, unit = True, UNIT
+    if w == "c1":
+        n, eps, dt, nsteps = 1024, 1e-3, 1.0 / 1024, 64
+        pos, vel, m = ics.henon_plummer(n, 0)
+        prm = oracle.Params(eps=eps)
+        fn = lambda: oracle.run(pos, vel, m, prm, 2, dt, nsteps)
+        sample = f"per step the full run: {nsteps} DKD steps of N = {n} (FP64)"
+        metric, workload = ("leapfrog step latency, N=1024",
+                            "plummer_N1024_henon_eps1e-3_dkd_dt1/1024_64steps")
+        hib, unit = False, "us/step"
+    elif w == "c3":
+        n = 262144
+        pos, _, m = ics.plummer(n, 0, masses=ics.salpeter_masses(n, 0))
+        fn, sample = targets(pos, m, 1e-4, 256)
+        metric, workload = ("accuracy sweep and leapfrog throughput, N=262144 Salpeter",
+                            "plummer_salpeter_N262144_eps1e-4")
+    elif w == "c4":
+        sizes = ics.ensemble_sizes(512, 256, 8192, seed=0)
+        chosen, tot = [], 0.0
+        for k, n in enumerate(sizes):
+            chosen.append((k, int(n)))
+            tot += float(n) * float(n)
+            if tot >= 1e8:
+                break
+        systems = []
+        for k, n in chosen:
+            p, _, m = ics.henon_plummer(n, k)
+            systems.append((p, m, ics.paper_softening(n)))
+        fn = lambda: [oracle.accel_int(p, m, 1.0, e) for p, m, e in systems]
+        pairs_per_step = tot
+        sample = (f"per step the full sums of clusters 0-{len(chosen) - 1} of the 512 "
+                  f"({int(sum(n for _, n in chosen))} bodies, eq. 5, FP64)")
+        metric, workload = ("batched ensemble throughput",
+                            "512_plummer_clusters_N256-8192_henon_si6a_dt1/512_ds")
+    elif w == "paper":
+        n = 30720
+        pos, _, m = ics.uniform_sphere(n, 0, q_vir=0.3)
+        fn, sample = targets(pos, m, ics.paper_softening(n), 2048)
+        metric, workload = ("paper workload series (uniform sphere Q = 0.3, leapfrog)",
+                            "uniform_sphere_Q0.3_N480_30720_1536000_leapfrog_dt5e-4")
+    elif w == "plunge":
+        n = 15360
+        pos, _, m = ics.plunge_cluster(n, 0)
+        fn, sample = targets(pos, m, ics.paper_softening(n), 2048)
+        metric, workload = ("black-hole collision runs (Sect. 6.2)",
+                            f"plunge_plummer_N{n}_r0_10_v0.001vc_epsbh0.05_si6a_t4_"
+                            f"{int(os.environ.get('NB_PLUNGE_STEPS', '20000'))}steps_ds")
+    elif w == "sym":
+        n = 262144
+        pos, _, m = ics.henon_plummer(n, 0)
+        fn, sample = targets(pos, m, ics.paper_softening(n), 1024)
+        metric, workload = ("N(N-1)/2 variant vs full N^2 sum (float class)",
+                            "henon_plummer_N16384_65536_262144_fp32")
+    else:
+        raise ValueError(f"unknown workload {w}")
+    wall = _timed_steps(args, fn)
+    if unit == "us/step":
+        value = 1e6 * wall / (args.steps * nsteps)
+    else:
+        value = args.steps * pairs_per_step / wall / 1e9
+    cores = oracle.max_threads()
+    line = {"impl": "reference", "metric": metric, "value": value, "unit": unit,
+            "n_gpus": args.gpus, "device": "host cores (no GPU work)",
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": hib,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "workload": workload, "config": {"workload": workload},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run(args):
     """One workload line.  Under torchrun only the ensemble (c4) shards across
     ranks (whole clusters per rank); the single-system workloads run on rank
     0 alone and the other ranks exit without work."""
+    if getattr(args, "impl", "ours") == "reference":
+        return run_reference(args)
     import bench
     import torch
     world, rank, local = bench.rank_env()
