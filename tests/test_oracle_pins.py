@@ -330,6 +330,30 @@ def test_free_body_moves_in_a_straight_line(orc, order):
     np.testing.assert_allclose(x, x0 + n * h * v0, rtol=0, atol=1e-13)
 
 
+def test_results_do_not_depend_on_the_thread_count(orc):
+    """OpenMP splits only the independent per-body work, and every sum keeps
+    its serial order: one thread and all threads give the same bits."""
+    pos, vel, m = ics.plummer(300, seed=14, masses=ics.salpeter_masses(300, 14))
+    p = _params(orc, eps=0.02, ext_on=True, Mbh=2.0, eps_bh=0.1)
+    pos = pos + np.array([8.0, 1.0, 0.3])
+    full = orc.max_threads()
+    out = []
+    for t in (1, full):
+        orc.set_threads(t)
+        try:
+            e = orc.energy(pos, vel, m, p)
+            out.append((orc.accel(pos, m, p), orc.run(pos, vel, m, p, 6, 1 / 512, 3),
+                        [e.K, e.W, e.W_ext, *e.P, *e.L], orc.torque(pos, m, p)))
+        finally:
+            orc.set_threads(full)
+    (a1, (x1, v1), e1, t1), (a2, (x2, v2), e2, t2) = out
+    np.testing.assert_array_equal(a1, a2)
+    np.testing.assert_array_equal(x1, x2)
+    np.testing.assert_array_equal(v1, v2)
+    assert e1 == e2
+    np.testing.assert_array_equal(t1, t2)
+
+
 def test_degenerate_sizes_and_arguments(orc):
     """No bodies: empty accelerations and zero diagnostics; zero steps leave the
     state as it is; an order other than 2 or 6 is refused."""
