@@ -28,7 +28,8 @@ def block(f, name, a):
         f.write(" ".join(f"{v:.17e}" for v in row) + "\n")
 
 
-def main():
+def main(out=None):
+    """Write the fixture to ``out`` (default: its place beside this script)."""
     oracle.build()
     pos, vel, m = ics.plummer(N, SEED)
     pos, vel = ics.place_on_orbit(pos, vel)
@@ -38,7 +39,8 @@ def main():
     e = oracle.energy(pos, vel, m, p)
     x6, v6 = oracle.run(pos, vel, m, p, 6, DT, STEPS)
     x2, v2 = oracle.run(pos, vel, m, p, 2, DT, STEPS)
-    out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_plummer16_orbit.txt")
+    if out is None:
+        out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_plummer16_orbit.txt")
     with open(out, "w") as f:
         f.write("# Written by tests/golden/make_golden.py from the CPU oracle (oracle/), FP64.\n")
         f.write("# Inputs: Plummer sphere (a = 1, M = 1, N = 16, seed 7) with its centre of mass\n")

@@ -5,6 +5,7 @@ against the derivative of a potential) -- chosen so that a dropped term, a
 wrong sign, index or exponent anywhere in the oracle fails at least one.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -697,6 +698,22 @@ def test_oracle_reproduces_its_fixture(orc):
         x, v = orc.run(pos, vel, m, p, order, dt, int(steps))
         np.testing.assert_allclose(x, g[f"pos_order{order}"], rtol=0, atol=1e-12)
         np.testing.assert_allclose(v, g[f"vel_order{order}"], rtol=0, atol=1e-12)
+
+
+def test_fixture_is_exactly_what_its_script_writes(tmp_path):
+    """The committed fixture is the byte-for-byte output of the committed
+    script (which calls only the oracle and the seeded inputs), so no stored
+    value has another source."""
+    import importlib.util
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_golden",
+                                                  os.path.join(here, "make_golden.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    out = tmp_path / "fixture.txt"
+    mod.main(str(out))
+    with open(os.path.join(here, "oracle_plummer16_orbit.txt"), "rb") as f:
+        assert out.read_bytes() == f.read()
 
 
 def test_paper_context_matches_the_printed_tables():
