@@ -215,7 +215,8 @@ int nb_step(nb_ctx *ctx, int order, double dt, int64_t nsteps);
  * NB_ENONFINITE, NB_ECUDA. */
 int nb_energy(nb_ctx *ctx, nb_energy_t *out);
 
-/* The same per cluster: out has nb_clusters() entries. */
+/* The same per cluster: out has nb_clusters() entries, cluster k's record
+ * at out[k].  Errors as nb_energy. */
 int nb_energy_clusters(nb_ctx *ctx, nb_energy_t *out);
 
 /* External torque M_ext = sum m_i r_i x a_ext(r_i) (eq. 8), summed over the
@@ -242,7 +243,8 @@ int nb_set_precision(nb_ctx *ctx, int precision);
  * event-record nodes).  Starting resets the counters.  Errors: NB_EINVAL. */
 int nb_prof_enable(nb_ctx *ctx, int on);
 
-/* Read the counters accumulated since nb_prof_enable(ctx, 1). */
+/* Read the counters accumulated since nb_prof_enable(ctx, 1) into *out.
+ * Errors: NB_EINVAL (NULL ctx or out). */
 int nb_prof_read(nb_ctx *ctx, nb_prof_t *out);
 
 /* Measure the arithmetic peaks the pair kernels are bounded by (the
