@@ -67,12 +67,65 @@ def test_create_rejects_bad_params_without_gpu(lib, field, value):
     assert nbsym.nb_last_error()
 
 
+NULL_CALLS = r"""
+import sys
+sys.path.insert(0, %r)
+from paper_1003_3896_gb300 import nbsym as nb
+E = nb.NB_EINVAL
+calls = {
+    "nb_create": nb.nb_create(None, 16, None),
+    "nb_create_batch": nb.nb_create_batch(None, 1, None, None),
+    "nb_set_cluster_params": nb.nb_set_cluster_params(None, None, None),
+    "nb_clusters": nb.nb_clusters(None),
+    "nb_load": nb.nb_load(None, 1, None, None, None),
+    "nb_load_device": nb.nb_load_device(None, 1, None, None, None),
+    "nb_accel": nb.nb_accel(None, None),
+    "nb_accel_device": nb.nb_accel_device(None, None),
+    "nb_step": nb.nb_step(None, 2, 0.1, 1),
+    "nb_energy": nb.nb_energy(None, None),
+    "nb_energy_clusters": nb.nb_energy_clusters(None, None),
+    "nb_torque": nb.nb_torque(None, None),
+    "nb_get_state": nb.nb_get_state(None, None, None),
+    "nb_get_state_device": nb.nb_get_state_device(None, None, None),
+    "nb_size": nb.nb_size(None),
+    "nb_set_precision": nb.nb_set_precision(None, 0),
+    "nb_prof_enable": nb.nb_prof_enable(None, 1),
+    "nb_prof_read": nb.nb_prof_read(None, None),
+    "nb_accel_static": nb.nb_accel_static(None, 16, None, None, None),
+    "nb_accel_range": nb.nb_accel_range(None, 0, 1, None),
+    "nb_accel_symmetric": nb.nb_accel_symmetric(None, None, None),
+    "nb_tune": nb.nb_tune(None, 2, None),
+    "nb_pair_shape": nb.nb_pair_shape(None, None, None, None, None),
+    "nb_server_create": nb.nb_server_create(None, None),
+    "nb_server_submit": nb.nb_server_submit(None, None, None, None, None, None),
+    "nb_server_poll": nb.nb_server_poll(None, 1, None),
+    "nb_server_wait": nb.nb_server_wait(None, 1, 0.0, None),
+    "nb_server_result": nb.nb_server_result(None, 1, None, None),
+    "nb_server_cancel": nb.nb_server_cancel(None, 1),
+    "nb_server_forget": nb.nb_server_forget(None, 1),
+    "nb_server_stats": nb.nb_server_stats(None, None),
+}
+nb.nb_destroy(None)
+nb.nb_server_destroy(None)
+nb.nb_params_default(None)
+nb.nb_server_params_default(None)
+bad = {k: v for k, v in calls.items() if v != E}
+print("checked", len(calls), "bad", bad)
+sys.exit(1 if bad else 0)
+"""
+
+
 def test_null_handles_are_rejected(lib):
-    from paper_1003_3896_gb300 import nbsym
-    assert nbsym.nb_step(None, 2, 0.1, 1) == nbsym.NB_EINVAL
-    assert nbsym.nb_accel(None, None) == nbsym.NB_EINVAL
-    assert nbsym.nb_size(None) == nbsym.NB_EINVAL
-    nbsym.nb_destroy(None)
+    """Every entry point that takes a context, a server, parameters or an
+    output pointer returns NB_EINVAL for NULL without touching the device, and
+    the destroy / defaults calls are NULL-safe.  Run in a child process, so a
+    missing check shows as a crash report instead of ending the test run."""
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, "-c", NULL_CALLS % ROOT], capture_output=True,
+                       text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "checked 31 bad {}" in r.stdout
 
 
 def test_oracle_is_not_on_the_product_path():
