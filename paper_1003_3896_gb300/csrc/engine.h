@@ -16,6 +16,10 @@ namespace nb {
 int set_error(int code, const char *fmt, ...);
 const char *last_error();
 
+// Validation of nb_params (nb_create's rules): NB_OK, or NB_EINVAL with the
+// message set.
+int check_nb_params(const nb_params *p);
+
 #define NB_TRY(call)                                                                       \
     do {                                                                                   \
         cudaError_t e_ = (call);                                                           \

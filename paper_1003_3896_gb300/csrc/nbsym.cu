@@ -259,6 +259,11 @@ int create_common(const nb_params *p, int64_t cap, const int64_t *sizes, int64_t
 
 }  // namespace
 
+namespace nb {
+// The parameter checks of nb_create, shared with the no-allocation entry point.
+int check_nb_params(const nb_params *p) { return check_params(p); }
+}  // namespace nb
+
 extern "C" {
 
 int nb_abi_version(void) { return NB_ABI_VERSION; }

@@ -25,6 +25,7 @@
 
 #include "nb_internal.cuh"
 #include "../../include/nbsym.h"
+#include "engine.h"
 
 namespace nb {
 namespace {
@@ -127,15 +128,17 @@ using namespace nb;
 extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_pos,
                                const double *d_mass, double *d_acc_out)
 {
-    if (!p || !d_pos || !d_mass || !d_acc_out) return NB_EINVAL;
-    if (n < 1 || n > NA_MAX_N) return NB_EINVAL;
-    if (!(p->G > 0) || !(p->eps >= 0) || p->precision < NB_FP64 || p->precision > NB_DD)
-        return NB_EINVAL;
-    if (p->ext_on && !(p->bd > 0 && p->ab > 0)) return NB_EINVAL;
-    if (!(p->Mbh >= 0) || !(p->eps_bh >= 0)) return NB_EINVAL;
+    if (!p || !d_pos || !d_mass || !d_acc_out)
+        return set_error(NB_EINVAL, "nb_accel_static: NULL argument");
+    if (n < 1 || n > NA_MAX_N)
+        return set_error(NB_EINVAL, "nb_accel_static: n must be in [1, %d]", (int)NA_MAX_N);
+    const int prc = check_nb_params(p);
+    if (prc) return prc;
     int prev = -1;
-    if (cudaGetDevice(&prev) != cudaSuccess) return NB_ECUDA;
-    if (p->device != prev && cudaSetDevice(p->device) != cudaSuccess) return NB_EINVAL;
+    if (cudaGetDevice(&prev) != cudaSuccess)
+        return set_error(NB_ECUDA, "nb_accel_static: no usable CUDA device");
+    if (p->device != prev && cudaSetDevice(p->device) != cudaSuccess)
+        return set_error(NB_EINVAL, "nb_accel_static: bad device %d", p->device);
     int rc = NB_OK;
     do {
         unsigned char *b = nullptr;
@@ -286,5 +289,7 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
         if (launch_accel_out(s, pl.d, ext, d_acc_out, st) != cudaSuccess) rc = NB_ECUDA;
     } while (0);
     if (prev != p->device) cudaSetDevice(prev);
+    if (rc == NB_ECUDA) return set_error(rc, "nb_accel_static: a device call or launch failed");
+    if (rc) return set_error(rc, "nb_accel_static: device %d out of range", p->device);
     return rc;
 }

@@ -180,3 +180,26 @@ def test_traffic_record_keys_on_code_not_comments():
     assert bench.code_digest(src) == bench.code_digest(same)
     assert bench.code_digest(src) != bench.code_digest(other)
     assert len(bench.pair_source_digest()) == 16
+
+
+def test_static_entry_point_validates_like_create(lib):
+    """nb_accel_static applies nb_create's parameter rules and says what was
+    wrong (no stale message from an earlier call), all before the device."""
+    from paper_1003_3896_gb300 import nbsym
+    p = nbsym.Params()
+    nbsym.nb_params_default(C.byref(p))
+    cases = [(16385, {}, "n must be in [1, 16384]"), (0, {}, "n must be in"),
+             (16, {"G": float("inf")}, "G must be finite"),
+             (16, {"eps": float("inf")}, "eps must be finite"),
+             (16, {"ext_on": 1, "Md": float("nan")}, "external field needs"),
+             (16, {"precision": 9}, "precision must be")]
+    for n, change, msg in cases:
+        q = nbsym.Params()
+        C.pointer(q)[0] = p
+        for k, v in change.items():
+            setattr(q, k, v)
+        nbsym.nb_create(None, 16, None)          # leaves another message behind
+        assert nbsym.nb_accel_static(C.byref(q), n, 8, 8, 8) == nbsym.NB_EINVAL
+        assert msg in nbsym.nb_last_error().decode(), (change, nbsym.nb_last_error())
+    assert nbsym.nb_accel_static(C.byref(p), 16, None, 8, 8) == nbsym.NB_EINVAL
+    assert "NULL" in nbsym.nb_last_error().decode()
