@@ -619,13 +619,13 @@ int nb_get_state_device(nb_ctx *c, double *pos, double *vel)
 
 int64_t nb_size(const nb_ctx *c)
 {
-    if (!c) return NB_EINVAL;
+    if (!c) return set_error(NB_EINVAL, "ctx is NULL");
     return c->n;
 }
 
 int64_t nb_clusters(const nb_ctx *c)
 {
-    if (!c) return NB_EINVAL;
+    if (!c) return set_error(NB_EINVAL, "ctx is NULL");
     return c->batch ? (int64_t)c->sizes.size() : 1;
 }
 

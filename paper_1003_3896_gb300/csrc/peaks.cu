@@ -9,6 +9,7 @@
 
 #include "nb_internal.cuh"
 #include "../../include/nbsym.h"
+#include "engine.h"
 
 namespace {
 
@@ -152,10 +153,10 @@ int time_best(F launch, cudaStream_t st, float *ms_out)
 
 extern "C" int nb_measure_peaks(int device, nb_peaks_t *out)
 {
-    if (!out) return NB_EINVAL;
+    if (!out) return nb::set_error(NB_EINVAL, "nb_measure_peaks: out is NULL");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
-        return NB_EINVAL;
+        return nb::set_error(NB_EINVAL, "nb_measure_peaks: no CUDA device %d", device);
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(device);
@@ -190,5 +191,6 @@ extern "C" int nb_measure_peaks(int device, nb_peaks_t *out)
     if (st) cudaStreamDestroy(st);
     if (dummy) cudaFree(dummy);
     cudaSetDevice(prev);
+    if (rc) return nb::set_error(rc, "nb_measure_peaks: a device call or launch failed");
     return rc;
 }
