@@ -4,7 +4,9 @@ Argument marshalling only: every step of the computation runs in the CUDA
 library.  Importing this module loads the library and raises ImportError if
 it has not been built (``paper_1003_3896_gb300.build.build()``); there is no
 fallback.  Device-pointer methods accept either an integer address or any
-object with ``data_ptr()`` (a torch tensor), so torch is never imported here.
+object with ``data_ptr()`` (a torch tensor), so torch is never imported here;
+such objects are checked to be contiguous float64 of sufficient size before
+their address reaches the library.
 """
 from __future__ import annotations
 
@@ -152,6 +154,24 @@ def _addr(x) -> int:
     return int(x.data_ptr())
 
 
+def _dev(x, count: int, what: str) -> int:
+    """Address of device memory for ``count`` float64 values: an integer
+    address is taken as given; an object with ``data_ptr()`` (a torch tensor)
+    must be contiguous float64 with at least ``count`` elements, so that the
+    library never reads or writes past it.  None passes NULL."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "dtype") and "float64" not in str(x.dtype):
+        raise ValueError(f"{what}: float64 expected, got {x.dtype}")
+    if hasattr(x, "is_contiguous") and not x.is_contiguous():
+        raise ValueError(f"{what}: not contiguous")
+    if hasattr(x, "numel") and x.numel() < count:
+        raise ValueError(f"{what}: {x.numel()} elements, {count} needed")
+    return int(x.data_ptr())
+
+
 def _host3(a, n) -> np.ndarray:
     a = np.ascontiguousarray(a, dtype=np.float64)
     if a.size != 3 * n:
@@ -209,8 +229,12 @@ class Context:
         return int(check(nb_clusters(self._h)))
 
     def set_cluster_params(self, eps=None, dt_scale=None):
-        e = None if eps is None else np.ascontiguousarray(eps, dtype=np.float64)
-        d = None if dt_scale is None else np.ascontiguousarray(dt_scale, dtype=np.float64)
+        k = self.clusters
+        e = None if eps is None else np.ascontiguousarray(eps, dtype=np.float64).ravel()
+        d = None if dt_scale is None else np.ascontiguousarray(dt_scale, dtype=np.float64).ravel()
+        for name, a in (("eps", e), ("dt_scale", d)):
+            if a is not None and a.size != k:
+                raise ValueError(f"{name}: {a.size} values for {k} clusters")
         check(nb_set_cluster_params(self._h, None if e is None else _p(e),
                                     None if d is None else _p(d)))
 
@@ -248,7 +272,9 @@ class Context:
         check(nb_load(self._h, n, _p(pos), _p(vel), _p(mass)))
 
     def load_device(self, n: int, pos, vel, mass):
-        check(nb_load_device(self._h, int(n), _addr(pos), _addr(vel), _addr(mass)))
+        n = int(n)
+        check(nb_load_device(self._h, n, _dev(pos, 3 * n, "pos"), _dev(vel, 3 * n, "vel"),
+                             _dev(mass, n, "mass")))
 
     @property
     def n(self) -> int:
@@ -262,7 +288,8 @@ class Context:
         return pos, vel
 
     def get_state_device(self, pos, vel):
-        check(nb_get_state_device(self._h, _addr(pos), _addr(vel)))
+        n = self.n
+        check(nb_get_state_device(self._h, _dev(pos, 3 * n, "pos"), _dev(vel, 3 * n, "vel")))
 
     # -- compute
     def accel(self) -> np.ndarray:
@@ -271,7 +298,7 @@ class Context:
         return out
 
     def accel_device(self, out):
-        check(nb_accel_device(self._h, _addr(out)))
+        check(nb_accel_device(self._h, _dev(out, 3 * self.n, "out")))
 
     def step(self, order: int, dt: float, nsteps: int = 1):
         check(nb_step(self._h, int(order), float(dt), int(nsteps)))

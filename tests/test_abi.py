@@ -203,3 +203,50 @@ def test_static_entry_point_validates_like_create(lib):
         assert msg in nbsym.nb_last_error().decode(), (change, nbsym.nb_last_error())
     assert nbsym.nb_accel_static(C.byref(p), 16, None, 8, 8) == nbsym.NB_EINVAL
     assert "NULL" in nbsym.nb_last_error().decode()
+
+
+class _FakeTensor:
+    """Stands in for a device tensor: only what the binding inspects."""
+
+    def __init__(self, numel, dtype="torch.float64", contiguous=True):
+        self._n, self.dtype, self._c = numel, dtype, contiguous
+
+    def numel(self):
+        return self._n
+
+    def is_contiguous(self):
+        return self._c
+
+    def data_ptr(self):
+        return 0x1000
+
+
+def test_binding_checks_buffers_before_the_library(lib):
+    """Device buffers too small, of another dtype or not contiguous, and
+    per-cluster arrays of the wrong length, are refused by the binding before
+    any pointer reaches the library."""
+    from paper_1003_3896_gb300 import nbsym
+
+    class Sized(nbsym.Context):
+        n = 5
+        clusters = 2
+
+        def __init__(self):
+            self._h = None
+
+    c = Sized()
+    ok = _FakeTensor(15)
+    for bad in (_FakeTensor(14), _FakeTensor(15, "torch.float32"),
+                _FakeTensor(15, contiguous=False)):
+        with pytest.raises(ValueError):
+            c.load_device(5, bad, ok, _FakeTensor(5))
+        with pytest.raises(ValueError):
+            c.accel_device(bad)
+        with pytest.raises(ValueError):
+            c.get_state_device(ok, bad)
+    with pytest.raises(ValueError):
+        c.load_device(5, ok, ok, _FakeTensor(4))
+    with pytest.raises(ValueError):
+        c.set_cluster_params(eps=[0.1, 0.2, 0.3])
+    with pytest.raises(ValueError):
+        c.set_cluster_params(dt_scale=[1.0])
