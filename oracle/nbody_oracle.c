@@ -24,6 +24,25 @@
  *     plus an optional point mass at the galactic centre, Plummer-softened
  *     by eps_bh: the massive black hole of the collision runs of Sect. 6.2,
  *     read as a static central mass.
+ *
+ * Every function is pinned to something other than itself (the CPU tests of
+ * the oracle; the same pins are run against planted mistakes, each of which
+ * must fail one); none is "parity unpinned":
+ *   orc_accel_int     two-body and n-gon ring closed forms, shells, zero net
+ *                     force and torque, translation / rotation / scaling,
+ *                     -grad W by differences, Plummer mean field, 60-digit
+ *                     brute force within a rounding bound;
+ *   orc_accel_int_at  equals orc_accel_int bit for bit on the bodies asked;
+ *   orc_ext_phi, orc_ext_accel(_one)  -grad Phi by differences, limits,
+ *                     symmetries, scaling laws, v_c closed form, 60-digit
+ *                     closed form, black hole = Plummer sphere of its scale;
+ *   orc_accel         pair sum plus field (eq. 3), lone body feels the field;
+ *   orc_energy        two-body closed forms, -grad W and -grad W_ext, virial
+ *                     ratios, 60-digit W;
+ *   orc_torque        closed form, dL/dt = M_ext along a step;
+ *   orc_run           Kepler orbits at orders 2 and 6 against Kepler's
+ *                     equation, energy error scaling, time reversal,
+ *                     conservation laws, straight-line free motion.
  */
 #include <math.h>
 #include <stdint.h>
