@@ -12,7 +12,7 @@ What must hold for every launch the planner can make:
   partial-slot count, which must not exceed the pool's slot capacity (unless
   the grid is one block): a violation would write past the slot planes.
 Checked exhaustively for W, G <= 300, at the 32-bit boundary, and over
-thousands of random ensembles and launch shapes.
+thousands of random ensembles and launch shapes, up to 2^19 - 1 clusters.
 """
 import os
 import shutil
@@ -86,8 +86,11 @@ int main()
         }
     // random ensembles and launch shapes, as the planner builds them
     long long narrow_seen = 0, wide_seen = 0, shrunk = 0;
-    for (int trial = 0; trial < 4000; ++trial) {
-        const int K = trial % 3 == 0 ? 1 : (int)rnd_in(1, 600);
+    for (int trial = 0; trial < 4002; ++trial) {
+        // two trials at the ensemble-size limit's scale: 65536 and 2^19 - 1
+        // clusters of 1-100 bodies; the rest 1 or up to 600 clusters
+        const int K = trial >= 4000 ? (trial == 4000 ? 65536 : (1 << 19) - 1)
+                                    : (trial % 3 == 0 ? 1 : (int)rnd_in(1, 600));
         const int Is[4] = {1, 2, 4, 8};
         const int I = Is[rnd() % 4];
         const int ipb = TILE * I;
@@ -97,7 +100,7 @@ int main()
         std::vector<int64_t> nk(K), uoff(K + 1, 0);
         int64_t max_ntiles = 1;
         for (int k = 0; k < K; ++k) {
-            nk[k] = K == 1 ? rnd_in(1, 1600000) : rnd_in(1, 9000);
+            nk[k] = K == 1 ? rnd_in(1, 1600000) : rnd_in(1, K > 600 ? 100 : 9000);
             const int64_t nt = (nk[k] + TILE - 1) / TILE;
             if (nt > max_ntiles) max_ntiles = nt;
         }
