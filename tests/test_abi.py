@@ -250,3 +250,18 @@ def test_binding_checks_buffers_before_the_library(lib):
         c.set_cluster_params(eps=[0.1, 0.2, 0.3])
     with pytest.raises(ValueError):
         c.set_cluster_params(dt_scale=[1.0])
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """With no built libnbsym.so beside it the binding raises ImportError at
+    import: there is no CPU or library fallback to fall into."""
+    import shutil
+    import subprocess
+    import sys
+    shutil.copy(os.path.join(ROOT, "paper_1003_3896_gb300", "nbsym.py"), tmp_path / "nbsym.py")
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "try:\n    import nbsym\nexcept ImportError as e:\n    print('ImportError:', e)\n"
+            "else:\n    print('imported')\n") % str(tmp_path)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.startswith("ImportError:") and "libnbsym.so is missing" in r.stdout
