@@ -113,6 +113,7 @@ def _f64(a, shape=None) -> np.ndarray:
 
 
 def set_threads(n: int) -> None:
+    """OpenMP threads the oracle uses (results do not depend on it)."""
     _load().orc_set_threads(int(n))
 
 
@@ -145,12 +146,15 @@ def accel_int_at(pos, mass, idx, G: float = 1.0, eps: float = 0.0) -> np.ndarray
 
 
 def ext_phi(p: Params, x) -> float:
+    """Potential Phi(x) per unit mass of the external field of eq. 3 (disk +
+    bulge + optional central point mass); a_ext = -grad Phi."""
     x = _f64(x, (3,))
     pc = p._c()
     return float(_load().orc_ext_phi(C.byref(pc), _ptr(x)))
 
 
 def ext_accel(p: Params, pos) -> np.ndarray:
+    """External acceleration -grad Phi (eq. 3's field term) at each row of pos."""
     pos = _f64(pos).reshape(-1, 3)
     out = np.empty_like(pos)
     pc = p._c()
@@ -180,6 +184,9 @@ class Energy:
 
 
 def energy(pos, vel, mass, p: Params) -> Energy:
+    """Diagnostics of Sect. 5.1: K, the softened pair energy W of eq. 4,
+    W_ext = sum m Phi, E = K + W + W_ext (whose relative change is eq. 9),
+    momentum P and angular momentum L (eq. 10)."""
     mass = _f64(mass).ravel()
     n = mass.size
     pos = _f64(pos, (n, 3))
@@ -191,6 +198,7 @@ def energy(pos, vel, mass, p: Params) -> Energy:
 
 
 def torque(pos, mass, p: Params) -> np.ndarray:
+    """External torque of eq. 8, sum m_i r_i x a_ext(r_i)."""
     mass = _f64(mass).ravel()
     n = mass.size
     pos = _f64(pos, (n, 3))
@@ -201,6 +209,8 @@ def torque(pos, mass, p: Params) -> np.ndarray:
 
 
 def si6a_weights() -> np.ndarray:
+    """Stage weights (w0, w1, w2, w3) of the sixth-order composition of
+    Sect. 3.1, applied in the order w3 w2 w1 w0 w1 w2 w3."""
     w = np.empty(4)
     _load().orc_si6a_weights(_ptr(w))
     return w
