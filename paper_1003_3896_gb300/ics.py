@@ -139,7 +139,8 @@ def plummer(n: int, seed: int, a: float = 1.0, total_mass: float = 1.0,
         mass = np.full(n, total_mass / n)
     else:
         mass = np.asarray(masses, dtype=np.float64).copy()
-        assert mass.shape == (n,)
+        if mass.shape != (n,):
+            raise ValueError(f"masses has shape {mass.shape}, expected ({n},)")
     if com_frame:
         pos, vel = _com_frame(pos, vel, mass)
     return np.ascontiguousarray(pos), np.ascontiguousarray(vel), mass
