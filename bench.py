@@ -14,7 +14,9 @@ Under torchrun each rank integrates its own independent cluster (seed =
 rank): no collective on the data path (weak scaling).
 
 ``--impl reference`` times the CPU oracle on the host cores instead, on a
-bounded sample of the same workload (bodies x all N sources per step).
+bounded sample of the same workload (bodies x all N sources per step); with
+``--workload`` it does the same for that workload (bench_workloads.py).
+Under torchrun only rank 0 runs it.
 """
 from __future__ import annotations
 
