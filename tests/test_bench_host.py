@@ -64,3 +64,21 @@ def test_traffic_quoted_only_for_the_captured_shape():
     assert bench.pair_traffic(t["n"], "fp32", shape) is None
     assert bench.pair_traffic(t["n"], t["precision"], {**shape, "blocks_per_sm": 6}) is None
     assert bench.pair_traffic(t["n"], t["precision"], {**shape, "bodies_per_thread": 4}) is None
+
+
+def test_error_statistics_of_the_accuracy_sweep():
+    """Global relative RMS plus per-body median and 99th percentile of the
+    relative error; a body with a zero reference is left out of the latter."""
+    import numpy as np
+    import bench_workloads as bw
+    ref = np.ones((101, 3))
+    e = np.linspace(0.0, 1e-6, 100)
+    a = ref.copy()
+    a[:100] *= (1 + e)[:, None]
+    ref[100] = 0.0
+    a[100] = 1e-3
+    s = bw._err_stats(a, ref)
+    assert abs(s["per_body_median"] - np.median(e)) < 1e-15
+    assert abs(s["per_body_p99"] - np.percentile(e, 99)) < 1e-15
+    want = np.sqrt(((a - ref) ** 2).sum() / (ref ** 2).sum())
+    assert abs(s["rel_rms"] - want) <= 1e-15 * want
