@@ -30,7 +30,7 @@
 extern "C" {
 #endif
 
-#define NB_ABI_VERSION 2
+#define NB_ABI_VERSION 3
 
 /* Opaque context: device state of one particle system plus its buffers,
  * stream, captured step graphs and launch configuration.  Library-owned. */
@@ -59,9 +59,15 @@ typedef struct nb_ctx nb_ctx;
  *             the coordinate difference (Sect. 5.2).
  *  NB_DS_FULL -- as NB_DS but the double-single coordinate difference is
  *             formed for every pair, as the paper's DSP code does.
+ *  NB_DS_NEAR -- NB_DS in its two-pass form (float pairs plus the close-pair
+ *             pass) at every size: NB_DS without the switch to NB_DS_FULL on
+ *             small sets.  Same arithmetic and tolerance as NB_DS on large
+ *             sets; lets a caller (or a test) run that form on systems small
+ *             enough to check step by step against a slow reference.
  * In every mode the state (positions, velocities), the kick/drift update,
  * the external field and the energy diagnostic are double precision. */
-enum nb_precision { NB_FP64 = 0, NB_DS = 1, NB_FP32 = 2, NB_DS_FULL = 3, NB_DD = 4 };
+enum nb_precision { NB_FP64 = 0, NB_DS = 1, NB_FP32 = 2, NB_DS_FULL = 3, NB_DD = 4,
+                    NB_DS_NEAR = 5 };
 
 enum nb_status {
     NB_OK = 0,
@@ -98,7 +104,7 @@ typedef struct {
                           pass runs beside the pair kernel; every call joins
                           it back into this stream (events, captured into the
                           step graphs), so work is ordered on this stream */
-    double near_frac;  /* NB_DS only: pairs closer than near_frac * R_rms /
+    double near_frac;  /* NB_DS, NB_DS_NEAR: pairs closer than near_frac * R_rms /
                           N^{1/3} (R_rms = mass-weighted rms radius about the
                           centre of mass, so the radius scales with the mean
                           spacing) get the double-single coordinate

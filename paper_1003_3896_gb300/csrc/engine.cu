@@ -376,7 +376,7 @@ int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan
 int plan_mode(const ClusterSet &C, int precision)
 {
     const int m = mode_of(precision);
-    if (m != PM_DS_NEAR) return m;
+    if (m != PM_DS_NEAR || precision == NB_DS_NEAR) return m;
     double pairs = 0;
     for (int32_t k = 0; k < C.K; ++k) pairs += (double)C.nk[k] * (double)C.nk[k];
     return pairs <= DS_FULL_MAX_PAIRS ? PM_DS_FULL : PM_DS_NEAR;
@@ -406,7 +406,7 @@ DevState view(const Pool &P, const ClusterSet &C, int precision)
     s.ng_slot = C.ng_slot;
     s.ng_rank = C.ng_rank;
     s.flag = C.flag;
-    if (precision != NB_DS) s.corr = nullptr;
+    if (precision != NB_DS && precision != NB_DS_NEAR) s.corr = nullptr;
     return s;
 }
 

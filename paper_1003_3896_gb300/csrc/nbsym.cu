@@ -73,9 +73,9 @@ int check_params(const nb_params *p)
     if (!finite_pos(p->G)) return set_error(NB_EINVAL, "G must be finite and > 0");
     if (!std::isfinite(p->eps) || p->eps < 0)
         return set_error(NB_EINVAL, "eps must be finite and >= 0");
-    if (p->precision < NB_FP64 || p->precision > NB_DD)
-        return set_error(NB_EINVAL,
-                         "precision must be NB_FP64, NB_DS, NB_FP32, NB_DS_FULL or NB_DD");
+    if (p->precision < NB_FP64 || p->precision > NB_DS_NEAR)
+        return set_error(NB_EINVAL, "precision must be NB_FP64, NB_DS, NB_FP32, NB_DS_FULL, "
+                                    "NB_DD or NB_DS_NEAR");
     if (p->ext_on) {
         if (!std::isfinite(p->Md) || p->Md < 0 || !std::isfinite(p->Mb) || p->Mb < 0 ||
             !std::isfinite(p->ad) || p->ad < 0 || !finite_pos(p->bd) || !finite_pos(p->ab))
@@ -632,7 +632,7 @@ int64_t nb_clusters(const nb_ctx *c)
 int nb_set_precision(nb_ctx *c, int precision)
 {
     if (!c) return set_error(NB_EINVAL, "ctx is NULL");
-    if (precision < NB_FP64 || precision > NB_DD)
+    if (precision < NB_FP64 || precision > NB_DS_NEAR)
         return set_error(NB_EINVAL, "bad precision");
     DeviceGuard dg(c->p.device);
     c->p.precision = precision;

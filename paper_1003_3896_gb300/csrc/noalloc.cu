@@ -212,6 +212,7 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
                   : p->precision == NB_FP32 ? PM_FP32
                   : p->precision == NB_DS_FULL ? PM_DS_FULL
                   : p->precision == NB_DD ? PM_DD
+                  : p->precision == NB_DS_NEAR ? PM_DS_NEAR
                   : (double)n * (double)n <= DS_FULL_MAX_PAIRS ? PM_DS_FULL : PM_DS_NEAR;
         pl.I = pl.mode == PM_FP64 ? 1 : 2;
         const int ipb = TILE * pl.I;

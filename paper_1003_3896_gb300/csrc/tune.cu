@@ -116,7 +116,7 @@ int tune_load(const char *path, int64_t *loaded)
         const int r =
             std::fscanf(f, "%d %d %d %lld %lld %d %d %d", &sms, &prec, &K, &n, &mt, &I, &jt, &b);
         if (r == EOF) break;
-        if (r != 8 || sms <= 0 || prec < NB_FP64 || prec > NB_DD || K <= 0 || n <= 0 ||
+        if (r != 8 || sms <= 0 || prec < NB_FP64 || prec > NB_DS_NEAR || K <= 0 || n <= 0 ||
             mt <= 0) {
             std::fclose(f);
             return set_error(NB_EINVAL, "%s: malformed entry %lld", path, (long long)count + 1);

@@ -22,9 +22,9 @@ if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with paper_1003_3896_gb300.build.build()")
 _lib = C.CDLL(LIB_PATH)
 
-NB_FP64, NB_DS, NB_FP32, NB_DS_FULL, NB_DD = 0, 1, 2, 3, 4
+NB_FP64, NB_DS, NB_FP32, NB_DS_FULL, NB_DD, NB_DS_NEAR = 0, 1, 2, 3, 4, 5
 PRECISIONS = {"fp64": NB_FP64, "ds": NB_DS, "fp32": NB_FP32, "ds_full": NB_DS_FULL,
-              "dd": NB_DD}
+              "dd": NB_DD, "ds_near": NB_DS_NEAR}
 NB_OK, NB_EINVAL, NB_ENOMEM, NB_ECUDA, NB_ESTATE, NB_ETIMEOUT, NB_ENONFINITE = 0, -1, -2, -3, -4, -5, -6
 STATUS_NAMES = {0: "NB_OK", -1: "NB_EINVAL", -2: "NB_ENOMEM", -3: "NB_ECUDA", -4: "NB_ESTATE",
                 -5: "NB_ETIMEOUT", -6: "NB_ENONFINITE"}

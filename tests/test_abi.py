@@ -42,7 +42,7 @@ def test_every_declared_symbol_exported(lib):
 
 def test_abi_version_and_defaults(lib):
     from paper_1003_3896_gb300 import nbsym
-    assert nbsym.nb_abi_version() == 2
+    assert nbsym.nb_abi_version() == 3
     p = nbsym.Params()
     nbsym.nb_params_default(C.byref(p))
     assert p.G == 1.0 and p.eps == 0.0 and p.precision == nbsym.NB_DS

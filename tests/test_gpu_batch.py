@@ -125,6 +125,41 @@ def test_batch_steps_equal_alone_runs(nbs, orc, prec):
         off += n
 
 
+def test_batch_two_pass_steps_match_oracle_and_alone(nbs, orc):
+    """A set above the near-pass threshold (sum of N_k^2 > 2^27: one
+    12000-body cluster among small ones), so the batched step graph runs the
+    two-pass mixed form (pair kernel plus near-pair pass on the side stream)
+    with per-cluster frames and near radii: 4 SI6A steps with per-cluster
+    softening and step scale, every cluster's positions against the oracle
+    and against the cluster stepped alone, within the mixed bar 1e-6."""
+    sizes = [700, 12000, 1, 3000, 129]
+    cl = clusters(sizes, base_seed=250)
+    pos, vel, m = concat(cl)
+    eps = [c[3] for c in cl]
+    scale = [1.0, 1.0, 2.0, 0.5, 1.5]
+    dt = 1.0 / 512
+    with nbs.Context(sizes=sizes, precision="ds") as b:
+        b.set_cluster_params(eps=eps, dt_scale=scale)
+        b.load(pos, vel, m)
+        b.accel()
+        b.prof_enable(True)
+        b.accel()
+        assert b.prof_read()["kernel_launches"] == 7   # pair, near pass (5), output
+        b.prof_enable(False)
+        b.step(6, dt, 4)
+        x, v = b.get_state()
+    off = 0
+    for k, ((p, vv, mm, e), n) in enumerate(zip(cl, sizes)):
+        rx, rv = orc.run(p, vv, mm, orc.Params(eps=e), 6, dt * scale[k], 4)
+        assert np.abs(x[off:off + n] - rx).max() <= 1e-6, (k, np.abs(x[off:off + n] - rx).max())
+        with nbs.Context(n, eps=e, precision="ds") as c:
+            c.load(p, vv, mm)
+            c.step(6, dt * scale[k], 4)
+            xa, _ = c.get_state()
+        assert np.abs(x[off:off + n] - xa).max() <= 1e-6
+        off += n
+
+
 def test_batch_energy_totals(nbs, orc):
     cl = clusters(SIZES[:5], base_seed=300)
     pos, vel, m = concat(cl)

@@ -34,6 +34,20 @@ def rel_rms(a, ref):
     return math.sqrt(((a - ref) ** 2).sum() / (ref ** 2).sum())
 
 
+# Per-body bars on e_i = |a_i - a_ref,i| / max(|a_ref,i|, 0.1 rms|a_ref|) (the
+# floor keeps bodies where the sum cancels to |a| ~ 0 from dividing by
+# nothing): the mixed forms 5e-6 (twice the worst measured, 2.5e-6; a body
+# whose close pairs miss the double-single correction exceeds 1e-5), FP64 and
+# float-float 1e-11 (worst measured 3.8e-12).  Pure float has no per-body bar.
+PER_BODY = {"fp64": 1e-11, "dd": 1e-11, "ds": 5e-6, "ds_full": 5e-6, "ds_near": 5e-6}
+
+
+def per_body_max(a, ref):
+    rms = math.sqrt((ref ** 2).sum(1).mean())
+    err = np.sqrt(((a - ref) ** 2).sum(1))
+    return float((err / np.maximum(np.sqrt((ref ** 2).sum(1)), 0.1 * rms)).max())
+
+
 def ext_params(orc, eps, ext_on):
     return orc.Params(G=1.0, eps=eps, ext_on=ext_on)
 
@@ -358,6 +372,8 @@ def test_c2_full_size_sampled(nbs, orc):
             a = c.accel()[idx] - ext
             err = rel_rms(a, ref)
             assert err <= TOL[prec], (prec, err)
+            if prec in PER_BODY:
+                assert per_body_max(a, ref) <= PER_BODY[prec], (prec, per_body_max(a, ref))
 
 
 def test_c3_full_size_sampled(nbs, orc):
@@ -373,6 +389,8 @@ def test_c3_full_size_sampled(nbs, orc):
             c.set_precision(prec)
             a = c.accel()[idx]
             assert rel_rms(a, ref) <= TOL[prec], (prec, rel_rms(a, ref))
+            if prec in PER_BODY:
+                assert per_body_max(a, ref) <= PER_BODY[prec], (prec, per_body_max(a, ref))
 
 
 def test_near_pair_correction_is_what_makes_mixed_accurate(nbs, orc):
@@ -386,13 +404,19 @@ def test_near_pair_correction_is_what_makes_mixed_accurate(nbs, orc):
     pos, vel, m = system(n, seed=29, offset=True)
     eps = ics.paper_softening(n)
     ref = orc.accel(pos, m, ext_params(orc, eps, True))
-    err = {}
+    err, body = {}, {}
     for nf in (1e-9, 0.0, 1e4):
         with nbs.Context(n, eps=eps, precision="ds", ext_on=True, near_frac=nf) as c:
             c.load(pos, vel, m)
-            err[nf] = rel_rms(c.accel(), ref)
+            a = c.accel()
+        err[nf] = rel_rms(a, ref)
+        body[nf] = per_body_max(a, ref)
     assert err[0.0] <= TOL["ds"] and err[1e4] <= TOL["ds"], err
     assert err[1e-9] > 2 * err[0.0], err
+    # every body, not only the norm: the bodies the pass corrects are within
+    # the per-body bar with it and far outside without it
+    assert body[0.0] <= PER_BODY["ds"] and body[1e4] <= PER_BODY["ds"], body
+    assert body[1e-9] > 2 * PER_BODY["ds"], body
 
 
 def test_measured_peaks_are_plausible(nbs):

@@ -63,6 +63,33 @@ def test_each_result_same_alone_and_in_mix(nbs):
         assert np.abs(v - va).max() <= 10 * tol
 
 
+def test_two_pass_group_same_alone_and_in_mix(nbs, orc):
+    """A 12000-body mixed job makes its group's set large enough (sum of N^2
+    above 2^27) for the two-pass form, so the served step graph runs the
+    near-pair pass; the other jobs of the group share it while they last.
+    Every result equals the job run alone (its own context) within the mixed
+    bar, and the large job matches the oracle's 3 SI6A steps."""
+    jobs = [(12000, 6, 1 / 512, 3), (900, 6, 1 / 512, 5), (2500, 6, 1 / 256, 2)]
+    with nbs.Server(hbm_budget_bytes=2e9, max_jobs=8) as srv:
+        ids = []
+        for k, (n, order, dt, steps) in enumerate(jobs):
+            pos, vel, m, eps = ic(n, 950 + k)
+            ids.append(srv.submit(pos, vel, m, order, dt, steps, precision="ds", eps=eps))
+        st = [srv.wait(j, 300) for j in ids]
+        assert all(s["state"] == nbs.JOB_DONE for s in st), st
+        results = [srv.result(j) for j in ids]
+    for k, ((n, order, dt, steps), (x, v)) in enumerate(zip(jobs, results)):
+        pos, vel, m, eps = ic(n, 950 + k)
+        with nbs.Context(n, eps=eps, precision="ds") as c:
+            c.load(pos, vel, m)
+            c.step(order, dt, steps)
+            xa, _ = c.get_state()
+        assert np.abs(x - xa).max() <= 1e-6, (k, np.abs(x - xa).max())
+        if k == 0:
+            rx, _ = orc.run(pos, vel, m, orc.Params(eps=eps), order, dt, steps)
+            assert np.abs(x - rx).max() <= 1e-6, np.abs(x - rx).max()
+
+
 def test_admission_respects_budget_and_slots(nbs):
     """A budget for about two 1000-body jobs: never more than two resident,
     every job still completes in arrival order of admission."""

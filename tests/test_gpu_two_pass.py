@@ -1,0 +1,204 @@
+"""The headline mixed path, two passes (float pair kernel plus the near-pair
+correction, NB_DS above 2^27 pairs per evaluation, or NB_DS_NEAR at any
+size), stepped against the CPU oracle: positions after 4 steps of both
+schemes (Sect. 3.1) within 1e-6, long-run |dE/E| within twice the oracle's,
+and the error of every compared body, not only the global norm.
+
+Each test first checks that the context really runs the two-pass form: one
+force evaluation then enqueues the pair kernel, the five kernels of the
+near-pair pass and the output kernel (7), where the one-pass forms enqueue 2.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1003_3896_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+POS_TOL = 1e-6        # positions after 4 steps, mixed arithmetic (absolute, max norm)
+
+
+@pytest.fixture(scope="module")
+def nbs():
+    from paper_1003_3896_gb300 import build
+    build.build()
+    from paper_1003_3896_gb300 import nbsym
+    return nbsym
+
+
+def rel_rms(a, ref):
+    return math.sqrt(((a - ref) ** 2).sum() / (ref ** 2).sum())
+
+
+def orbit(n, seed):
+    pos, vel, m = ics.plummer(n, seed)
+    pos, vel = ics.place_on_orbit(pos, vel)
+    return pos, vel, m, ics.paper_softening(n)
+
+
+def assert_two_pass(c):
+    """One evaluation enqueues 7 kernels in the two-pass form (pair, five of
+    the near-pair pass, output), 2 otherwise."""
+    c.accel()                        # leaves the float planes current
+    c.prof_enable(True)
+    c.accel()
+    k = c.prof_read()["kernel_launches"]
+    c.prof_enable(False)
+    assert k == 7, f"not the two-pass form: {k} kernels per evaluation"
+
+
+@pytest.mark.parametrize("order", [2, 6])
+@pytest.mark.parametrize("n,prec", [(16384, "ds"), (2500, "ds_near"), (4099, "ds_near")])
+def test_two_pass_four_steps_positions(nbs, orc, order, n, prec):
+    """4 steps of dt = 1/256 in the disk + bulge field, cluster at R = 50:
+    NB_DS at N = 16384 (above the size where it switches to the every-pair
+    difference) and NB_DS_NEAR at small N with a ragged last tile."""
+    pos, vel, m, eps = orbit(n, 31 + n)
+    dt = 1.0 / 256
+    with nbs.Context(n, eps=eps, precision=prec, ext_on=True) as c:
+        c.load(pos, vel, m)
+        assert_two_pass(c)
+        c.step(order, dt, 4)
+        x, v = c.get_state()
+    rx, rv = orc.run(pos, vel, m, orc.Params(eps=eps, ext_on=True), order, dt, 4)
+    assert np.abs(x - rx).max() <= POS_TOL, np.abs(x - rx).max()
+    assert np.abs(v - rv).max() <= 50 * POS_TOL
+
+
+@pytest.mark.parametrize("order", [2, 6])
+def test_c2_four_steps_full_size(nbs, orc, order):
+    """The benchmark's workload itself: N = 65536 Plummer at R = 50 in the
+    disk + bulge field, paper softening, dt = 1/256, in the launch shape the
+    benchmark times; every body's position after 4 steps against the oracle's
+    full run."""
+    n = 65536
+    pos, vel, m, eps = orbit(n, 0)
+    dt = 1.0 / 256
+    with nbs.Context(n, eps=eps, precision="ds", ext_on=True) as c:
+        c.load(pos, vel, m)
+        assert_two_pass(c)
+        assert c.pair_shape()["grid"] > 3 * 152
+        c.step(order, dt, 4)
+        x, v = c.get_state()
+    rx, rv = orc.run(pos, vel, m, orc.Params(eps=eps, ext_on=True), order, dt, 4)
+    assert np.abs(x - rx).max() <= POS_TOL, np.abs(x - rx).max()
+    assert np.abs(v - rv).max() <= 50 * POS_TOL
+
+
+def test_two_pass_long_run_energy(nbs, orc):
+    """40 SI6A steps of dt = 1/256 at N = 16384 in the field: |dE/E| within
+    twice the oracle's own over the same run (energies of both end states by
+    the oracle's FP64 diagnostic)."""
+    n = 16384
+    pos, vel, m, eps = orbit(n, 3)
+    p = orc.Params(eps=eps, ext_on=True)
+    e0 = orc.energy(pos, vel, m, p).E
+    rx, rv = orc.run(pos, vel, m, p, 6, 1 / 256, 40)
+    de_ref = abs((orc.energy(rx, rv, m, p).E - e0) / e0)
+    with nbs.Context(n, eps=eps, precision="ds", ext_on=True) as c:
+        c.load(pos, vel, m)
+        assert_two_pass(c)
+        c.step(6, 1 / 256, 40)
+        x, v = c.get_state()
+        g1 = c.energy().E
+    de = abs((orc.energy(x, v, m, p).E - e0) / e0)
+    assert de <= 2 * de_ref + 2e-14, (de, de_ref)
+    # the library's own diagnostic of its end state agrees with the oracle's
+    assert abs(g1 - orc.energy(x, v, m, p).E) <= 1e-12 * abs(e0)
+
+
+def test_two_pass_resumes_bit_identically(nbs):
+    """Frames and near radius are recomputed at every step from the state
+    alone: 2 + 2 steps from a saved state equal 4 steps, bit for bit."""
+    n = 16384
+    pos, vel, m, eps = orbit(n, 9)
+    with nbs.Context(n, eps=eps, precision="ds", ext_on=True) as c:
+        c.load(pos, vel, m)
+        c.step(6, 1 / 256, 4)
+        x4, v4 = c.get_state()
+    with nbs.Context(n, eps=eps, precision="ds", ext_on=True) as c:
+        c.load(pos, vel, m)
+        c.step(6, 1 / 256, 2)
+        x2, v2 = c.get_state()
+        c.load(x2, v2, m)
+        c.step(6, 1 / 256, 2)
+        x, v = c.get_state()
+    np.testing.assert_array_equal(x, x4)
+    np.testing.assert_array_equal(v, v4)
+
+
+# ------------------------------------------------------------ per-body error
+
+# Per-body error e_i = |a_i - a_ref,i| / max(|a_ref,i|, 0.1 rms|a_ref|).  The
+# floor keeps bodies near the potential minimum, where the sum cancels to
+# |a| ~ 0, from dividing by nothing.  What the two-pass form leaves on a body
+# is the float rounding of its pair terms and partial sums (a few 2^-24
+# relative to the sum of the terms' magnitudes) plus, for pairs beyond the
+# near radius d_th, the rounding of the frame-relative coordinates (about
+# 2^-24 |x - c| / d per pair); measured worst over the bodies compared here:
+# 0.9e-6 to 1.3e-6 on the orbit systems, 2.5e-6 on the Salpeter sweep.
+# Without the correction a body dominated by one close neighbour (d << d_th)
+# keeps the whole 2^-24 |x - c| / d: measured worst 1.8e-5 (N = 16384) to
+# 1.1e-4 (N = 262144).  The bar sits at twice the worst correct value.
+PER_BODY_TOL = 5e-6
+
+
+def per_body(a, ref, rms):
+    err = np.sqrt(((a - ref) ** 2).sum(1))
+    return err / np.maximum(np.sqrt((ref ** 2).sum(1)), 0.1 * rms)
+
+
+def close_bodies(pos, k):
+    """Indices of the k bodies with the nearest neighbours (the ones the
+    near-pair pass corrects)."""
+    spatial = pytest.importorskip("scipy.spatial")
+    d, _ = spatial.cKDTree(pos).query(pos, 2)
+    return np.argsort(d[:, 1])[:k]
+
+
+@pytest.mark.parametrize("n,seed", [(16384, 0), (65536, 0)])
+def test_per_body_error_bound(nbs, orc, n, seed):
+    """Orbit geometry (cluster at R = 50, the field on): 300 random bodies
+    plus the 100 with the closest neighbours.  The two-pass result holds
+    every compared body to PER_BODY_TOL (and the global norm to 1e-6); with
+    the near radius shrunk to nothing (the correction removed) the close
+    bodies exceed twice the bar, so the check sees a correction that is
+    missing, has the wrong sign (twice the uncorrected error) or misses its
+    closest pairs."""
+    pos, vel, m, eps = orbit(n, seed)
+    rng = np.random.default_rng(7)
+    close = close_bodies(pos, 100)
+    idx = np.unique(np.concatenate([rng.choice(n, 300, replace=False), close]))
+    ref = orc.accel_int_at(pos, m, idx, 1.0, eps)
+    ext = orc.ext_accel(orc.Params(eps=eps, ext_on=True), pos[idx])
+    rms = math.sqrt((ref ** 2).sum(1).mean())
+    worst = {}
+    for nf in (0.0, 1e-9):
+        with nbs.Context(n, eps=eps, precision="ds_near", ext_on=True, near_frac=nf) as c:
+            c.load(pos, vel, m)
+            a = c.accel()[idx] - ext
+        worst[nf] = (per_body(a, ref, rms).max(), rel_rms(a, ref))
+    assert worst[0.0][0] <= PER_BODY_TOL, worst
+    assert worst[0.0][1] <= 1e-6, worst
+    assert worst[1e-9][0] > 2 * PER_BODY_TOL, worst
+
+
+def test_per_body_error_c3_sweep(nbs, orc):
+    """N = 262144 with Salpeter masses, eps = 1e-4 (the accuracy sweep's
+    system): every compared body of the two-pass result within the per-body
+    bar, the every-pair double-single form too."""
+    n = 262144
+    pos, vel, m = ics.plummer(n, 0, masses=ics.salpeter_masses(n, 0))
+    rng = np.random.default_rng(8)
+    idx = np.unique(np.concatenate([rng.choice(n, 250, replace=False), close_bodies(pos, 50)]))
+    ref = orc.accel_int_at(pos, m, idx, 1.0, 1e-4)
+    rms = math.sqrt((ref ** 2).sum(1).mean())
+    with nbs.Context(n, eps=1e-4, precision="ds") as c:
+        c.load(pos, vel, m)
+        assert_two_pass(c)
+        for prec in ("ds", "ds_full"):
+            c.set_precision(prec)
+            e = per_body(c.accel()[idx], ref, rms)
+            assert e.max() <= PER_BODY_TOL, (prec, e.max())
