@@ -416,11 +416,14 @@ def main():
     kernel = {"fp64": "pair_fp64_kernel", "dd": "pair_ff_kernel"}.get(args.precision,
                                                                        "pair_sp_kernel")
     if args.precision == "fp64":
-        # the FP64 pipe: its nominal dense rate for this GPU, and the DFMA
-        # rate measured in the same run
-        peak, peak_basis = FP64_PEAK_TFLOPS, "nominal FP64 of GB300 (1.25 TFLOP/s)"
-        frac_clock = achieved / peak * 2070.0 / sustained_mhz
-        frac_meas = achieved / peaks["dfma_tflops"]
+        # the FP64 pipe: the DFMA rate measured in the same run is the
+        # ceiling (this GPU's DFMA issue measures ~83% of the nominal 1.25
+        # TFLOP/s); the nominal fraction is reported beside it
+        peak = peaks["dfma_tflops"]
+        peak_basis = (f"FP64 DFMA measured in this run ({peak:.3f} TFLOP/s; nominal "
+                      f"{FP64_PEAK_TFLOPS} TFLOP/s gives frac_of_nominal_fp64)")
+        frac_clock = achieved / FP64_PEAK_TFLOPS * 2070.0 / sustained_mhz
+        frac_meas = achieved / FP64_PEAK_TFLOPS
     else:
         peak = fp32_peak_tflops(sms, 2070.0)
         peak_basis = f"{sms} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max clock)"
@@ -439,7 +442,7 @@ def main():
                      "kernel": f"{kernel} ({args.precision})",
                      "peak_basis": peak_basis,
                      "frac_at_sampled_clock": frac_clock,
-                     ("frac_of_measured_fp64" if args.precision == "fp64"
+                     ("frac_of_nominal_fp64" if args.precision == "fp64"
                       else "frac_of_measured_fp32"): frac_meas,
                      "measured_peaks": peaks,
                      "pair_kernel_ms_mean": prof["pair_ms"] / max(1, prof["pair_launches"]),

@@ -267,22 +267,24 @@ int nb_measure_peaks(int device, nb_peaks_t *out);
  * never pay the implicit device synchronisation of cudaMalloc/cudaFree, and
  * plug-in environments that forbid device allocation after start-up.
  *
- * Computes the same accelerations as nb_accel (internal sum of eq. 5 in the
- * arithmetic p->precision selects, plus the external field when p->ext_on)
- * for n bodies given as device pointers: d_pos (n rows of x, y, z), d_mass
- * (n), result to d_acc_out (n rows), all caller-owned memory on p->device.
- * Work is enqueued on p->stream (NULL = the legacy default stream); the call
- * returns without synchronising, so the caller synchronises that stream
- * before reading d_acc_out.  No non-finite check is made.
+ * Computes the same accelerations as nb_accel (in the arithmetic
+ * p->precision selects, plus the external field when p->ext_on) for n bodies
+ * given as device pointers: d_pos (n rows of x, y, z), d_mass (n), result to
+ * d_acc_out (n rows), all caller-owned memory on p->device.  Work is
+ * enqueued on p->stream (NULL = the legacy default stream); the call returns
+ * without synchronising, so the caller synchronises that stream before
+ * reading d_acc_out.  No non-finite check is made.
  *
  * Limit: 1 <= n <= 16384.  All working memory sits in one static device
  * array of about 7.3 MB that every GPU loading the library keeps until the
  * process exits.  The first call on a device looks up that array's address
- * (cudaGetSymbolAddress) and must come before any stream capture.  Calls
+ * (cudaGetSymbolAddress) and must come before any stream capture; so must
+ * the first call after cudaDeviceReset, which looks it up again.  Calls
  * share the array: calls whose work overlaps on the GPU race, so serialise
  * them.  Calls no cudaMalloc, cudaFree or allocating library routine.
  * Errors: NB_EINVAL (NULL pointer, n out of range, bad parameters or
- * device), NB_ECUDA. */
+ * device), NB_ECUDA (with the runtime's message; a launch error that earlier
+ * work of the caller left pending is reported here too). */
 int nb_accel_static(const nb_params *p, int64_t n, const double *d_pos,
                     const double *d_mass, double *d_acc_out);
 

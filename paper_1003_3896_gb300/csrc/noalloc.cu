@@ -14,13 +14,18 @@
 // Host code cannot use the array's name as a device address (on the host it
 // names a stand-in object), so the first call on each device, with that
 // device current, looks the address up with cudaGetSymbolAddress and caches
-// it.  That first call should therefore come before any stream capture.
+// it beside the device's current context.  That first call should therefore
+// come before any stream capture.  A call that finds another context current
+// (the primary context was torn down by cudaDeviceReset and created anew)
+// looks the address up again, so it too should come before any capture.
 //
 // Every call shares the one array and leaves its contents behind; each call
 // writes every scratch element it later reads (its tables are rebuilt on the
 // device, the non-finite flag is cleared), so nothing leaks from one call into
 // the next.  Calls whose work overlaps on the GPU (different streams, or
 // several host threads) race on the array: serialise them.
+#include <cuda.h>   // CUcontext (types only; the driver call is found at run time)
+
 #include <mutex>
 
 #include "nb_internal.cuh"
@@ -59,16 +64,47 @@ static __device__ __align__(256) unsigned char na_scratch[NA_BYTES];
 constexpr int MAX_DEV = 64;
 std::mutex g_mu;
 unsigned char *g_base[MAX_DEV] = {};
+CUcontext g_ctx[MAX_DEV] = {};
 
-// Device address of na_scratch on the current device (looked up once).
+typedef CUresult (*ctx_get_current_t)(CUcontext *);
+
+// The driver's cuCtxGetCurrent, found once through the runtime (no link-time
+// dependency on the driver library).
+ctx_get_current_t ctx_get_current()
+{
+    static ctx_get_current_t fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<ctx_get_current_t>(f);
+        looked = true;
+    }
+    return fn;
+}
+
+// Device address of na_scratch on the current device: looked up once per
+// device and context, with that device current.  Sets the error message.
 int scratch_base(int dev, unsigned char **out)
 {
-    if (dev < 0 || dev >= MAX_DEV) return NB_EINVAL;
+    if (dev < 0 || dev >= MAX_DEV)
+        return set_error(NB_EINVAL, "nb_accel_static: device %d out of range", dev);
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_base[dev]) {
+    const ctx_get_current_t get = ctx_get_current();
+    CUcontext ctx = nullptr;
+    if (!get || get(&ctx) != CUDA_SUCCESS || !ctx)
+        return set_error(NB_ECUDA, "nb_accel_static: no current CUDA context on device %d", dev);
+    if (!g_base[dev] || g_ctx[dev] != ctx) {
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, na_scratch) != cudaSuccess || !p) return NB_ECUDA;
+        const cudaError_t e = cudaGetSymbolAddress(&p, na_scratch);
+        if (e != cudaSuccess || !p)
+            return set_error(NB_ECUDA, "nb_accel_static: cudaGetSymbolAddress failed: %s",
+                             cudaGetErrorString(e));
         g_base[dev] = static_cast<unsigned char *>(p);
+        g_ctx[dev] = ctx;
     }
     *out = g_base[dev];
     return NB_OK;
@@ -140,12 +176,17 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
     if (p->device != prev && cudaSetDevice(p->device) != cudaSuccess)
         return set_error(NB_EINVAL, "nb_accel_static: bad device %d", p->device);
     int rc = NB_OK;
+    // a failed runtime call: its message is recorded (cudaGetLastError also
+    // returns an error that earlier work of the caller left pending)
+    auto fail = [](const char *what, cudaError_t e) {
+        return set_error(NB_ECUDA, "nb_accel_static: %s failed: %s", what, cudaGetErrorString(e));
+    };
     do {
         unsigned char *b = nullptr;
         rc = scratch_base(p->device, &b);
         if (rc) break;
         if (near_table_size(NA_MAX_N) != NA_H) {
-            rc = NB_ECUDA;
+            rc = set_error(NB_ECUDA, "nb_accel_static: near-pair table size mismatch");
             break;
         }
         cudaStream_t st = (cudaStream_t)p->stream;
@@ -202,9 +243,9 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
         s.diag = reinterpret_cast<double *>(b + OFF_G + sizeof(Frame));
 
         int sms = 0;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) !=
-            cudaSuccess) {
-            rc = NB_ECUDA;
+        cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+        if (e != cudaSuccess) {
+            rc = fail("cudaDeviceGetAttribute", e);
             break;
         }
         PairLaunch pl;
@@ -255,12 +296,15 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
 
         na_tables_kernel<<<1, 32, 0, st>>>(t, n, p->eps, ipb);
         na_unpack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, d_pos, d_mass);
-        if (cudaGetLastError() != cudaSuccess) { rc = NB_ECUDA; break; }
+        if ((e = cudaGetLastError()) != cudaSuccess) {
+            rc = fail("table / unpack launch", e);
+            break;
+        }
         if (pl.mode != PM_FP64) {
             const double nf = p->near_frac > 0 ? p->near_frac : 0.4;
-            if (launch_frame(s, nf, pl.mode == PM_DS_NEAR, st) != cudaSuccess ||
-                launch_split(s, st) != cudaSuccess) {
-                rc = NB_ECUDA;
+            if ((e = launch_frame(s, nf, pl.mode == PM_DS_NEAR, st)) != cudaSuccess ||
+                (e = launch_split(s, st)) != cudaSuccess) {
+                rc = fail("frame / split launch", e);
                 break;
             }
         }
@@ -274,23 +318,22 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
         ht.nk = h_nk;
         ht.ntiles = h_nt;
         ht.eps2f = h_e2;
-        if (launch_pair(s, pl, ht, p->G, st) != cudaSuccess) {
-            rc = NB_ECUDA;
+        if ((e = launch_pair(s, pl, ht, p->G, st)) != cudaSuccess) {
+            rc = fail("pair kernel launch", e);
             break;
         }
         // the mixed mode re-forms near pairs from the double-single difference
         if (pl.mode == PM_DS_NEAR) {
-            if (launch_near_correct(s, p->G, false, st) != cudaSuccess) {
-                rc = NB_ECUDA;
+            if ((e = launch_near_correct(s, p->G, false, st)) != cudaSuccess) {
+                rc = fail("near-pair pass launch", e);
                 break;
             }
         } else {
             s.corr = nullptr;
         }
-        if (launch_accel_out(s, pl.d, ext, d_acc_out, st) != cudaSuccess) rc = NB_ECUDA;
+        if ((e = launch_accel_out(s, pl.d, ext, d_acc_out, st)) != cudaSuccess)
+            rc = fail("output launch", e);
     } while (0);
     if (prev != p->device) cudaSetDevice(prev);
-    if (rc == NB_ECUDA) return set_error(rc, "nb_accel_static: a device call or launch failed");
-    if (rc) return set_error(rc, "nb_accel_static: device %d out of range", p->device);
     return rc;
 }

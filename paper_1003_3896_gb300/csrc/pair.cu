@@ -174,8 +174,9 @@ struct IPairs {
 // bodies (local indices ibase + k * TILE).  MASK zeroes the j == i term
 // (eps = 0, diagonal chunks).  UM (all masses of the cluster equal): the pair
 // term is d / r^3 without m_j, one multiply fewer; the caller scales by m.
-// At P = 4 the chunk stays a loop of four groups of 8 j: fully unrolled, the
-// kernel's code outgrows the instruction cache and runs 30% slower.  PA: the
+// At P = 4 the chunk stays a loop of two groups of 16 j: fully unrolled, the
+// kernel's code outgrows the instruction cache and runs 30% slower, while
+// groups of 8 j left 1% on the table.  PA: the
 // packed pairs evaluated, the first PA of P (a partly filled i-block leaves
 // the others as padding for every lane of the warp; a variant per count keeps
 // each loop fully unrolled, where a runtime bound inside it cost more than the
@@ -185,12 +186,13 @@ __device__ __forceinline__ void chunk_pass(const float4 (*cb)[4], int j0, int ib
                                            IPairs<P> &ip, float eps2)
 {
     const float2 e2 = make_float2(eps2, eps2);
-    constexpr int GU = P >= 4 ? 1 : CH / 8;
+    constexpr int GS = 16;                      // j bodies per unrolled group
+    constexpr int GU = P >= 4 ? 1 : CH / GS;
 #pragma unroll GU
-    for (int g = 0; g < CH / 8; ++g) {
+    for (int g = 0; g < CH / GS; ++g) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int jj = g * 8 + q;
+        for (int q = 0; q < GS; ++q) {
+            const int jj = g * GS + q;
             const float4 A = cb[jj][0];
             const float4 B = cb[jj][1];
             const float2 xx = make_float2(A.x, A.y), yy = make_float2(A.z, A.w);
@@ -233,8 +235,17 @@ __device__ __forceinline__ void chunk_pass(const float4 (*cb)[4], int j0, int ib
 }
 
 // Resident blocks per SM the register allocation is bounded for: 2P bodies per
-// thread trade registers against shared-memory broadcasts per pair.
-__host__ __device__ constexpr int sp_min_blocks(int P) { return P == 1 ? 8 : (P == 2 ? 6 : 3); }
+// thread trade registers against shared-memory broadcasts per pair.  The
+// every-pair double-single mode holds three more packed coordinates per i-pair
+// and a second j-stream word per body, so it gets a looser cap (6 blocks at
+// P = 1, 3 at P = 2); under the caps of the other modes it spilled (12 bytes
+// per thread at P = 1, up to 1.4 KB at P = 2), and 4 blocks at P = 2 still
+// spilled 16 bytes.
+__host__ __device__ constexpr int sp_min_blocks(int P, int MODE)
+{
+    return MODE == PM_DS_FULL ? (P == 1 ? 6 : (P == 2 ? 3 : 2))
+                              : (P == 1 ? 8 : (P == 2 ? 6 : 3));
+}
 
 // KC > 0: the cluster values come from the by-value table tab (K <= KC);
 // KC == 0: from the device tables of c.
@@ -242,7 +253,7 @@ template <int KC>
 using TabOf = ParamTab<KC == 0 ? 1 : KC>;
 
 template <int P, int MODE, int KC, bool UM>
-__global__ void __launch_bounds__(TILE, sp_min_blocks(P)) pair_sp_kernel(
+__global__ void __launch_bounds__(TILE, sp_min_blocks(P, MODE)) pair_sp_kernel(
     const float4 *__restrict__ jd, const float4 *__restrict__ jl,
     const float *__restrict__ xh, const float *__restrict__ yh, const float *__restrict__ zh,
     const float *__restrict__ xl, const float *__restrict__ yl, const float *__restrict__ zl,
