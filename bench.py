@@ -305,8 +305,14 @@ def main():
     ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c4", "c5", "paper", "plunge", "sym"],
                     help="c2 (default): the headline line; the others print their own "
                          "labelled lines (see bench_workloads.py)")
-    ap.add_argument("--jobs", type=int, default=48, help="c5: jobs in the bounded trace")
-    ap.add_argument("--steps-cap", type=int, default=20, help="c5: cap on steps per job")
+    ap.add_argument("--jobs", type=int, default=32,
+                    help="c5: jobs in the bounded trace (the first arrivals)")
+    ap.add_argument("--steps-cap", type=int, default=1000,
+                    help="c5: cap on steps per job (1000, the trace's own upper bound: none)")
+    ap.add_argument("--n-cap", type=int, default=131072,
+                    help="c5: cap on bodies per job (131072, the trace's own upper bound: none)")
+    ap.add_argument("--fp64-kernel", action="store_true",
+                    help="c5: run FP64 jobs on the plain FP64 kernel instead of float-float")
     ap.add_argument("--rates", default="",
                     help="c5: comma-separated arrival rates (jobs/s) to replay the trace at "
                          "after the 200/s run, e.g. 2,4,8 (the rate sweep)")

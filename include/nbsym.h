@@ -324,8 +324,10 @@ int nb_accel_symmetric(nb_ctx *ctx, double *acc_out, double *pair_ms);
  * the occupancy limit the grid is resident at once; above it (up to 6 times
  * that limit) it runs in waves, which evens out SMs whose resident blocks
  * progress at different rates.  nb_tune times every shape this build compiled for
- * the context's current precision on its loaded state (reps launches each,
- * CUDA events on the context's stream), switches the context to the fastest
+ * the context's current precision on its loaded state (reps force evaluations,
+ * the mixed mode's near-pair pass included, and reps kicks each; CUDA events on
+ * the context's stream), switches the context to the shape with the least
+ * evaluation + kick time
  * and records it in a process-wide table keyed by the workload's shape (SM
  * count, precision, cluster count, bodies, widest cluster), which every later
  * context or serving group of the same shape uses.  Two shapes can split the
@@ -339,8 +341,14 @@ typedef struct {
     int j_tile;              /* chosen j bodies per unit: 128, 64 or 32 */
     int candidates;          /* shapes timed */
     int64_t grid;            /* blocks of the chosen shape */
-    double pair_ms;          /* mean pair-launch time of the chosen shape */
+    double pair_ms;          /* mean time of one force evaluation with the
+                                chosen shape: the pair launch, with the mixed
+                                mode's near-pair pass beside it */
     double default_ms;       /* the same for the shape chosen without tuning */
+    double cost_ms;          /* pair_ms plus the mean time of one kick that
+                                sums its partial slots: what shapes are chosen
+                                by */
+    double default_cost_ms;  /* the same for the shape chosen without tuning */
 } nb_tune_t;
 
 /* Tune the context (1 <= reps <= 1000; out may be NULL).  Synchronous; the
@@ -398,10 +406,11 @@ typedef struct {
     double Md, ad, bd, Mb, ab;
     double near_frac;         /* as nb_params (NB_DS jobs) */
     double Mbh, eps_bh;       /* as nb_params */
-    int fp64_via_dd;          /* 1: jobs submitted as NB_FP64 run the NB_DD
-                                 (float-float) arithmetic, which meets the FP64
-                                 tolerance at ~8x the FP64 pipe's rate; 0
-                                 (default): the plain FP64 kernel */
+    int fp64_via_dd;          /* 1 (default): jobs submitted as NB_FP64 run the
+                                 NB_DD (float-float) arithmetic, which meets the
+                                 FP64 tolerance at ~8x the FP64 pipe's rate (this
+                                 GPU's FP64 pipe runs at 1/77 of its FP32 rate);
+                                 0: the plain FP64 kernel */
 } nb_server_params;
 
 typedef struct {
@@ -430,10 +439,18 @@ typedef struct {
     int64_t kernel_launches;  /* kernels the scheduler enqueued */
     int64_t capacity_bodies;  /* pool capacity from the budget */
     double clock_s;           /* server clock now */
+    double pair_ms[3];        /* summed device time of the pair-force launches
+                                 (CUDA events on each group's stream), by
+                                 arithmetic: [0] the FP64 kernel, [1] NB_DS,
+                                 [2] NB_DD (and FP64 jobs run in it).  Groups
+                                 overlap on the device, so a launch's time
+                                 includes the SMs it shared with other groups */
+    double pair_interactions[3]; /* N^2 summed over those launches, same index */
 } nb_server_stats_t;
 
 /* Defaults: device 0, 4 GB budget, 64 jobs, G = 1, field off with the disk +
- * bulge constants of nb_params_default.  NULL-safe. */
+ * bulge constants of nb_params_default, FP64 jobs in float-float
+ * (fp64_via_dd = 1).  NULL-safe. */
 void nb_server_params_default(nb_server_params *p);
 
 /* Allocate the pool and start the scheduler thread.  Errors: NB_EINVAL,

@@ -121,6 +121,7 @@ struct TuneReport {
     int64_t grid = 0;
     int candidates = 0;
     double pair_ms = 0, default_ms = 0;
+    double cost_ms = 0, default_cost_ms = 0;
 };
 TuneKey tune_key(const Pool &P, const ClusterSet &C, int precision);
 bool tune_lookup(const TuneKey &k, PairShape *out);
@@ -131,8 +132,10 @@ int tune_save(const char *path);
 int tune_load(const char *path, int64_t *loaded);
 struct Phys;
 // Time every compiled shape of the precision's pair kernel on the set's
-// current state (reps launches each), remember the fastest for the set's
-// shape and return the plan built with it.
+// current state (reps force evaluations, near-pair pass included, and reps
+// kicks each; the state is untouched), remember the shape with the least
+// evaluation + kick time for the set's shape and return the plan built with
+// it.  Needs the float planes current.
 int tune_pair(const Pool &P, ClusterSet &C, int precision, const Phys &ph, cudaStream_t st,
               int reps, TuneReport &rep, Plan &out);
 

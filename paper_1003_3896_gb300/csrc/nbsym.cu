@@ -713,6 +713,8 @@ int nb_tune(nb_ctx *c, int reps, nb_tune_t *out)
         out->grid = rep.grid;
         out->pair_ms = rep.pair_ms;
         out->default_ms = rep.default_ms;
+        out->cost_ms = rep.cost_ms;
+        out->default_cost_ms = rep.default_cost_ms;
     }
     return NB_OK;
 }

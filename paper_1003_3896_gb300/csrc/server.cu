@@ -50,6 +50,7 @@ struct Group {
     int precision = 0, order = 2;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
+    std::vector<cudaEvent_t> ev;          // (start, stop) of each pair launch of a step
     ClusterSet set;
     Plan plan;
     std::vector<int64_t> members;         // job ids in the current set
@@ -195,6 +196,14 @@ void complete_step(nb_server *s, Group &g)
 {
     g.inflight = false;
     s->stats.interactions += (double)g.step_pairs;
+    // device time of the step's pair launches, by arithmetic
+    const int a = g.precision == NB_FP64 ? 0 : (g.precision == NB_DS ? 1 : 2);
+    for (int q = 0; q < (g.order == 6 ? 7 : 1); ++q) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, g.ev[2 * q], g.ev[2 * q + 1]) == cudaSuccess)
+            s->stats.pair_ms[a] += ms;
+    }
+    s->stats.pair_interactions[a] += (double)g.step_pairs;
     for (int64_t id : g.stepping) {
         Job &j = *s->jobs[id];
         ++j.steps_done;
@@ -250,7 +259,7 @@ int launch_step(nb_server *s, Group &g)
         g.dirty = false;
     }
     int64_t k = 0;
-    int rc = enq_step(s->pool, g.set, g.plan, s->phys, g.order, 1.0, g.stream, nullptr, &k);
+    int rc = enq_step(s->pool, g.set, g.plan, s->phys, g.order, 1.0, g.stream, &g.ev, &k);
     if (rc) return rc;
     NB_TRY(cudaEventRecord(g.done, g.stream));
     g.inflight = true;
@@ -341,6 +350,7 @@ void nb_server_params_default(nb_server_params *p)
     p->bd = 0.26;
     p->Mb = 15.0;
     p->ab = 0.7;
+    p->fp64_via_dd = 1;
 }
 
 int nb_server_create(const nb_server_params *p, nb_server **out)
@@ -385,6 +395,10 @@ int nb_server_create(const nb_server_params *p, nb_server **out)
         if (!rc && (cudaStreamCreateWithFlags(&gr.stream, cudaStreamNonBlocking) != cudaSuccess ||
                     cudaEventCreateWithFlags(&gr.done, cudaEventDisableTiming) != cudaSuccess))
             rc = set_error(NB_ECUDA, "stream or event creation failed");
+        gr.ev.assign(14, nullptr);   // 7 force evaluations per step at most
+        for (auto &e : gr.ev)
+            if (!rc && cudaEventCreate(&e) != cudaSuccess)
+                rc = set_error(NB_ECUDA, "event creation failed");
     }
     if (!rc) rc = set_create(s->io, 1, cap);
     if (!rc && cudaStreamCreateWithFlags(&s->io_stream, cudaStreamNonBlocking) != cudaSuccess)
@@ -414,6 +428,8 @@ void nb_server_destroy(nb_server *s)
         if (g.stream) cudaStreamSynchronize(g.stream);
         set_destroy(g.set);
         if (g.done) cudaEventDestroy(g.done);
+        for (auto e : g.ev)
+            if (e) cudaEventDestroy(e);
         if (g.stream) cudaStreamDestroy(g.stream);
     }
     set_destroy(s->io);

@@ -137,28 +137,46 @@ int tune_load(const char *path, int64_t *loaded)
     return NB_OK;
 }
 
-// Mean time of one pair launch of the given plan, over reps launches after
-// one untimed launch.
+// Mean time of one force evaluation with the given plan as a step runs it
+// (*ms: the pair launch, with the mixed mode's near-pair pass beside it on
+// the side stream), over reps evaluations after one untimed one, and of one
+// kick that consumes its partial slots (*kick_ms).  Shapes are chosen by the
+// sum: a grid of more blocks may win in the pair kernel and lose it again in
+// the kick (more partial slots per i-block to sum), and a single resident
+// wave has no slack for the near-pair pass's share of the SMs.  The kick
+// reads and writes positions and velocities in the pool's staging buffer
+// instead of the state and leaves the float planes alone, so the state is
+// not touched.
 static int time_plan(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph,
-                     cudaStream_t st, int reps, cudaEvent_t e0, cudaEvent_t e1, double *ms)
+                     cudaStream_t st, int reps, cudaEvent_t e0, cudaEvent_t e1, double *ms,
+                     double *kick_ms)
 {
-    const DevState s = view(P, C, pl);
-    HostTab ht;
-    ht.K = C.K;
-    ht.uoff = C.uoff.data();
-    ht.boff = C.boff.data();
-    ht.nk = C.nk.data();
-    ht.ntiles = C.ntiles.data();
-    ht.eps2f = C.eps2f.data();
-    ht.mu = C.mu.data();
-    NB_TRY(launch_pair(s, pl.pl, ht, ph.G, st));
+    int rc = enq_force(P, C, pl, ph, st, nullptr, nullptr, nullptr);
+    if (rc) return rc;
     NB_TRY(cudaEventRecord(e0, st));
-    for (int r = 0; r < reps; ++r) NB_TRY(launch_pair(s, pl.pl, ht, ph.G, st));
+    for (int r = 0; r < reps && rc == NB_OK; ++r)
+        rc = enq_force(P, C, pl, ph, st, nullptr, nullptr, nullptr);
+    if (rc) return rc;
     NB_TRY(cudaEventRecord(e1, st));
     NB_TRY(cudaEventSynchronize(e1));
     float t = 0.f;
     NB_TRY(cudaEventElapsedTime(&t, e0, e1));
     *ms = t / reps;
+    DevState so = view(P, C, pl);
+    so.x = P.stage;
+    so.y = P.stage + P.cap;
+    so.z = P.stage + 2 * P.cap;
+    so.vx = P.stage + 3 * P.cap;
+    so.vy = P.stage + 4 * P.cap;
+    so.vz = P.stage + 5 * P.cap;
+    NB_TRY(launch_kick_drift(so, pl.pl.d, 1.0, 1.0, 1, 0, ph.ext, st));
+    NB_TRY(cudaEventRecord(e0, st));
+    for (int r = 0; r < reps; ++r)
+        NB_TRY(launch_kick_drift(so, pl.pl.d, 1.0, 1.0, 1, 0, ph.ext, st));
+    NB_TRY(cudaEventRecord(e1, st));
+    NB_TRY(cudaEventSynchronize(e1));
+    NB_TRY(cudaEventElapsedTime(&t, e0, e1));
+    *kick_ms = t / reps;
     return NB_OK;
 }
 
@@ -177,7 +195,7 @@ int tune_pair(const Pool &P, ClusterSet &C, int precision, const Phys &ph, cudaS
     rep = TuneReport();
     rep.precision = precision;
     PairShape best{0, 0, 0};
-    double best_ms = 0;
+    double best_ms = 0, best_cost = 0;   // evaluation time and cost of the best shape
     int64_t best_gw = 0;
     std::vector<int64_t> seen;   // (I, grid, jt) already timed
     do {
@@ -185,7 +203,9 @@ int tune_pair(const Pool &P, ClusterSet &C, int precision, const Phys &ph, cudaS
         Plan def;
         rc = plan_make(P, C, precision, st, def, nullptr, /*use_table=*/false);
         if (rc) break;
-        rc = time_plan(P, C, def, ph, st, reps, e0, e1, &rep.default_ms);
+        double def_kick = 0;
+        rc = time_plan(P, C, def, ph, st, reps, e0, e1, &rep.default_ms, &def_kick);
+        rep.default_cost_ms = rep.default_ms + def_kick;
         if (rc) break;
         const int Is[] = {1, 2, 4, 8};
         for (int I : Is) {
@@ -197,10 +217,19 @@ int tune_pair(const Pool &P, ClusterSet &C, int precision, const Phys &ph, cudaS
                 w_full += ((C.nk[k] + TILE * I - 1) / (TILE * I)) * ((C.nk[k] + TILE - 1) / TILE);
             const bool scarce = w_full < 2 * (int64_t)P.num_sms * occ;
             // grids of 1 to MAX_WAVES resident waves, and single waves a
-            // little below the occupancy limit
+            // little below the occupancy limit.  With the near-pair pass
+            // beside the pair kernel only grids of DEFAULT_WAVES or more
+            // waves: the side stream's blocks, resident first, leave a grid
+            // of one or two waves unevenly placed over the SMs (some get
+            // three of its blocks, some one), and such a kernel runs at the
+            // pace of its most loaded SM (a one-wave grid of the 512-cluster
+            // ensemble took 2.23 ms timed alone and 3.37 ms in the step
+            // graph); later waves go to whichever SM frees a slot.
+            const bool beside = mode == PM_DS_NEAR;
             int bs[8], nb = 0;
-            for (int w : {MAX_WAVES, DEFAULT_WAVES, 2}) bs[nb++] = w * occ;
-            for (int b = occ; b >= 1 && b > occ - 4; --b) bs[nb++] = b;
+            for (int w : {MAX_WAVES, DEFAULT_WAVES, 2})
+                if (!beside || w >= DEFAULT_WAVES) bs[nb++] = w * occ;
+            for (int b = occ; !beside && b >= 1 && b > occ - 4; --b) bs[nb++] = b;
             for (int jt = TILE; rc == NB_OK && jt >= (scarce ? 32 : TILE); jt /= 2)
             for (int q = 0; q < nb; ++q) {
                 const int b = bs[q];
@@ -213,19 +242,21 @@ int tune_pair(const Pool &P, ClusterSet &C, int precision, const Phys &ph, cudaS
                 for (int64_t v : seen) dup = dup || v == tag;
                 if (dup) continue;
                 seen.push_back(tag);
-                double ms = 0;
-                rc = time_plan(P, C, pl, ph, st, reps, e0, e1, &ms);
+                double ms = 0, kick = 0;
+                rc = time_plan(P, C, pl, ph, st, reps, e0, e1, &ms, &kick);
                 if (rc) break;
                 ++rep.candidates;
-                // more blocks x i-block width means more partial slots for
-                // the kick to sum: such a shape has to win by 0.5%, one with
-                // fewer may lose by as much
-                const double tie = 1.005;
+                // cost: one force evaluation and one kick; within 0.2% the
+                // shape with fewer blocks x i-block width (fewer partial
+                // slots) wins
+                const double cost = ms + kick;
+                const double tie = 1.002;
                 const int64_t gw = pl.pl.d.G * I;
-                if (best.I == 0 || ms * (gw > best_gw ? tie : 1.0) <
-                                       best_ms * (gw < best_gw ? tie : 1.0)) {
+                if (best.I == 0 || cost * (gw > best_gw ? tie : 1.0) <
+                                       best_cost * (gw < best_gw ? tie : 1.0)) {
                     best = s;
                     best_ms = ms;
+                    best_cost = cost;
                     best_gw = gw;
                     rep.grid = pl.pl.d.G;
                 }
@@ -239,6 +270,7 @@ int tune_pair(const Pool &P, ClusterSet &C, int precision, const Phys &ph, cudaS
         }
         rep.shape = best;
         rep.pair_ms = best_ms;
+        rep.cost_ms = best_cost;
         tune_store(tune_key(P, C, precision), best);
         rc = plan_make(P, C, precision, st, out, &best, false);
     } while (0);

@@ -58,7 +58,8 @@ class TuneT(C.Structure):
     _fields_ = [("precision", C.c_int), ("bodies_per_thread", C.c_int),
                 ("blocks_per_sm", C.c_int), ("j_tile", C.c_int), ("candidates", C.c_int),
                 ("grid", C.c_int64),
-                ("pair_ms", C.c_double), ("default_ms", C.c_double)]
+                ("pair_ms", C.c_double), ("default_ms", C.c_double),
+                ("cost_ms", C.c_double), ("default_cost_ms", C.c_double)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -380,7 +381,8 @@ class ServerStats(C.Structure):
                 ("failed", C.c_int64), ("cancelled", C.c_int64), ("queued", C.c_int64),
                 ("running", C.c_int64), ("interactions", C.c_double),
                 ("kernel_launches", C.c_int64), ("capacity_bodies", C.c_int64),
-                ("clock_s", C.c_double)]
+                ("clock_s", C.c_double), ("pair_ms", C.c_double * 3),
+                ("pair_interactions", C.c_double * 3)]
 
 
 JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED, JOB_CANCELLED = 0, 1, 2, 3, 4
@@ -475,4 +477,7 @@ class Server:
     def stats(self) -> dict:
         s = ServerStats()
         check(nb_server_stats(self._h, C.byref(s)))
-        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+        out = {k: getattr(s, k) for k, _ in ServerStats._fields_}
+        for k in ("pair_ms", "pair_interactions"):
+            out[k] = list(out[k])
+        return out

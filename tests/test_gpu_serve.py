@@ -48,6 +48,12 @@ def test_each_result_same_alone_and_in_mix(nbs):
         assert overlap
         stats = srv.stats()
         assert stats["completed"] == len(JOBS) and stats["interactions"] > 0
+        # pair launches timed by arithmetic: mixed jobs, and the FP64 jobs in
+        # float-float (the default); none on the FP64 kernel
+        assert stats["pair_ms"][1] > 0 and stats["pair_interactions"][1] > 0
+        assert stats["pair_ms"][2] > 0 and stats["pair_interactions"][2] > 0
+        assert stats["pair_interactions"][0] == 0
+        assert sum(stats["pair_interactions"]) == stats["interactions"]
         results = [srv.result(j) for j in ids]
     for k, ((n, order, prec, dt, steps), (x, v)) in enumerate(zip(JOBS, results)):
         pos, vel, m, eps = ic(n, 500 + k)
@@ -113,7 +119,8 @@ def test_admission_respects_budget_and_slots(nbs):
 
 
 def test_slot_limit_and_cancel(nbs):
-    with nbs.Server(hbm_budget_bytes=1e9, max_jobs=1) as srv:
+    # the FP64 kernel keeps the long job running for seconds
+    with nbs.Server(hbm_budget_bytes=1e9, max_jobs=1, fp64_via_dd=0) as srv:
         pos, vel, m, eps = ic(4000, 700)
         long_job = srv.submit(pos, vel, m, 6, 1 / 512, 400, precision="fp64", eps=eps)
         p2, v2, m2, e2 = ic(500, 701)
@@ -163,16 +170,26 @@ def test_bad_jobs_rejected(nbs):
 
 
 def test_fp64_jobs_via_float_float(nbs, orc):
-    """With fp64_via_dd the server runs FP64 jobs in float-float arithmetic:
-    the result still meets the FP64 bar against the oracle (4 steps,
-    positions within 1e-10), and NB_DD jobs are accepted directly."""
+    """By default (fp64_via_dd = 1) the server runs FP64 jobs in float-float
+    arithmetic: the result still meets the FP64 bar against the oracle (4
+    steps, positions within 1e-10), and NB_DD jobs are accepted directly.
+    With fp64_via_dd = 0 they run the FP64 kernel, to the same bar."""
     n, order, dt, steps = 1500, 6, 1.0 / 512, 4
     pos, vel, m, eps = ic(n, 77)
     rx, _ = orc.run(pos, vel, m, orc.Params(eps=eps), order, dt, steps)
-    with nbs.Server(hbm_budget_bytes=1e9, max_jobs=8, fp64_via_dd=1) as srv:
+    with nbs.Server(hbm_budget_bytes=1e9, max_jobs=8) as srv:
         a = srv.submit(pos, vel, m, order, dt, steps, precision="fp64", eps=eps)
         b = srv.submit(pos, vel, m, order, dt, steps, precision="dd", eps=eps)
         for jid in (a, b):
             assert srv.wait(jid, 300)["state"] == nbs.JOB_DONE
             x, _ = srv.result(jid)
             assert np.abs(x - rx).max() <= 1e-10, np.abs(x - rx).max()
+        st = srv.stats()
+        assert st["pair_interactions"][0] == 0 and st["pair_interactions"][2] > 0
+    with nbs.Server(hbm_budget_bytes=1e9, max_jobs=8, fp64_via_dd=0) as srv:
+        a = srv.submit(pos, vel, m, order, dt, steps, precision="fp64", eps=eps)
+        assert srv.wait(a, 300)["state"] == nbs.JOB_DONE
+        x, _ = srv.result(a)
+        assert np.abs(x - rx).max() <= 1e-10, np.abs(x - rx).max()
+        st = srv.stats()
+        assert st["pair_interactions"][0] > 0 and st["pair_interactions"][2] == 0

@@ -37,8 +37,10 @@ def test_tuned_plan_keeps_parity_and_is_reused(nbs, orc, prec, n, tol):
         r = ctx.tune(reps=2)
         assert r["candidates"] >= 2
         assert r["pair_ms"] > 0 and r["default_ms"] > 0
-        # the planner's own shape is among the candidates
-        assert r["pair_ms"] <= 1.15 * r["default_ms"]
+        assert r["cost_ms"] >= r["pair_ms"] and r["default_cost_ms"] >= r["default_ms"]
+        # shapes are chosen by evaluation + kick time, and the planner's own
+        # shape is among the candidates (timed twice: noise of a few percent)
+        assert r["cost_ms"] <= 1.05 * r["default_cost_ms"]
         shape = ctx.pair_shape()
         assert shape["bodies_per_thread"] == r["bodies_per_thread"]
         assert shape["blocks_per_sm"] == r["blocks_per_sm"]
