@@ -284,6 +284,70 @@ def run_reference(args, rank, world):
     return 0
 
 
+def run_strong(args):
+    """One cluster shared by all ranks, each owning a range of bodies (the
+    paper's multi-GPU scheme, Sect. 4.2; paper_1003_3896_gb300/isplit.py):
+    the paper's uniform sphere (Q = 0.3) of N = --strong-n bodies, leapfrog
+    steps of dt = 5e-4, mixed precision; positions all-gathered over NCCL
+    between substeps.  Total work is fixed as ranks are added (strong
+    scaling); value = N^2 per evaluation x evaluations / slowest rank's time."""
+    world, rank, local = rank_env()
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1003_3896_gb300 import build as nbbuild
+    if rank == 0:
+        nbbuild.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1003_3896_gb300 import ics, isplit, nbsym
+    n = args.strong_n
+    pos, vel, m = ics.uniform_sphere(n, 0, q_vir=0.3)
+    eps = ics.paper_softening(n)
+    dt = 5e-4
+    ctx = nbsym.Context(n, eps=eps, precision=args.precision, device=local)
+    ctx.load(pos, vel, m)
+    rg, chunk = isplit.ranges(n, world)
+    i0, i1 = rg[rank]
+    me = isplit.Rank(isplit.ContextBackend(ctx, dev), i0, i1, chunk)
+    ex = isplit.DistExchange() if world > 1 else isplit.LocalExchange()
+    w = nbsym.stage_weights(2)
+    isplit.run([me], ex, w, dt, args.warmup)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        isplit.run([me], ex, w, dt, args.steps)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+    t_max = max_over_ranks(t, dev)
+    value = args.steps * float(n) * n / t_max / 1e9
+    peak = fp32_peak_tflops(torch.cuda.get_device_properties(dev).multi_processor_count, 2070.0)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "f32-pair/ds-acc" if args.precision == "ds" else args.precision,
+            "data": "synthetic",
+            "config": {"workload": f"uniform_sphere_Q0.3_N{n}_leapfrog_dt5e-4_isplit",
+                       "n": n, "order": 2, "dt": dt, "precision": args.precision,
+                       "eps": "0.005/N^(1/3)", "l2": "inputs far larger than L2",
+                       "parallelism": f"i-split x{world} (positions all-gathered per substep)"},
+            "frac_of_fp32_peak_per_gpu": 20 * value / 1e3 / world / peak,
+            "clocks": clk.summary(),
+            "paper_context": {"source": "paper Table 3 / Sect. 5.1, N = 1536000, 2 x Tesla C1060",
+                              "sp_gflops_2gpu": 846.0, "two_gpu_leapfrog_step_s": 60.0}}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -316,7 +380,13 @@ def main():
     ap.add_argument("--rates", default="",
                     help="c5: comma-separated arrival rates (jobs/s) to replay the trace at "
                          "after the 200/s run, e.g. 2,4,8 (the rate sweep)")
+    ap.add_argument("--strong", action="store_true",
+                    help="one cluster split by body range over the ranks (strong scaling)")
+    ap.add_argument("--strong-n", type=int, default=1536000,
+                    help="--strong: bodies of the shared cluster")
     args = ap.parse_args()
+    if args.strong and args.impl != "reference":
+        return run_strong(args)
     if args.workload != "c2":
         import bench_workloads
         return bench_workloads.run(args)

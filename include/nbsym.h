@@ -301,6 +301,41 @@ int nb_accel_static(const nb_params *p, int64_t n, const double *d_pos,
  * (nothing loaded), NB_ENONFINITE, NB_ECUDA. */
 int nb_accel_range(nb_ctx *ctx, int64_t i0, int64_t i1, double *acc_out);
 
+/* The kick weights of one step of the given order (Sect. 3.1) to w, which
+ * has room for 7: order 2 (drift-kick-drift leapfrog) one weight, 1; order 6
+ * (SI6A) the seven leapfrog weights w3 w2 w1 w0 w1 w2 w3 of Yoshida's
+ * sixth-order solution A, w0 = 1 - 2 (w1 + w2 + w3).  The drifts between
+ * them are half sums of neighbouring weights: w_0 / 2 first, (w_k + w_k+1) / 2
+ * between kicks k and k + 1, w_last / 2 last (nb_step merges adjacent half
+ * drifts this way).  Returns the number of weights.  Errors: NB_EINVAL (NULL
+ * w, order not 2 or 6). */
+int nb_stage_weights(int order, double *w);
+
+/* One substep of the leapfrog / SI6A sequence (Sect. 3.1) for bodies
+ * [i0, i1) of a one-cluster context: when kick != 0, v_i += kick * a_i with
+ * a_i the right-hand side of eq. 3 at the current positions (the internal sum
+ * against all n bodies, computed as nb_accel_range does, plus the external
+ * field); then x_i += drift * v_i.  kick and drift are the step length times
+ * the stage weight (a drift-only substep passes kick = 0).  Other bodies are
+ * untouched.  This is one GPU's share of a step in the paper's multi-GPU
+ * scheme (Sect. 4.2): every GPU holds all positions, advances its own i-range
+ * and then receives the others' new positions (nb_set_state).  Split
+ * ranges give the same bits as the whole range.  Synchronous.  Errors:
+ * NB_EINVAL (NULL, bad range, non-finite weights, more than one cluster),
+ * NB_ESTATE (nothing loaded), NB_ECUDA. */
+int nb_substep_range(nb_ctx *ctx, int64_t i0, int64_t i1, double kick, double drift);
+
+/* Replace the positions and / or velocities of all n bodies (n rows of x, y,
+ * z each; host memory; either pointer may be NULL to keep those values) of a
+ * loaded context; masses, softening and the launch plan are kept, unlike
+ * nb_load.  Synchronous.  Errors: NB_EINVAL (NULL ctx), NB_ESTATE (nothing
+ * loaded), NB_ECUDA. */
+int nb_set_state(nb_ctx *ctx, const double *pos, const double *vel);
+
+/* As nb_set_state from device memory (e.g. the buffer an all-gather of the
+ * GPUs' i-ranges filled). */
+int nb_set_state_device(nb_ctx *ctx, const double *d_pos, const double *d_vel);
+
 /* The N(N-1)/2 variant of the internal sum (Newton's third law: each
  * unordered pair evaluated once and its force added to both bodies), which
  * the paper rejects for its GPU (Sect. 4.2); provided to measure it here.

@@ -126,6 +126,25 @@ __global__ void unpack_kernel(DevState s, const double *__restrict__ pos,
     s.mf[i] = __double2float_rn(mass[t]);   // masses never change after load
 }
 
+// Positions and / or velocities (NULL: kept) of a loaded state.
+__global__ void set_state_kernel(DevState s, const double *__restrict__ pos,
+                                 const double *__restrict__ vel)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= s.n) return;
+    const int64_t i = body_at(s.cl, t).gi;
+    if (pos) {
+        s.x[i] = pos[3 * t];
+        s.y[i] = pos[3 * t + 1];
+        s.z[i] = pos[3 * t + 2];
+    }
+    if (vel) {
+        s.vx[i] = vel[3 * t];
+        s.vy[i] = vel[3 * t + 1];
+        s.vz[i] = vel[3 * t + 2];
+    }
+}
+
 __global__ void pack_kernel(DevState s, double *__restrict__ pos, double *__restrict__ vel)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -161,6 +180,13 @@ cudaError_t launch_unpack(const DevState &s, const double *pos, const double *ve
                           const double *mass, cudaStream_t st)
 {
     unpack_kernel<<<blocks_for(s.n, ot_for(s.n)), ot_for(s.n), 0, st>>>(s, pos, vel, mass);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_state(const DevState &s, const double *pos, const double *vel,
+                             cudaStream_t st)
+{
+    set_state_kernel<<<blocks_for(s.n, ot_for(s.n)), ot_for(s.n), 0, st>>>(s, pos, vel);
     return cudaGetLastError();
 }
 
@@ -419,10 +445,10 @@ __device__ __forceinline__ void sum_slots(const DevState &s, const Decomp &d, co
 // of the field-free kick).
 template <bool EXT, int SB>
 __global__ void kick_drift_kernel(DevState s, Decomp d, double wk, double wd, int do_kick,
-                                  int do_split, ExtField ext)
+                                  int do_split, ExtField ext, int64_t t0, int64_t t1)
 {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= s.n) return;
+    const int64_t t = t0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= t1) return;
     const BodyRef r = body_at(s.cl, t);
     const int64_t i = r.gi;
     const double dt = s.cl.dts[r.k];
@@ -462,22 +488,31 @@ __global__ void kick_drift_kernel(DevState s, Decomp d, double wk, double wd, in
 cudaError_t launch_kick_drift(const DevState &s, const Decomp &d, double wk, double wd,
                               int do_kick, int do_split, const ExtField &ext, cudaStream_t st)
 {
+    return launch_kick_drift_range(s, d, wk, wd, do_kick, do_split, ext, 0, s.n, st);
+}
+
+cudaError_t launch_kick_drift_range(const DevState &s, const Decomp &d, double wk, double wd,
+                                    int do_kick, int do_split, const ExtField &ext, int64_t t0,
+                                    int64_t t1, cudaStream_t st)
+{
+    if (t1 <= t0) return cudaSuccess;
     // blocks of at most 128 threads: with ~100 registers a thread, 128-thread
     // blocks pack 20 warps on an SM against 16 for 256 (the kick waits on
     // memory; the ensemble's kick ran 8% faster)
-    const int t = ot_for(s.n) < 128 ? ot_for(s.n) : 128;
-    const unsigned nb = blocks_for(s.n, t);
+    const int64_t m = t1 - t0;
+    const int t = ot_for(m) < 128 ? ot_for(m) : 128;
+    const unsigned nb = blocks_for(m, t);
     const bool narrow = d.slots <= 4;   // every i-block has at most 4 slots
     if (ext.on) {
         if (narrow)
-            kick_drift_kernel<true, 4><<<nb, t, 0, st>>>(s, d, wk, wd, do_kick, do_split, ext);
+            kick_drift_kernel<true, 4><<<nb, t, 0, st>>>(s, d, wk, wd, do_kick, do_split, ext, t0, t1);
         else
-            kick_drift_kernel<true, 8><<<nb, t, 0, st>>>(s, d, wk, wd, do_kick, do_split, ext);
+            kick_drift_kernel<true, 8><<<nb, t, 0, st>>>(s, d, wk, wd, do_kick, do_split, ext, t0, t1);
     } else {
         if (narrow)
-            kick_drift_kernel<false, 4><<<nb, t, 0, st>>>(s, d, wk, wd, do_kick, do_split, ext);
+            kick_drift_kernel<false, 4><<<nb, t, 0, st>>>(s, d, wk, wd, do_kick, do_split, ext, t0, t1);
         else
-            kick_drift_kernel<false, 8><<<nb, t, 0, st>>>(s, d, wk, wd, do_kick, do_split, ext);
+            kick_drift_kernel<false, 8><<<nb, t, 0, st>>>(s, d, wk, wd, do_kick, do_split, ext, t0, t1);
     }
     return cudaGetLastError();
 }

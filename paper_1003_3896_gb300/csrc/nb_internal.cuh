@@ -242,6 +242,9 @@ cudaError_t launch_cluster_map(const Clusters &c, int32_t *cid, int64_t n, cudaS
 cudaError_t launch_unpack(const DevState &s, const double *pos, const double *vel,
                           const double *mass, cudaStream_t st);
 cudaError_t launch_pack(const DevState &s, double *pos, double *vel, cudaStream_t st);
+// Positions and / or velocities (NULL: kept) into the pool planes.
+cudaError_t launch_set_state(const DevState &s, const double *pos, const double *vel,
+                             cudaStream_t st);
 // Frame origin and rms radius of every cluster; with near, also the
 // near-pair radius of the mixed mode's correction pass (2 or 4 kernels).
 cudaError_t launch_frame(const DevState &s, double near_frac, bool near, cudaStream_t st);
@@ -254,6 +257,10 @@ cudaError_t launch_split(const DevState &s, cudaStream_t st);
 // j-stream mass words (needed once after any load; masses never change).
 cudaError_t launch_kick_drift(const DevState &s, const Decomp &d, double wk, double wd,
                               int do_kick, int do_split, const ExtField &ext, cudaStream_t st);
+// The same for linear bodies [t0, t1) only.
+cudaError_t launch_kick_drift_range(const DevState &s, const Decomp &d, double wk, double wd,
+                                    int do_kick, int do_split, const ExtField &ext, int64_t t0,
+                                    int64_t t1, cudaStream_t st);
 cudaError_t launch_accel_out(const DevState &s, const Decomp &d, const ExtField &ext,
                              double *out_aos, cudaStream_t st);
 // The same for linear bodies [t0, t1) only, row t - t0 of out_aos.

@@ -268,6 +268,20 @@ extern "C" {
 
 int nb_abi_version(void) { return NB_ABI_VERSION; }
 
+int nb_stage_weights(int order, double *w)
+{
+    if (!w) return set_error(NB_EINVAL, "w is NULL");
+    if (order == 2) {
+        w[0] = 1.0;
+        return 1;
+    }
+    if (order != 6) return set_error(NB_EINVAL, "order must be 2 or 6");
+    const double w0 = 1.0 - 2.0 * (SI6_W1 + SI6_W2 + SI6_W3);
+    const double seq[7] = {SI6_W3, SI6_W2, SI6_W1, w0, SI6_W1, SI6_W2, SI6_W3};
+    for (int k = 0; k < 7; ++k) w[k] = seq[k];
+    return 7;
+}
+
 const char *nb_last_error(void) { return last_error(); }
 
 void nb_params_default(nb_params *p)
@@ -481,6 +495,86 @@ int nb_accel_range(nb_ctx *c, int64_t i0, int64_t i1, double *acc_out)
     NB_TRY(cudaMemcpyAsync(acc_out, out, sizeof(double) * 3 * (size_t)(i1 - i0),
                            cudaMemcpyDeviceToHost, c->stream));
     return check_flag(c, "nb_accel_range");
+}
+
+int nb_substep_range(nb_ctx *c, int64_t i0, int64_t i1, double kick, double drift)
+{
+    if (!c) return set_error(NB_EINVAL, "ctx is NULL");
+    if (c->n == 0) return set_error(NB_ESTATE, "nb_substep_range before nb_load");
+    if (c->set.K != 1) return set_error(NB_EINVAL, "nb_substep_range takes one cluster");
+    if (i0 < 0 || i1 > c->n || i0 >= i1)
+        return set_error(NB_EINVAL, "range [%lld, %lld) outside [0, %lld)", (long long)i0,
+                         (long long)i1, (long long)c->n);
+    if (!std::isfinite(kick) || !std::isfinite(drift))
+        return set_error(NB_EINVAL, "kick and drift must be finite");
+    DeviceGuard dg(c->p.device);
+    const Plan &pl = c->plan;
+    PairLaunch rl = pl.pl;
+    const int ipb = TILE * rl.I;
+    const int64_t b0 = i0 / ipb, b1 = (i1 + ipb - 1) / ipb, W = b1 - b0;
+    int64_t G = (int64_t)c->pool.num_sms * rl.blocks_per_sm;
+    if (G > W) G = W;
+    rl.d = make_decomp(W, c->set.max_ntiles, ipb, G, c->pool.s.part_slots, TILE, 1);
+    rl.d.b0 = b0;
+    rl.d.mask_self = pl.pl.d.mask_self;
+    const DevState s = view(c->pool, c->set, pl);
+    if (kick != 0.0) {
+        // the force evaluation of nb_accel_range (whole i-block rows, each
+        // summed in order by one block), consumed by the kick of the range
+        int rc = refresh_split(c);
+        if (rc) return rc;
+        const int64_t uoff[2] = {0, W};
+        HostTab ht;
+        ht.K = 1;
+        ht.uoff = uoff;
+        ht.boff = c->set.boff.data();
+        ht.nk = c->set.nk.data();
+        ht.ntiles = c->set.ntiles.data();
+        ht.eps2f = c->set.eps2f.data();
+        ht.mu = c->set.mu.data();
+        NB_TRY(launch_pair(s, rl, ht, c->phys.G, c->stream));
+        if (rl.mode == PM_DS_NEAR) NB_TRY(launch_near_correct(s, c->phys.G, rl.um, c->stream));
+    }
+    NB_TRY(launch_kick_drift_range(s, rl.d, kick, drift, kick != 0.0 ? 1 : 0, 0, c->phys.ext,
+                                   i0, i1, c->stream));
+    NB_TRY(cudaStreamSynchronize(c->stream));
+    c->split_stale = true;
+    return NB_OK;
+}
+
+static int set_state_common(nb_ctx *c, const double *pos, const double *vel, bool host)
+{
+    if (!c) return set_error(NB_EINVAL, "ctx is NULL");
+    if (c->n == 0) return set_error(NB_ESTATE, "nb_set_state before nb_load");
+    if (!pos && !vel) return NB_OK;
+    DeviceGuard dg(c->p.device);
+    const int64_t n = c->n;
+    const double *dp = pos, *dv = vel;
+    if (host) {
+        double *sp = c->pool.stage, *sv = c->pool.stage + 3 * c->pool.cap;
+        if (pos)
+            NB_TRY(cudaMemcpyAsync(sp, pos, (size_t)(3 * n) * sizeof(double),
+                                   cudaMemcpyHostToDevice, c->stream));
+        if (vel)
+            NB_TRY(cudaMemcpyAsync(sv, vel, (size_t)(3 * n) * sizeof(double),
+                                   cudaMemcpyHostToDevice, c->stream));
+        dp = pos ? sp : nullptr;
+        dv = vel ? sv : nullptr;
+    }
+    NB_TRY(launch_set_state(view(c->pool, c->set, c->p.precision), dp, dv, c->stream));
+    NB_TRY(cudaStreamSynchronize(c->stream));
+    c->split_stale = true;
+    return NB_OK;
+}
+
+int nb_set_state(nb_ctx *c, const double *pos, const double *vel)
+{
+    return set_state_common(c, pos, vel, true);
+}
+
+int nb_set_state_device(nb_ctx *c, const double *d_pos, const double *d_vel)
+{
+    return set_state_common(c, d_pos, d_vel, false);
 }
 
 int nb_step(nb_ctx *c, int order, double dt, int64_t nsteps)

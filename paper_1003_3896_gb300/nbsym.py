@@ -102,6 +102,11 @@ nb_accel_static = _sig("nb_accel_static", C.c_int, C.POINTER(Params), C.c_int64,
 nb_tune = _sig("nb_tune", C.c_int, _ctxp, C.c_int, C.POINTER(TuneT))
 nb_accel_range = _sig("nb_accel_range", C.c_int, _ctxp, C.c_int64, C.c_int64, _dp)
 nb_accel_symmetric = _sig("nb_accel_symmetric", C.c_int, _ctxp, _dp, C.POINTER(C.c_double))
+nb_stage_weights = _sig("nb_stage_weights", C.c_int, C.c_int, _dp)
+nb_substep_range = _sig("nb_substep_range", C.c_int, _ctxp, C.c_int64, C.c_int64, C.c_double,
+                        C.c_double)
+nb_set_state = _sig("nb_set_state", C.c_int, _ctxp, _dp, _dp)
+nb_set_state_device = _sig("nb_set_state_device", C.c_int, _ctxp, _vp, _vp)
 nb_tune_save = _sig("nb_tune_save", C.c_int, C.c_char_p)
 nb_tune_load = _sig("nb_tune_load", C.c_int64, C.c_char_p)
 nb_tune_entries = _sig("nb_tune_entries", C.c_int64)
@@ -126,6 +131,13 @@ def tune_entries() -> int:
 
 def tune_clear():
     nb_tune_clear()
+
+
+def stage_weights(order: int) -> list:
+    """Kick weights of one step of the given order (nb_stage_weights)."""
+    w = np.empty(7)
+    k = check(nb_stage_weights(int(order), _p(w)))
+    return [float(x) for x in w[:k]]
 
 
 def measure_peaks(device: int = 0) -> dict:
@@ -324,6 +336,21 @@ class Context:
         out = np.empty((max(int(i1) - int(i0), 1), 3))   # the library checks the range
         check(nb_accel_range(self._h, int(i0), int(i1), _p(out)))
         return out
+
+    def substep_range(self, i0: int, i1: int, kick: float, drift: float):
+        """Kick (when kick != 0) and drift bodies [i0, i1) (nb_substep_range)."""
+        check(nb_substep_range(self._h, int(i0), int(i1), float(kick), float(drift)))
+
+    def set_state(self, pos=None, vel=None):
+        """Replace positions and / or velocities, host arrays (nb_set_state)."""
+        p = None if pos is None else _host3(pos, self.n)
+        v = None if vel is None else _host3(vel, self.n)
+        check(nb_set_state(self._h, None if p is None else _p(p), None if v is None else _p(v)))
+
+    def set_state_device(self, pos=None, vel=None):
+        """Replace positions and / or velocities from device memory."""
+        check(nb_set_state_device(self._h, _dev(pos, 3 * self.n, "pos"),
+                                  _dev(vel, 3 * self.n, "vel")))
 
     def accel_symmetric(self):
         """(accelerations, pair-kernel ms) from the N(N-1)/2 float variant."""

@@ -94,6 +94,10 @@ calls = {
     "nb_accel_static": nb.nb_accel_static(None, 16, None, None, None),
     "nb_accel_range": nb.nb_accel_range(None, 0, 1, None),
     "nb_accel_symmetric": nb.nb_accel_symmetric(None, None, None),
+    "nb_substep_range": nb.nb_substep_range(None, 0, 1, 0.0, 0.1),
+    "nb_stage_weights": nb.nb_stage_weights(6, None),
+    "nb_set_state": nb.nb_set_state(None, None, None),
+    "nb_set_state_device": nb.nb_set_state_device(None, None, None),
     "nb_tune": nb.nb_tune(None, 2, None),
     "nb_pair_shape": nb.nb_pair_shape(None, None, None, None, None),
     "nb_server_create": nb.nb_server_create(None, None),
@@ -125,7 +129,7 @@ def test_null_handles_are_rejected(lib):
     r = subprocess.run([sys.executable, "-c", NULL_CALLS % ROOT], capture_output=True,
                        text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
-    assert "checked 31 bad {}" in r.stdout
+    assert "checked 35 bad {}" in r.stdout
 
 
 def test_oracle_is_not_on_the_product_path():
