@@ -481,6 +481,13 @@ typedef struct {
                                  overlap on the device, so a launch's time
                                  includes the SMs it shared with other groups */
     double pair_interactions[3]; /* N^2 summed over those launches, same index */
+    double pair_busy_ms[3];   /* device time during which at least one pair
+                                 launch of that arithmetic ran (the union of the
+                                 launches' event intervals, over the first 2^20
+                                 launches of each): pair_interactions[a] /
+                                 pair_busy_ms[a] is that kernel's rate in the
+                                 mix, concurrent launches counted together */
+    double pair_busy_ms_any;  /* the same over all arithmetics */
 } nb_server_stats_t;
 
 /* Defaults: device 0, 4 GB budget, 64 jobs, G = 1, field off with the disk +

@@ -273,42 +273,64 @@ __global__ void __launch_bounds__(NC_T) near_correct_kernel(DevState s, double G
     const float th2 = s.cl.frame[k].th2;
     const float xi = P.x, yi = P.y, zi = P.z;
     const float lxi = Lo.x, lyi = Lo.y, lzi = Lo.z;
-    // candidates in cell order 0..7, each cell's members in body order
+    // candidates in cell order 0..7, each cell's members in body order,
+    // NBT at a time: their indices are resolved first, so their position
+    // loads are in flight together; only the few candidates inside the near
+    // radius load their lo words (one candidate in twenty on a Plummer
+    // sphere).  The body itself is the candidate at its own cell-ordered
+    // position e0.
+    constexpr int NBT = 4;
     int q = 0;
     int2 r = rng[0][tid];
     int e = r.x;
-    for (int it = 0; it < total; ++it, ++e) {
-        while (e >= r.y) {
-            r = rng[++q][tid];
-            e = r.x;
+    for (int it = 0; it < total; it += NBT) {
+        int ee[NBT];
+#pragma unroll
+        for (int b = 0; b < NBT; ++b) {
+            ee[b] = -1;
+            if (it + b < total) {
+                while (e >= r.y) {
+                    r = rng[++q][tid];
+                    e = r.x;
+                }
+                ee[b] = e++;
+            }
         }
-        const float4 Pj = s.ng_spos[e];
-        const float4 Lj = s.ng_slo[e];
-        // the pair kernel's float contribution, operation for operation
-        const float mj = Pj.w;
-        const float ddx = __fadd_rn(Pj.x, -xi);
-        const float ddy = __fadd_rn(Pj.y, -yi);
-        const float ddz = __fadd_rn(Pj.z, -zi);
-        float r2 = __fmaf_rn(ddx, ddx, eps2);
-        r2 = __fmaf_rn(ddy, ddy, r2);
-        r2 = __fmaf_rn(ddz, ddz, r2);
-        if (__float_as_int(Lj.w) == t || !(r2 < th2)) continue;
-        const float ri = near_rsqrt(r2);
-        const float sf = UM ? __fmul_rn(ri, __fmul_rn(ri, ri))
-                            : __fmul_rn(__fmul_rn(mj, ri), __fmul_rn(ri, ri));
-        // the same pair with the double-single coordinate difference
-        const float ex = __fadd_rn(ddx, __fsub_rn(Lj.x, lxi));
-        const float ey = __fadd_rn(ddy, __fsub_rn(Lj.y, lyi));
-        const float ez = __fadd_rn(ddz, __fsub_rn(Lj.z, lzi));
-        float e2 = __fmaf_rn(ex, ex, eps2);
-        e2 = __fmaf_rn(ey, ey, e2);
-        e2 = __fmaf_rn(ez, ez, e2);
-        const float re = near_rsqrt(e2);
-        const float se = UM ? __fmul_rn(re, __fmul_rn(re, re))
-                            : __fmul_rn(__fmul_rn(mj, re), __fmul_rn(re, re));
-        ax += (double)__fmul_rn(ex, se) - (double)__fmul_rn(ddx, sf);
-        ay += (double)__fmul_rn(ey, se) - (double)__fmul_rn(ddy, sf);
-        az += (double)__fmul_rn(ez, se) - (double)__fmul_rn(ddz, sf);
+        float4 Pb[NBT];
+#pragma unroll
+        for (int b = 0; b < NBT; ++b)
+            Pb[b] = s.ng_spos[ee[b] >= 0 ? ee[b] : e0];
+#pragma unroll
+        for (int b = 0; b < NBT; ++b) {
+            if (ee[b] < 0) break;
+            const float4 Pj = Pb[b];
+            // the pair kernel's float contribution, operation for operation
+            const float mj = Pj.w;
+            const float ddx = __fadd_rn(Pj.x, -xi);
+            const float ddy = __fadd_rn(Pj.y, -yi);
+            const float ddz = __fadd_rn(Pj.z, -zi);
+            float r2 = __fmaf_rn(ddx, ddx, eps2);
+            r2 = __fmaf_rn(ddy, ddy, r2);
+            r2 = __fmaf_rn(ddz, ddz, r2);
+            if (ee[b] == (int)e0 || !(r2 < th2)) continue;
+            const float4 Lj = s.ng_slo[ee[b]];
+            const float ri = near_rsqrt(r2);
+            const float sf = UM ? __fmul_rn(ri, __fmul_rn(ri, ri))
+                                : __fmul_rn(__fmul_rn(mj, ri), __fmul_rn(ri, ri));
+            // the same pair with the double-single coordinate difference
+            const float ex = __fadd_rn(ddx, __fsub_rn(Lj.x, lxi));
+            const float ey = __fadd_rn(ddy, __fsub_rn(Lj.y, lyi));
+            const float ez = __fadd_rn(ddz, __fsub_rn(Lj.z, lzi));
+            float e2 = __fmaf_rn(ex, ex, eps2);
+            e2 = __fmaf_rn(ey, ey, e2);
+            e2 = __fmaf_rn(ez, ez, e2);
+            const float re = near_rsqrt(e2);
+            const float se = UM ? __fmul_rn(re, __fmul_rn(re, re))
+                                : __fmul_rn(__fmul_rn(mj, re), __fmul_rn(re, re));
+            ax += (double)__fmul_rn(ex, se) - (double)__fmul_rn(ddx, sf);
+            ay += (double)__fmul_rn(ey, se) - (double)__fmul_rn(ddy, sf);
+            az += (double)__fmul_rn(ez, se) - (double)__fmul_rn(ddz, sf);
+        }
     }
     const int64_t i = s.cl.boff[k] + t - s.cl.noff[k];
     const double Gm = UM ? G * s.cl.mu[k] : G;

@@ -12,6 +12,14 @@
 // steps of a group, finished jobs leave it (their state is copied back and
 // their pool range freed) and newly admitted jobs join it.  A job whose state
 // is not finite when it finishes is failed alone.
+//
+// Up to two steps of a group are in flight: the next one is enqueued while
+// the current one runs whenever no member finishes at the current one and no
+// job waits to join or leave, so the group's stream does not idle while the
+// scheduler notices a finished step.  (Steps are enqueued kernel by kernel:
+// a step graph per group, captured again at each membership change, made the
+// served trace slower, since its jobs join and leave at every few steps.)
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -46,19 +54,28 @@ struct Job {
     std::string error;
 };
 
+// One of a group's two step buffers: its pair-launch timing events, its
+// completion event and what it stepped.
+struct StepSlot {
+    cudaEvent_t done = nullptr;
+    std::vector<cudaEvent_t> ev;          // (start, stop) of each pair launch of the step
+    std::vector<int64_t> stepping;        // members of the step in flight
+    int64_t step_pairs = 0;               // interactions of that step
+};
+
 struct Group {
     int precision = 0, order = 2;
     cudaStream_t stream = nullptr;
-    cudaEvent_t done = nullptr;
-    std::vector<cudaEvent_t> ev;          // (start, stop) of each pair launch of a step
     ClusterSet set;
     Plan plan;
     std::vector<int64_t> members;         // job ids in the current set
     bool dirty = true;                    // membership changed since the last layout
-    bool inflight = false;
-    std::vector<int64_t> stepping;        // members of the step in flight
-    int64_t step_pairs = 0;               // interactions of that step
+    StepSlot slot[2];
+    int head = 0;                         // oldest step in flight
+    int nflight = 0;                      // steps in flight (0, 1 or 2)
 };
+
+constexpr size_t PAIR_IV_CAP = (size_t)1 << 20;
 
 // Bytes of device memory the pool and the group scratch use per body slot.
 constexpr double BYTES_PER_BODY = 7 * 8 + 7 * 4 + 64 + 3 * 3 * 8 + 3 * 8 + 7 * 8 + 5 * (16 + 16);
@@ -85,6 +102,10 @@ struct nb_server {
     Clock::time_point t0;
     nb_server_stats_t stats{};
     std::string fatal;
+    // device-time intervals [start, end) of the pair launches, ms after the
+    // reference event, by arithmetic (the first PAIR_IV_CAP of each)
+    cudaEvent_t ref = nullptr;
+    std::vector<std::pair<float, float>> iv[3];
 };
 
 namespace {
@@ -190,24 +211,33 @@ void admit(nb_server *s)
     }
 }
 
-// The step in flight of group g has completed: count it, retire finished or
-// cancelled jobs.
+// The oldest step in flight of group g has completed: count it; when no
+// other step is in flight, retire finished or cancelled jobs.
 void complete_step(nb_server *s, Group &g)
 {
-    g.inflight = false;
-    s->stats.interactions += (double)g.step_pairs;
+    StepSlot &sl = g.slot[g.head];
+    g.head ^= 1;
+    --g.nflight;
+    s->stats.interactions += (double)sl.step_pairs;
     // device time of the step's pair launches, by arithmetic
     const int a = g.precision == NB_FP64 ? 0 : (g.precision == NB_DS ? 1 : 2);
     for (int q = 0; q < (g.order == 6 ? 7 : 1); ++q) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, g.ev[2 * q], g.ev[2 * q + 1]) == cudaSuccess)
+        float ms = 0.f, t0 = 0.f, t1 = 0.f;
+        if (cudaEventElapsedTime(&ms, sl.ev[2 * q], sl.ev[2 * q + 1]) == cudaSuccess)
             s->stats.pair_ms[a] += ms;
+        if (s->iv[a].size() < PAIR_IV_CAP &&
+            cudaEventElapsedTime(&t0, s->ref, sl.ev[2 * q]) == cudaSuccess &&
+            cudaEventElapsedTime(&t1, s->ref, sl.ev[2 * q + 1]) == cudaSuccess)
+            s->iv[a].emplace_back(t0, t1);
     }
-    s->stats.pair_interactions[a] += (double)g.step_pairs;
-    for (int64_t id : g.stepping) {
+    s->stats.pair_interactions[a] += (double)sl.step_pairs;
+    for (int64_t id : sl.stepping) {
         Job &j = *s->jobs[id];
         ++j.steps_done;
     }
+    // a second step was enqueued only if nobody finishes at this one; a
+    // cancelled job leaves once nothing of its group is in flight
+    if (g.nflight > 0) return;
     std::vector<int64_t> keep;
     for (int64_t id : g.members) {
         Job &j = *s->jobs[id];
@@ -235,8 +265,22 @@ void complete_step(nb_server *s, Group &g)
     g.members.swap(keep);
 }
 
+// Whether the step after the one in flight may be enqueued now: the layout
+// is current, nobody waits to join, and no member finishes or is cancelled
+// at the step in flight.
+bool can_enqueue_ahead(const nb_server *s, const Group &g)
+{
+    if (g.nflight != 1 || g.dirty) return false;
+    for (int64_t id : g.members) {
+        const Job &j = *s->jobs.at(id);
+        if (j.cancel || j.steps_done + 1 >= j.d.nsteps) return false;
+    }
+    return true;
+}
+
 // Enqueue the next step of group g (lock held: the tables are rebuilt from
-// the job records).
+// the job records when the membership changed, which happens only with no
+// step of the group in flight).
 int launch_step(nb_server *s, Group &g)
 {
     if (g.members.empty()) return NB_OK;
@@ -258,15 +302,16 @@ int launch_step(nb_server *s, Group &g)
         if (rc) return rc;
         g.dirty = false;
     }
+    StepSlot &sl = g.slot[(g.head + g.nflight) & 1];
     int64_t k = 0;
-    int rc = enq_step(s->pool, g.set, g.plan, s->phys, g.order, 1.0, g.stream, &g.ev, &k);
+    const int rc = enq_step(s->pool, g.set, g.plan, s->phys, g.order, 1.0, g.stream, &sl.ev, &k);
     if (rc) return rc;
-    NB_TRY(cudaEventRecord(g.done, g.stream));
-    g.inflight = true;
-    g.stepping = g.members;
-    g.step_pairs = 0;
+    NB_TRY(cudaEventRecord(sl.done, g.stream));
+    ++g.nflight;
+    sl.stepping = g.members;
+    sl.step_pairs = 0;
     for (int64_t q = 0; q < g.set.K; ++q)
-        g.step_pairs += g.set.nk[q] * g.set.nk[q] * (g.order == 6 ? 7 : 1);
+        sl.step_pairs += g.set.nk[q] * g.set.nk[q] * (g.order == 6 ? 7 : 1);
     s->stats.kernel_launches += k;
     return NB_OK;
 }
@@ -276,7 +321,7 @@ void fail_all(nb_server *s, const char *why)
     for (auto &g : s->groups) {
         for (int64_t id : g.members) finish(s, *s->jobs[id], NB_JOB_FAILED, why);
         g.members.clear();
-        g.inflight = false;
+        g.nflight = 0;
         g.dirty = true;
     }
 }
@@ -289,29 +334,29 @@ void run(nb_server *s)
         admit(s);
         bool busy = false;
         for (auto &g : s->groups) {
-            if (g.inflight) {
-                const cudaError_t q = cudaEventQuery(g.done);
-                if (q == cudaErrorNotReady) {
-                    busy = true;
-                    continue;
-                }
+            bool failed = false;
+            while (g.nflight > 0) {
+                const cudaError_t q = cudaEventQuery(g.slot[g.head].done);
+                if (q == cudaErrorNotReady) break;
                 if (q != cudaSuccess) {
                     s->fatal = cudaGetErrorString(q);
                     fail_all(s, s->fatal.c_str());
-                    continue;
+                    failed = true;
+                    break;
                 }
                 complete_step(s, g);
-                admit(s);
+                if (g.nflight == 0) admit(s);
             }
-            if (!g.members.empty()) {
+            if (failed) continue;
+            if (!g.members.empty() && (g.nflight == 0 || can_enqueue_ahead(s, g))) {
                 const int rc = launch_step(s, g);
                 if (rc) {
                     s->fatal = last_error();
                     fail_all(s, s->fatal.c_str());
                     continue;
                 }
-                busy = true;
             }
+            if (g.nflight > 0) busy = true;
         }
         s->cv.notify_all();
         if (busy) {
@@ -392,17 +437,24 @@ int nb_server_create(const nb_server_params *p, nb_server **out)
         gr.precision = g < 2 ? NB_FP64 : (g < 4 ? NB_DS : NB_DD);
         gr.order = (g & 1) ? 6 : 2;
         rc = set_create(gr.set, p->max_jobs, cap);
-        if (!rc && (cudaStreamCreateWithFlags(&gr.stream, cudaStreamNonBlocking) != cudaSuccess ||
-                    cudaEventCreateWithFlags(&gr.done, cudaEventDisableTiming) != cudaSuccess))
-            rc = set_error(NB_ECUDA, "stream or event creation failed");
-        gr.ev.assign(14, nullptr);   // 7 force evaluations per step at most
-        for (auto &e : gr.ev)
-            if (!rc && cudaEventCreate(&e) != cudaSuccess)
+        if (!rc && cudaStreamCreateWithFlags(&gr.stream, cudaStreamNonBlocking) != cudaSuccess)
+            rc = set_error(NB_ECUDA, "stream creation failed");
+        for (StepSlot &sl : gr.slot) {
+            if (!rc && cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess)
                 rc = set_error(NB_ECUDA, "event creation failed");
+            sl.ev.assign(14, nullptr);   // 7 force evaluations per step at most
+            for (auto &e : sl.ev)
+                if (!rc && cudaEventCreate(&e) != cudaSuccess)
+                    rc = set_error(NB_ECUDA, "event creation failed");
+        }
     }
     if (!rc) rc = set_create(s->io, 1, cap);
     if (!rc && cudaStreamCreateWithFlags(&s->io_stream, cudaStreamNonBlocking) != cudaSuccess)
         rc = set_error(NB_ECUDA, "stream creation failed");
+    if (!rc && (cudaEventCreate(&s->ref) != cudaSuccess ||
+                cudaEventRecord(s->ref, s->io_stream) != cudaSuccess ||
+                cudaEventSynchronize(s->ref) != cudaSuccess))
+        rc = set_error(NB_ECUDA, "reference event failed");
     if (rc) {
         nb_server_destroy(s);
         return rc;
@@ -427,13 +479,16 @@ void nb_server_destroy(nb_server *s)
     for (auto &g : s->groups) {
         if (g.stream) cudaStreamSynchronize(g.stream);
         set_destroy(g.set);
-        if (g.done) cudaEventDestroy(g.done);
-        for (auto e : g.ev)
-            if (e) cudaEventDestroy(e);
+        for (StepSlot &sl : g.slot) {
+            if (sl.done) cudaEventDestroy(sl.done);
+            for (auto e : sl.ev)
+                if (e) cudaEventDestroy(e);
+        }
         if (g.stream) cudaStreamDestroy(g.stream);
     }
     set_destroy(s->io);
     if (s->io_stream) cudaStreamDestroy(s->io_stream);
+    if (s->ref) cudaEventDestroy(s->ref);
     pool_destroy(s->pool);
     delete s;
 }
@@ -545,6 +600,26 @@ int nb_server_forget(nb_server *s, int64_t job_id)
     return NB_OK;
 }
 
+// Total length of the union of intervals (sorted copy, merged in one sweep).
+static double union_ms(std::vector<std::pair<float, float>> v)
+{
+    std::sort(v.begin(), v.end());
+    double tot = 0.0, a = 0.0, b = -1.0;
+    bool open = false;
+    for (const auto &x : v) {
+        if (!open || x.first > b) {
+            if (open) tot += b - a;
+            a = x.first;
+            b = x.second;
+            open = true;
+        } else if (x.second > b) {
+            b = x.second;
+        }
+    }
+    if (open) tot += b - a;
+    return tot;
+}
+
 int nb_server_stats(nb_server *s, nb_server_stats_t *out)
 {
     if (!s || !out) return set_error(NB_EINVAL, "NULL argument");
@@ -552,6 +627,12 @@ int nb_server_stats(nb_server *s, nb_server_stats_t *out)
     *out = s->stats;
     out->capacity_bodies = s->cap;
     out->clock_s = now_s(s);
+    std::vector<std::pair<float, float>> all;
+    for (int a = 0; a < 3; ++a) {
+        out->pair_busy_ms[a] = union_ms(s->iv[a]);
+        all.insert(all.end(), s->iv[a].begin(), s->iv[a].end());
+    }
+    out->pair_busy_ms_any = union_ms(std::move(all));
     return NB_OK;
 }
 

@@ -409,7 +409,8 @@ class ServerStats(C.Structure):
                 ("running", C.c_int64), ("interactions", C.c_double),
                 ("kernel_launches", C.c_int64), ("capacity_bodies", C.c_int64),
                 ("clock_s", C.c_double), ("pair_ms", C.c_double * 3),
-                ("pair_interactions", C.c_double * 3)]
+                ("pair_interactions", C.c_double * 3), ("pair_busy_ms", C.c_double * 3),
+                ("pair_busy_ms_any", C.c_double)]
 
 
 JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED, JOB_CANCELLED = 0, 1, 2, 3, 4
@@ -505,6 +506,6 @@ class Server:
         s = ServerStats()
         check(nb_server_stats(self._h, C.byref(s)))
         out = {k: getattr(s, k) for k, _ in ServerStats._fields_}
-        for k in ("pair_ms", "pair_interactions"):
+        for k in ("pair_ms", "pair_interactions", "pair_busy_ms"):
             out[k] = list(out[k])
         return out
