@@ -244,7 +244,10 @@ def _serve_trace(args, nbsym, rate_hz, n_cap, fp64_via_dd=1, all_mixed=False):
     per-job latency is submission to completion (queueing included).
     all_mixed: every job in the mixed arithmetic (the served form of the
     FP32-pipe kernel alone)."""
-    trace = ics.serving_trace(n_jobs=args.jobs, rate_hz=rate_hz, seed=0, n_hi=n_cap)
+    # the first args.jobs arrivals of the one 2000-arrival stream (the
+    # generator draws each field for all jobs at once, so a shorter stream
+    # would not be this one's prefix)
+    trace = ics.serving_trace(n_jobs=2000, rate_hz=rate_hz, seed=0, n_hi=n_cap)[:args.jobs]
     dt = 1.0 / 512
     prepared = []
     for j in trace:

@@ -38,15 +38,18 @@ int pool_create(Pool &P, int device, int64_t cap)
         return set_error(NB_ECUDA, "cudaDeviceGetAttribute failed");
     DevState &s = P.s;
     s.cap = cap;
-    // partial-sum slots: an i-block needs about G * ipb / n + 2 of them,
-    // where G * ipb <= SMs * MAX_WAVES * (resident blocks * i-block width)
-    // and the last factor is at most 3072 for every compiled variant (8 x
-    // 256, 6 x 512, 3 x 1024); memory stays near 24 * (that + 2 cap) bytes
-    // whatever cap is.  make_decomp shrinks a grid that would need more.
+    // partial sums: a set of n bodies needs about G * ipb / n + 2 slots per
+    // body, where G * ipb <= SMs * MAX_WAVES * (resident blocks * i-block
+    // width) and the last factor is at most 3072 for every compiled variant
+    // (8 x 256, 6 x 512, 3 x 1024).  The planes are laid out per set (stride
+    // n, linear body index), so 3 (giw + 2 cap) doubles give a set of n
+    // bodies (giw + 2 cap) / n slots: a small set in a large pool (a serving
+    // group) gets as many as a context of its own size.  make_decomp
+    // shrinks a grid that would need more than a set has.
     const int64_t giw = (int64_t)P.num_sms * MAX_WAVES * 3072;
-    int64_t slots = 2 + (giw + cap - 1) / cap;
-    if (slots > 64) slots = 64;
-    s.part_slots = slots;
+    s.part_elems = 3 * (giw + 2 * cap);
+    s.part_slots = 0;
+    s.pstride = 0;
     s.red_len = 0;
     bool ok = true;
     auto A = [&](void **q, size_t bytes) {
@@ -62,7 +65,7 @@ int pool_create(Pool &P, int device, int64_t cap)
     A((void **)&s.xl, c4); A((void **)&s.yl, c4); A((void **)&s.zl, c4);
     A((void **)&s.jd, 2 * (size_t)cap * sizeof(float4));
     A((void **)&s.jl, 2 * (size_t)cap * sizeof(float4));
-    A((void **)&s.part, (size_t)s.part_slots * 3 * c8);
+    A((void **)&s.part, (size_t)s.part_elems * 8);
     A((void **)&s.corr, 3 * c8);
     A((void **)&P.stage, 7 * c8);
     if (!ok) {
@@ -360,7 +363,8 @@ int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan
     for (int32_t k = 0; k < C.K && pl.pl.um; ++k) pl.pl.um = C.mu[k] > 0;
     const int64_t W = C.uoff[C.K];
     int64_t G = want < W ? want : W;   // at least one unit per block
-    pl.pl.d = make_decomp(W, C.max_ntiles, TILE * I, G, P.s.part_slots, jt);
+    const int64_t slot_cap = part_slot_cap(P, C.n);
+    pl.pl.d = make_decomp(W, C.max_ntiles, TILE * I, G, slot_cap, jt);
     for (int32_t k = 0; k < C.K; ++k)
         if (C.eps2d[k] == 0.0) pl.pl.d.mask_self = 1;
     int occ_pot = pair_occupancy(PM_FP64, 1);
@@ -368,7 +372,7 @@ int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan
     const int64_t Wp = C.uoff_pot[C.K];
     int64_t Gp = (int64_t)P.num_sms * occ_pot;
     if (Wp / 2 < Gp) Gp = Wp / 2 > 0 ? Wp / 2 : 1;
-    pl.pot = make_decomp(Wp, C.max_ntiles, TILE, Gp, P.s.part_slots);
+    pl.pot = make_decomp(Wp, C.max_ntiles, TILE, Gp, slot_cap);
     out = pl;
     return NB_OK;
 }
@@ -389,11 +393,19 @@ DevState view(const Pool &P, const ClusterSet &C, const Plan &pl)
     return s;
 }
 
+int64_t part_slot_cap(const Pool &P, int64_t n)
+{
+    const int64_t per = n > 0 ? P.s.part_elems / (3 * n) : MAX_PART_SLOTS;
+    return per < MAX_PART_SLOTS ? per : MAX_PART_SLOTS;
+}
+
 DevState view(const Pool &P, const ClusterSet &C, int precision)
 {
     DevState s = P.s;
     s.cl = C.cl;
     s.n = C.n;
+    s.pstride = C.n > 0 ? C.n : 1;
+    s.part_slots = part_slot_cap(P, C.n);
     s.diag = C.diag;
     s.red = C.red;
     s.red_len = C.scap * 16;
@@ -447,6 +459,7 @@ int enq_force(const Pool &P, const ClusterSet &C, const Plan &pl, const Phys &ph
     ht.K = C.K;
     ht.uoff = C.uoff.data();
     ht.boff = C.boff.data();
+    ht.noff = C.noff.data();
     ht.nk = C.nk.data();
     ht.ntiles = C.ntiles.data();
     ht.eps2f = C.eps2f.data();

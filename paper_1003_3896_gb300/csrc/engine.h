@@ -154,6 +154,8 @@ DevState view(const Pool &P, const ClusterSet &C, const Plan &pl);
 // of at most DS_FULL_MAX_PAIRS pairs forms the double-single difference on
 // every pair (no near-pair pass).
 int plan_mode(const ClusterSet &C, int precision);
+// Partial slots per body a set of n bodies has in the pool's storage.
+int64_t part_slot_cap(const Pool &P, int64_t n);
 int mode_of(int precision);
 bool float_planes(int precision);
 

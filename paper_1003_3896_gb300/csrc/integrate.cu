@@ -407,7 +407,7 @@ cudaError_t launch_split(const DevState &s, cudaStream_t st)
 // registers, and so resident warps, for the memory latency)
 template <int SB>
 __device__ __forceinline__ void sum_slots(const DevState &s, const Decomp &d, const BodyRef &r,
-                                          double &ax, double &ay, double &az)
+                                          int64_t t, double &ax, double &ay, double &az)
 {
     int64_t first, count;
     iblock_slots(d, s.cl, r.k, r.li, first, count);
@@ -420,10 +420,10 @@ __device__ __forceinline__ void sum_slots(const DevState &s, const Decomp &d, co
         for (int q = 0; q < SB; ++q) {
             bx[q] = by[q] = bz[q] = 0.0;
             if (k0 + q < count) {
-                const double *p = s.part + ((k0 + q) * 3) * s.cap + r.gi;
+                const double *p = s.part + ((k0 + q) * 3) * s.pstride + t;
                 bx[q] = p[0];
-                by[q] = p[s.cap];
-                bz[q] = p[2 * s.cap];
+                by[q] = p[s.pstride];
+                bz[q] = p[2 * s.pstride];
             }
         }
 #pragma unroll
@@ -456,7 +456,7 @@ __global__ void kick_drift_kernel(DevState s, Decomp d, double wk, double wd, in
     double vx = s.vx[i], vy = s.vy[i], vz = s.vz[i];
     if (do_kick) {
         double ax, ay, az;
-        sum_slots<SB>(s, d, r, ax, ay, az);
+        sum_slots<SB>(s, d, r, t, ax, ay, az);
         if (EXT) {
             double ex, ey, ez;
             field_accel(ext, x, y, z, ex, ey, ez);
@@ -525,7 +525,7 @@ __global__ void accel_out_kernel(DevState s, Decomp d, ExtField ext, double *__r
     if (t >= t1) return;
     const BodyRef r = body_at(s.cl, t);
     double ax, ay, az;
-    sum_slots<8>(s, d, r, ax, ay, az);
+    sum_slots<8>(s, d, r, t, ax, ay, az);
     if (ext.on) {
         double ex, ey, ez;
         field_accel(ext, s.x[r.gi], s.y[r.gi], s.z[r.gi], ex, ey, ez);
@@ -578,7 +578,7 @@ __global__ void energy_partial_kernel(DevState s, Decomp d, ExtField ext)
             double bp[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q)
-                bp[q] = q0 + q < count ? s.part[((q0 + q) * 3) * s.cap + i] : 0.0;
+                bp[q] = q0 + q < count ? s.part[((q0 + q) * 3) * s.pstride + t] : 0.0;
 #pragma unroll
             for (int q = 0; q < 8; ++q)
                 if (q0 + q < count) phi += bp[q];

@@ -92,8 +92,13 @@ struct DevState {
     // (zh, zh, m, m); jl = (xl, xl, yl, yl), (zl, zl, ml, ml) with ml the
     // float rounding residue of the mass.
     float4 *jd = nullptr, *jl = nullptr;
-    double *part = nullptr;     // partial sums [slot][3][cap]
-    int64_t part_slots = 0;
+    // partial sums of the pair decomposition, [slot][3][pstride] indexed by
+    // the linear body index of the current set (pstride = its body count), so
+    // a set of n bodies has part_elems / (3 n) slots whatever the pool's size
+    double *part = nullptr;
+    int64_t part_elems = 0;     // doubles allocated
+    int64_t pstride = 0;        // slot-plane stride: bodies of the current set
+    int64_t part_slots = 0;     // slots per body available to the current set
     // near-pair correction of the mixed mode (nullptr corr: not applied)
     double *corr = nullptr;     // [3][cap]
     // per linear body: table slot of its cell, arrival rank in the cell, and
@@ -208,10 +213,14 @@ constexpr double DS_FULL_MAX_PAIRS = 134217728.0;   // 2^27
 struct HostTab {
     int32_t K = 0;
     const int64_t *uoff = nullptr, *boff = nullptr, *nk = nullptr;
+    const int64_t *noff = nullptr;   // first linear body of each cluster (NULL: 0)
     const int32_t *ntiles = nullptr;
     const float *eps2f = nullptr;
     const double *mu = nullptr;
 };
+
+// Partial slots per body at most, whatever the storage would allow.
+constexpr int64_t MAX_PART_SLOTS = 128;
 
 // Resident blocks per SM of a pair-kernel variant (occupancy query).
 int pair_occupancy(int mode, int I);

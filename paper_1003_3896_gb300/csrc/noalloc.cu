@@ -210,6 +210,8 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
         s.jd = reinterpret_cast<float4 *>(b + OFF_J);
         s.jl = s.jd + 2 * N;
         s.part = reinterpret_cast<double *>(b + OFF_P);
+        s.part_elems = NA_SLOTS * 3 * NA_MAX_N;
+        s.pstride = n;                   // n <= NA_MAX_N: at least NA_SLOTS slots
         s.part_slots = NA_SLOTS;
         s.corr = reinterpret_cast<double *>(b + OFF_C);
         s.ng_bucket = reinterpret_cast<int *>(b + OFF_I);

@@ -83,6 +83,7 @@ __device__ __forceinline__ void ds_add(float &hi, float &lo, float t)
 struct Segment {
     int32_t k;        // cluster
     int64_t base;     // first pool slot of the cluster
+    int64_t lbase;    // its first linear body index (partial sums are stored by it)
     int32_t nk;       // bodies of the cluster
     int32_t b;        // i-block
     int32_t t0, t1;   // units [t0, t1) of the i-block
@@ -96,6 +97,7 @@ struct ParamTab {
     int32_t K;
     int64_t uoff[KC + 1];
     int64_t boff[KC];
+    int64_t noff[KC];
     double mu[KC];
     int32_t nk[KC];
     int32_t ntiles[KC];
@@ -131,6 +133,7 @@ __device__ __forceinline__ Segment segment_at(const Decomp &d, const ParamTab<KC
     s.J0 = d.rows ? 0 : s.t0 * d.jt;
     s.J1 = d.rows ? t.ntiles[s.k] * TILE : s.t1 * d.jt;
     s.base = t.boff[s.k];
+    s.lbase = t.noff[s.k];
     s.nk = t.nk[s.k];
     s.slot = g - d.owner(u0 + rb * nt);
     return s;
@@ -152,6 +155,7 @@ __device__ __forceinline__ Segment segment_at(const Decomp &d, const Clusters &c
     s.J0 = d.rows ? 0 : s.t0 * d.jt;
     s.J1 = d.rows ? c.ntiles[s.k] * TILE : s.t1 * d.jt;
     s.base = c.boff[s.k];
+    s.lbase = c.noff[s.k];
     s.nk = (int32_t)c.nk[s.k];
     s.slot = g - d.owner(u0 + rb * nt);
     return s;
@@ -258,7 +262,7 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P, MODE)) pair_sp_kernel(
     const float *__restrict__ xh, const float *__restrict__ yh, const float *__restrict__ zh,
     const float *__restrict__ xl, const float *__restrict__ yl, const float *__restrict__ zl,
     Clusters c, const __grid_constant__ TabOf<KC> tab, Decomp d, double G,
-    double *__restrict__ part, int64_t cap)
+    double *__restrict__ part, int64_t ps)
 {
     constexpr int I = 2 * P;
     constexpr bool FULL = (MODE == PM_DS_FULL);
@@ -394,11 +398,11 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P, MODE)) pair_sp_kernel(
         for (int kk = 0; kk < I; ++kk) {
             const int i = ibase + kk * TILE;
             if (i < n) {
-                double *o = part + (sg.slot * 3) * cap + base + i;
+                double *o = part + (sg.slot * 3) * ps + sg.lbase + i;
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc)
-                    o[cc * cap] = Gm * ((double)acc_sh[cc * I + kk][tid] +
-                                        (double)acc_sh[(3 + cc) * I + kk][tid]);
+                    o[cc * ps] = Gm * ((double)acc_sh[cc * I + kk][tid] +
+                                       (double)acc_sh[(3 + cc) * I + kk][tid]);
             }
         }
         u += sg.t1 - sg.t0;
@@ -566,7 +570,7 @@ __global__ void __launch_bounds__(TILE) pair_ff_kernel(
     const float *__restrict__ xh, const float *__restrict__ yh, const float *__restrict__ zh,
     const float *__restrict__ xl, const float *__restrict__ yl, const float *__restrict__ zl,
     Clusters c, const __grid_constant__ TabOf<KC> tab, Decomp d, double G,
-    double *__restrict__ part, int64_t cap)
+    double *__restrict__ part, int64_t ps)
 {
     constexpr int I = 2 * P;
     __shared__ __align__(16) float4 cbuf[WARPS][CH][4];
@@ -656,10 +660,10 @@ __global__ void __launch_bounds__(TILE) pair_ff_kernel(
         for (int k = 0; k < I; ++k) {
             const int i = ibase + k * TILE;
             if (i < n) {
-                double *o = part + (sg.slot * 3) * cap + base + i;
+                double *o = part + (sg.slot * 3) * ps + sg.lbase + i;
                 o[0] = Gm * dax[k];
-                o[cap] = Gm * day[k];
-                o[2 * cap] = Gm * daz[k];
+                o[ps] = Gm * day[k];
+                o[2 * ps] = Gm * daz[k];
             }
         }
         u += sg.t1 - sg.t0;
@@ -676,7 +680,7 @@ template <int I, bool POT>
 __global__ void __launch_bounds__(TILE) pair_fp64_kernel(
     const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
     const double *__restrict__ m, Clusters c, Decomp d, double G, double *__restrict__ part,
-    int64_t cap)
+    int64_t ps)
 {
     __shared__ double sx[TILE], sy[TILE], sz[TILE], sm[TILE];
     const int tid = threadIdx.x;
@@ -749,13 +753,13 @@ __global__ void __launch_bounds__(TILE) pair_fp64_kernel(
         for (int k = 0; k < I; ++k) {
             const int i = idx[k];
             if (i < n) {
-                double *p = part + (sg.slot * 3) * cap + base + i;
+                double *p = part + (sg.slot * 3) * ps + sg.lbase + i;
                 if (POT) {
                     p[0] = ax[k];
                 } else {
                     p[0] = G * ax[k];
-                    p[cap] = G * ay[k];
-                    p[2 * cap] = G * az[k];
+                    p[ps] = G * ay[k];
+                    p[2 * ps] = G * az[k];
                 }
             }
         }
@@ -807,6 +811,7 @@ static cudaError_t launch_sp(const DevState &s, const PairLaunch &pl, const Host
         for (int32_t q = 0; q < ht.K; ++q) {
             t.uoff[q] = ht.uoff[q];
             t.boff[q] = ht.boff[q];
+            t.noff[q] = ht.noff ? ht.noff[q] : 0;
             t.nk[q] = (int32_t)ht.nk[q];
             t.ntiles[q] = ht.ntiles[q];
             t.eps2f[q] = ht.eps2f[q];
@@ -815,7 +820,7 @@ static cudaError_t launch_sp(const DevState &s, const PairLaunch &pl, const Host
         t.uoff[ht.K] = ht.uoff[ht.K];
     }
     k<<<(unsigned)pl.d.G, TILE, 0, st>>>(s.jd, s.jl, s.xh, s.yh, s.zh, s.xl, s.yl, s.zl, s.cl, t,
-                                         pl.d, G, s.part, s.cap);
+                                         pl.d, G, s.part, s.pstride);
     return cudaGetLastError();
 }
 
@@ -860,7 +865,8 @@ cudaError_t launch_pair(const DevState &s, const PairLaunch &pl, const HostTab &
     if (pl.mode == PM_FP64) {
         dp_kernel_t k = dp_variant(pl.I);
         if (!k) return cudaErrorInvalidValue;
-        k<<<(unsigned)pl.d.G, TILE, 0, st>>>(s.x, s.y, s.z, s.m, s.cl, pl.d, G, s.part, s.cap);
+        k<<<(unsigned)pl.d.G, TILE, 0, st>>>(s.x, s.y, s.z, s.m, s.cl, pl.d, G, s.part,
+                                             s.pstride);
         return cudaGetLastError();
     }
     switch (kc_for(ht.K)) {
@@ -873,7 +879,7 @@ cudaError_t launch_pair(const DevState &s, const PairLaunch &pl, const HostTab &
 cudaError_t launch_potential(const DevState &s, const Decomp &d, cudaStream_t st)
 {
     pair_fp64_kernel<1, true><<<(unsigned)d.G, TILE, 0, st>>>(s.x, s.y, s.z, s.m, s.cl, d, 1.0,
-                                                               s.part, s.cap);
+                                                               s.part, s.pstride);
     return cudaGetLastError();
 }
 
