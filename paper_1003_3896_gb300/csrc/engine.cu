@@ -294,6 +294,8 @@ int set_layout(ClusterSet &C, int ipb, cudaStream_t st, int jt)
 
 // ---- plans -------------------------------------------------------------------
 
+bool sp_family(int mode) { return mode == PM_DS_NEAR || mode == PM_DS_FULL || mode == PM_FP32; }
+
 int mode_of(int precision)
 {
     switch (precision) {
@@ -365,6 +367,7 @@ int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan
     int64_t G = want < W ? want : W;   // at least one unit per block
     const int64_t slot_cap = part_slot_cap(P, C.n);
     pl.pl.d = make_decomp(W, C.max_ntiles, TILE * I, G, slot_cap, jt);
+    pl.pl.d.fpart = sp_family(pl.pl.mode) ? 1 : 0;
     for (int32_t k = 0; k < C.K; ++k)
         if (C.eps2d[k] == 0.0) pl.pl.d.mask_self = 1;
     int occ_pot = pair_occupancy(PM_FP64, 1);

@@ -405,13 +405,68 @@ cudaError_t launch_split(const DevState &s, cudaStream_t st)
 // SB: slots loaded together (a grid run in waves gives an i-block tens of
 // slots; an ensemble of small clusters a few, where a narrower batch keeps
 // registers, and so resident warps, for the memory latency)
+// Add the float pair (p, e) to the float-float number (h, l): Knuth's
+// two-sum of the high parts, the error and the low parts folded in, then
+// Dekker's fast two-sum to renormalise.
+__device__ __forceinline__ void ff_add(float &h, float &l, float p, float e)
+{
+    const float s = __fadd_rn(h, p);
+    const float bp = __fsub_rn(s, h);
+    const float err = __fadd_rn(__fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(p, bp)),
+                                __fadd_rn(l, e));
+    h = __fadd_rn(s, err);
+    l = __fsub_rn(err, __fsub_rn(h, s));
+}
+
+// Float-pair partial sums (Decomp::fpart): added in slot order in
+// float-float arithmetic, SB loads at a time, then one conversion to double.
 template <int SB>
+__device__ __forceinline__ void sum_slots_ff(const DevState &s, int64_t count, int64_t t,
+                                             double &ax, double &ay, double &az)
+{
+    const float2 *part2 = reinterpret_cast<const float2 *>(s.part);
+    float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f, hz = 0.f, lz = 0.f;
+    for (int64_t k0 = 0; k0 < count; k0 += SB) {
+        float2 bx[SB], by[SB], bz[SB];
+#pragma unroll
+        for (int q = 0; q < SB; ++q) {
+            bx[q] = by[q] = bz[q] = make_float2(0.f, 0.f);
+            if (k0 + q < count) {
+                const float2 *p = part2 + ((k0 + q) * 3) * s.pstride + t;
+                bx[q] = p[0];
+                by[q] = p[s.pstride];
+                bz[q] = p[2 * s.pstride];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < SB; ++q)
+            if (k0 + q < count) {
+                ff_add(hx, lx, bx[q].x, bx[q].y);
+                ff_add(hy, ly, by[q].x, by[q].y);
+                ff_add(hz, lz, bz[q].x, bz[q].y);
+            }
+    }
+    ax = (double)hx + (double)lx;
+    ay = (double)hy + (double)ly;
+    az = (double)hz + (double)lz;
+}
+
+template <int SB, bool FP>
 __device__ __forceinline__ void sum_slots(const DevState &s, const Decomp &d, const BodyRef &r,
                                           int64_t t, double &ax, double &ay, double &az)
 {
     int64_t first, count;
     iblock_slots(d, s.cl, r.k, r.li, first, count);
     (void)first;
+    if (FP) {
+        sum_slots_ff<SB>(s, count, t, ax, ay, az);
+        if (s.corr) {
+            ax += s.corr[r.gi];
+            ay += s.corr[s.cap + r.gi];
+            az += s.corr[2 * s.cap + r.gi];
+        }
+        return;
+    }
     ax = ay = az = 0.0;
     // slots in order, SB at a time so the loads are in flight together
     for (int64_t k0 = 0; k0 < count; k0 += SB) {
@@ -443,7 +498,7 @@ __device__ __forceinline__ void sum_slots(const DevState &s, const Decomp &d, co
 
 // EXT: the external field is on (a separate variant keeps its registers out
 // of the field-free kick).
-template <bool EXT, int SB>
+template <bool EXT, int SB, bool FP>
 __global__ void kick_drift_kernel(DevState s, Decomp d, double wk, double wd, int do_kick,
                                   int do_split, ExtField ext, int64_t t0, int64_t t1)
 {
@@ -456,7 +511,7 @@ __global__ void kick_drift_kernel(DevState s, Decomp d, double wk, double wd, in
     double vx = s.vx[i], vy = s.vy[i], vz = s.vz[i];
     if (do_kick) {
         double ax, ay, az;
-        sum_slots<SB>(s, d, r, t, ax, ay, az);
+        sum_slots<SB, FP>(s, d, r, t, ax, ay, az);
         if (EXT) {
             double ex, ey, ez;
             field_accel(ext, x, y, z, ex, ey, ez);
@@ -503,20 +558,25 @@ cudaError_t launch_kick_drift_range(const DevState &s, const Decomp &d, double w
     const int t = ot_for(m) < 128 ? ot_for(m) : 128;
     const unsigned nb = blocks_for(m, t);
     const bool narrow = d.slots <= 4;   // every i-block has at most 4 slots
-    if (ext.on) {
-        if (narrow)
-            kick_drift_kernel<true, 4><<<nb, t, 0, st>>>(s, d, wk, wd, do_kick, do_split, ext, t0, t1);
-        else
-            kick_drift_kernel<true, 8><<<nb, t, 0, st>>>(s, d, wk, wd, do_kick, do_split, ext, t0, t1);
+#define NB_KD(E, B, F) kick_drift_kernel<E, B, F><<<nb, t, 0, st>>>(s, d, wk, wd, do_kick, do_split, ext, t0, t1)
+    if (d.fpart) {
+        if (ext.on) {
+            if (narrow) NB_KD(true, 4, true); else NB_KD(true, 8, true);
+        } else {
+            if (narrow) NB_KD(false, 4, true); else NB_KD(false, 8, true);
+        }
     } else {
-        if (narrow)
-            kick_drift_kernel<false, 4><<<nb, t, 0, st>>>(s, d, wk, wd, do_kick, do_split, ext, t0, t1);
-        else
-            kick_drift_kernel<false, 8><<<nb, t, 0, st>>>(s, d, wk, wd, do_kick, do_split, ext, t0, t1);
+        if (ext.on) {
+            if (narrow) NB_KD(true, 4, false); else NB_KD(true, 8, false);
+        } else {
+            if (narrow) NB_KD(false, 4, false); else NB_KD(false, 8, false);
+        }
     }
+#undef NB_KD
     return cudaGetLastError();
 }
 
+template <bool FP>
 __global__ void accel_out_kernel(DevState s, Decomp d, ExtField ext, double *__restrict__ out,
                                  int64_t t0, int64_t t1)
 {
@@ -525,7 +585,7 @@ __global__ void accel_out_kernel(DevState s, Decomp d, ExtField ext, double *__r
     if (t >= t1) return;
     const BodyRef r = body_at(s.cl, t);
     double ax, ay, az;
-    sum_slots<8>(s, d, r, t, ax, ay, az);
+    sum_slots<8, FP>(s, d, r, t, ax, ay, az);
     if (ext.on) {
         double ex, ey, ez;
         field_accel(ext, s.x[r.gi], s.y[r.gi], s.z[r.gi], ex, ey, ez);
@@ -549,7 +609,10 @@ cudaError_t launch_accel_out_range(const DevState &s, const Decomp &d, const Ext
                                    double *out_aos, int64_t t0, int64_t t1, cudaStream_t st)
 {
     const int t = ot_for(t1 - t0);
-    accel_out_kernel<<<blocks_for(t1 - t0, t), t, 0, st>>>(s, d, ext, out_aos, t0, t1);
+    if (d.fpart)
+        accel_out_kernel<true><<<blocks_for(t1 - t0, t), t, 0, st>>>(s, d, ext, out_aos, t0, t1);
+    else
+        accel_out_kernel<false><<<blocks_for(t1 - t0, t), t, 0, st>>>(s, d, ext, out_aos, t0, t1);
     return cudaGetLastError();
 }
 

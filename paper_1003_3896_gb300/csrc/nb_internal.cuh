@@ -141,6 +141,11 @@ struct Decomp {
     // cluster (for eps > 0 it is exactly zero anyway), which keeps the
     // decision a launch-wide constant
     int32_t mask_self = 0;
+    // 1: the partial sums are float pairs (hi, lo), the single-precision pair
+    // kernels' double-single sums already scaled by G m, which consumers add
+    // in float-float arithmetic on the FP32 pipes; 0: doubles (FP64 and
+    // float-float kernels, potential sums)
+    int32_t fpart = 0;
 
     // 1 when (W + 1) (G + 1) < 2^32: U and owner then divide in 32 bits (a
     // 64-bit division costs tens of instructions, on the kick's hot path)
@@ -188,6 +193,9 @@ struct ExtField {
 // 2 = pure float, 3 = double, 4 = float-float (every operation on hi + lo
 // pairs of floats, FP64-class accuracy on the FP32 pipes).
 enum PairMode { PM_DS_NEAR = 0, PM_DS_FULL = 1, PM_FP32 = 2, PM_FP64 = 3, PM_DD = 4 };
+// The single-precision family (pair_sp_kernel): its partial sums are float
+// pairs (Decomp::fpart).
+bool sp_family(int mode);
 
 struct PairLaunch {
     int mode;

@@ -477,6 +477,7 @@ int nb_accel_range(nb_ctx *c, int64_t i0, int64_t i1, double *acc_out)
     rl.d = make_decomp(W, c->set.max_ntiles, ipb, G, part_slot_cap(c->pool, c->n), TILE, 1);
     rl.d.b0 = b0;
     rl.d.mask_self = pl.pl.d.mask_self;
+    rl.d.fpart = pl.pl.d.fpart;
     const DevState s = view(c->pool, c->set, pl);
     const int64_t uoff[2] = {0, W};
     HostTab ht;
@@ -517,6 +518,7 @@ int nb_substep_range(nb_ctx *c, int64_t i0, int64_t i1, double kick, double drif
     rl.d = make_decomp(W, c->set.max_ntiles, ipb, G, part_slot_cap(c->pool, c->n), TILE, 1);
     rl.d.b0 = b0;
     rl.d.mask_self = pl.pl.d.mask_self;
+    rl.d.fpart = pl.pl.d.fpart;
     const DevState s = view(c->pool, c->set, pl);
     if (kick != 0.0) {
         // the force evaluation of nb_accel_range (whole i-block rows, each

@@ -267,6 +267,7 @@ extern "C" int nb_accel_static(const nb_params *p, int64_t n, const double *d_po
         if (W / 2 < G) G = W / 2 > 0 ? W / 2 : 1;
         pl.d = make_decomp(W, nt, ipb, G, NA_SLOTS);
         pl.d.mask_self = p->eps == 0.0 ? 1 : 0;
+        pl.d.fpart = sp_family(pl.mode) ? 1 : 0;
 
         Clusters &c = s.cl;
         c.K = 1;

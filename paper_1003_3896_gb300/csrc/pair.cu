@@ -393,16 +393,26 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P, MODE)) pair_sp_kernel(
             }
         }
 
+        // partial sums as float pairs: the double-single sum times G m (m the
+        // cluster's common mass in the uniform-mass form), a float-float
+        // product (FMA-exact h gh plus the cross terms), normalised
         const double Gm = UM ? G * (KC > 0 ? tab.mu[sg.k] : c.mu[sg.k]) : G;
+        const float gh = __double2float_rn(Gm), gl = __double2float_rn(Gm - (double)gh);
+        float2 *part2 = reinterpret_cast<float2 *>(part);
 #pragma unroll
         for (int kk = 0; kk < I; ++kk) {
             const int i = ibase + kk * TILE;
             if (i < n) {
-                double *o = part + (sg.slot * 3) * ps + sg.lbase + i;
+                float2 *o = part2 + (sg.slot * 3) * ps + sg.lbase + i;
 #pragma unroll
-                for (int cc = 0; cc < 3; ++cc)
-                    o[cc * ps] = Gm * ((double)acc_sh[cc * I + kk][tid] +
-                                       (double)acc_sh[(3 + cc) * I + kk][tid]);
+                for (int cc = 0; cc < 3; ++cc) {
+                    const float h = acc_sh[cc * I + kk][tid], l = acc_sh[(3 + cc) * I + kk][tid];
+                    const float pr = __fmul_rn(h, gh);
+                    float e = __fmaf_rn(h, gh, -pr);
+                    e = __fmaf_rn(h, gl, __fmaf_rn(l, gh, e));
+                    const float s = __fadd_rn(pr, e);
+                    o[cc * ps] = make_float2(s, __fsub_rn(e, __fsub_rn(s, pr)));
+                }
             }
         }
         u += sg.t1 - sg.t0;

@@ -54,10 +54,14 @@ def test_each_result_same_alone_and_in_mix(nbs):
         assert stats["pair_ms"][2] > 0 and stats["pair_interactions"][2] > 0
         assert stats["pair_interactions"][0] == 0
         assert sum(stats["pair_interactions"]) == stats["interactions"]
-        # busy time: the union of launch intervals, at most their sum
+        # busy time: the union of launch intervals, at most their sum (the
+        # intervals are float milliseconds after a reference event: allow a
+        # few of their ulps)
+        slack = 1e-3
         for a in (1, 2):
-            assert 0 < stats["pair_busy_ms"][a] <= stats["pair_ms"][a] * (1 + 1e-6)
-        assert max(stats["pair_busy_ms"]) <= stats["pair_busy_ms_any"] <= sum(stats["pair_busy_ms"]) * (1 + 1e-6)
+            assert 0 < stats["pair_busy_ms"][a] <= stats["pair_ms"][a] * (1 + 1e-4) + slack
+        assert (max(stats["pair_busy_ms"]) <= stats["pair_busy_ms_any"] + slack
+                and stats["pair_busy_ms_any"] <= sum(stats["pair_busy_ms"]) + slack)
         results = [srv.result(j) for j in ids]
     for k, ((n, order, prec, dt, steps), (x, v)) in enumerate(zip(JOBS, results)):
         pos, vel, m, eps = ic(n, 500 + k)
