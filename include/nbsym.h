@@ -11,7 +11,10 @@
  *  - Plain C types only.  Host arrays are borrowed for the duration of the
  *    call; the library copies what it needs.  Output buffers belong to the
  *    caller.  Device-pointer variants (suffix _device) take pointers to
- *    device memory on the context's device; they are also borrowed.
+ *    device memory on the context's device; they are also borrowed.  They
+ *    work on the context's stream: device memory that other streams write
+ *    must be complete before the call (synchronise those streams or order
+ *    them with events); when the call returns, what it wrote is complete.
  *  - Positions, velocities and accelerations are float64, n rows of (x, y, z)
  *    interleaved (row-major (n, 3)); masses are float64 (n,).
  *  - Accelerations, never forces: the m_i of eq. 2 / eq. 5 is divided out.

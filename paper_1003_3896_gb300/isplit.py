@@ -145,13 +145,20 @@ def gather(ranks, exchange):
 
 
 class ContextBackend:
-    """A one-cluster nbsym.Context as a rank's backend (device tensors)."""
+    """A one-cluster nbsym.Context as a rank's backend (device tensors).
+
+    The context runs on its own stream, torch (the exchange's slicing,
+    concatenation and collectives) on torch's current stream: a tensor torch
+    produced is waited for before the context reads it, and the context's
+    calls return with their work done (they synchronise its stream)."""
 
     def __init__(self, ctx, device):
         import torch
+        self.torch = torch
         self.ctx, self.n = ctx, ctx.n
-        self._pos = torch.empty((self.n, 3), dtype=torch.float64, device=device)
-        self._vel = torch.empty((self.n, 3), dtype=torch.float64, device=device)
+        self.device = torch.device(device)
+        self._pos = torch.empty((self.n, 3), dtype=torch.float64, device=self.device)
+        self._vel = torch.empty((self.n, 3), dtype=torch.float64, device=self.device)
 
     def substep_range(self, i0, i1, kick, drift):
         self.ctx.substep_range(i0, i1, kick, drift)
@@ -164,8 +171,13 @@ class ContextBackend:
         self.ctx.get_state_device(None, self._vel)
         return self._vel
 
+    def _ready(self, t):
+        t = t.contiguous()
+        self.torch.cuda.current_stream(self.device).synchronize()
+        return t
+
     def set_positions(self, t):
-        self.ctx.set_state_device(t.contiguous(), None)
+        self.ctx.set_state_device(self._ready(t), None)
 
     def set_velocities(self, t):
-        self.ctx.set_state_device(None, t.contiguous())
+        self.ctx.set_state_device(None, self._ready(t))

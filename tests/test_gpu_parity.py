@@ -321,6 +321,7 @@ def test_device_pointer_io_matches_host(nbs):
         tp = torch.from_numpy(pos).cuda()
         tv = torch.from_numpy(vel).cuda()
         tm = torch.from_numpy(m).cuda()
+        torch.cuda.synchronize()   # the context works on its own stream
         c.load_device(n, tp, tv, tm)
         out = torch.empty((n, 3), dtype=torch.float64, device="cuda")
         c.accel_device(out)
