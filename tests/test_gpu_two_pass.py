@@ -185,6 +185,27 @@ def test_per_body_error_bound(nbs, orc, n, seed):
     assert worst[1e-9][0] > 2 * PER_BODY_TOL, worst
 
 
+def test_short_near_radius_fails_per_body_not_global(nbs, orc):
+    """A correction that misses part of its pairs (near radius 4x too small)
+    on the N = 16384 orbit system, every body compared: the global norm still
+    meets its 1e-6 bar (measured 3.9e-7), the per-body bound does not
+    (measured worst 1.1e-5), while the default radius meets both."""
+    n = 16384
+    pos, vel, m, eps = orbit(n, 0)
+    ref = orc.accel_int(pos, m, 1.0, eps)
+    ext = orc.ext_accel(orc.Params(eps=eps, ext_on=True), pos)
+    rms = math.sqrt((ref ** 2).sum(1).mean())
+    res = {}
+    for nf in (0.0, 0.1):
+        with nbs.Context(n, eps=eps, precision="ds_near", ext_on=True, near_frac=nf) as c:
+            c.load(pos, vel, m)
+            a = c.accel() - ext
+        res[nf] = (rel_rms(a, ref), per_body(a, ref, rms).max())
+    assert res[0.0][0] <= 1e-6 and res[0.0][1] <= PER_BODY_TOL, res
+    assert res[0.1][0] <= 1e-6, res                 # the global norm does not see it
+    assert res[0.1][1] > PER_BODY_TOL, res          # the per-body bound does
+
+
 def test_per_body_error_c3_sweep(nbs, orc):
     """N = 262144 with Salpeter masses, eps = 1e-4 (the accuracy sweep's
     system): every compared body of the two-pass result within the per-body
