@@ -437,7 +437,9 @@ typedef struct nb_server nb_server;
 typedef struct {
     int device;
     double hbm_budget_bytes;  /* device memory for resident state (> 0);
-                                 about 460 bytes per body slot */
+                                 about 436 bytes per body slot, plus the
+                                 groups' partial sums beyond that share (at
+                                 most ~67 MB per group of the six) */
     int max_jobs;             /* resident jobs at most, 1..65536 */
     double G;                 /* as nb_params */
     int ext_on;

@@ -29,7 +29,14 @@ const char *last_error() { return g_err.c_str(); }
 
 // ---- pool --------------------------------------------------------------------
 
-int pool_create(Pool &P, int device, int64_t cap)
+int64_t part_elems_for(const Pool &P, int64_t n)
+{
+    const int64_t giw = (int64_t)P.num_sms * MAX_WAVES * 3072;
+    const int64_t slots_n = giw + 2 * n, cap_n = MAX_PART_SLOTS * n;
+    return 3 * (slots_n < cap_n ? slots_n : cap_n);
+}
+
+int pool_create(Pool &P, int device, int64_t cap, bool own_part)
 {
     P.device = device;
     P.cap = cap;
@@ -45,9 +52,10 @@ int pool_create(Pool &P, int device, int64_t cap)
     // n, linear body index), so 3 (giw + 2 cap) doubles give a set of n
     // bodies (giw + 2 cap) / n slots: a small set in a large pool (a serving
     // group) gets as many as a context of its own size.  make_decomp
-    // shrinks a grid that would need more than a set has.
-    const int64_t giw = (int64_t)P.num_sms * MAX_WAVES * 3072;
-    s.part_elems = 3 * (giw + 2 * cap);
+    // shrinks a grid that would need more than a set has.  Sets that run
+    // concurrently in one pool (the serving loop's groups) cannot share this
+    // storage: such a pool has none, and each set reserves its own.
+    s.part_elems = own_part ? part_elems_for(P, cap) : 0;
     s.part_slots = 0;
     s.pstride = 0;
     s.red_len = 0;
@@ -65,7 +73,7 @@ int pool_create(Pool &P, int device, int64_t cap)
     A((void **)&s.xl, c4); A((void **)&s.yl, c4); A((void **)&s.zl, c4);
     A((void **)&s.jd, 2 * (size_t)cap * sizeof(float4));
     A((void **)&s.jl, 2 * (size_t)cap * sizeof(float4));
-    A((void **)&s.part, (size_t)s.part_elems * 8);
+    if (s.part_elems > 0) A((void **)&s.part, (size_t)s.part_elems * 8);
     A((void **)&s.corr, 3 * c8);
     A((void **)&P.stage, 7 * c8);
     if (!ok) {
@@ -146,12 +154,34 @@ int set_create(ClusterSet &C, int32_t kcap, int64_t body_cap)
     return NB_OK;
 }
 
+int set_reserve_part(ClusterSet &C, int64_t elems, cudaStream_t st)
+{
+    if (C.part && C.part_elems >= elems) return NB_OK;
+    const int64_t want = C.part ? (elems > C.part_elems * 3 / 2 ? elems : C.part_elems * 3 / 2)
+                                : elems;
+    if (C.part) {
+        NB_TRY(cudaFreeAsync(C.part, st));
+        C.part = nullptr;
+        C.part_elems = 0;
+    }
+    void *q = nullptr;
+    if (cudaMallocAsync(&q, (size_t)want * 8, st) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(NB_ENOMEM, "partial-sum storage: %lld bytes not available",
+                         (long long)want * 8);
+    }
+    C.part = static_cast<double *>(q);
+    C.part_elems = want;
+    return NB_OK;
+}
+
 void set_destroy(ClusterSet &C)
 {
     void *ptrs[] = {C.dmem,    C.red,   C.ng_bucket, C.ng_entry, C.ng_total, C.flag,
                     C.cid,     C.ng_spos, C.ng_slo,  C.ng_slot,  C.ng_rank};
     for (void *q : ptrs)
         if (q) cudaFree(q);
+    if (C.part) cudaFree(C.part);
     if (C.fork) cudaEventDestroy(C.fork);
     if (C.join) cudaEventDestroy(C.join);
     if (C.side) cudaStreamDestroy(C.side);
@@ -365,7 +395,7 @@ int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan
     for (int32_t k = 0; k < C.K && pl.pl.um; ++k) pl.pl.um = C.mu[k] > 0;
     const int64_t W = C.uoff[C.K];
     int64_t G = want < W ? want : W;   // at least one unit per block
-    const int64_t slot_cap = part_slot_cap(P, C.n);
+    const int64_t slot_cap = part_slot_cap(P, C);
     pl.pl.d = make_decomp(W, C.max_ntiles, TILE * I, G, slot_cap, jt);
     pl.pl.d.fpart = sp_family(pl.pl.mode) ? 1 : 0;
     for (int32_t k = 0; k < C.K; ++k)
@@ -396,9 +426,10 @@ DevState view(const Pool &P, const ClusterSet &C, const Plan &pl)
     return s;
 }
 
-int64_t part_slot_cap(const Pool &P, int64_t n)
+int64_t part_slot_cap(const Pool &P, const ClusterSet &C)
 {
-    const int64_t per = n > 0 ? P.s.part_elems / (3 * n) : MAX_PART_SLOTS;
+    const int64_t elems = C.part ? C.part_elems : P.s.part_elems;
+    const int64_t per = C.n > 0 ? elems / (3 * C.n) : MAX_PART_SLOTS;
     return per < MAX_PART_SLOTS ? per : MAX_PART_SLOTS;
 }
 
@@ -407,8 +438,12 @@ DevState view(const Pool &P, const ClusterSet &C, int precision)
     DevState s = P.s;
     s.cl = C.cl;
     s.n = C.n;
+    if (C.part) {
+        s.part = C.part;
+        s.part_elems = C.part_elems;
+    }
     s.pstride = C.n > 0 ? C.n : 1;
-    s.part_slots = part_slot_cap(P, C.n);
+    s.part_slots = part_slot_cap(P, C);
     s.diag = C.diag;
     s.red = C.red;
     s.red_len = C.scap * 16;

@@ -36,7 +36,13 @@ struct Pool {
     DevState s;
     double *stage = nullptr;   // (7 cap) staging for interleaved host transfers
 };
-int pool_create(Pool &P, int device, int64_t cap);
+// own_part: allocate the partial-sum storage of a single cluster set (a
+// context); a pool shared by concurrent sets (the serving loop's groups)
+// leaves it out, and each set reserves its own (set_reserve_part).
+int pool_create(Pool &P, int device, int64_t cap, bool own_part = true);
+// Partial-sum doubles a set of n bodies may need: 3 min(giw + 2 n,
+// MAX_PART_SLOTS n), giw the widest grid's i-rows (SMs x MAX_WAVES x 3072).
+int64_t part_elems_for(const Pool &P, int64_t n);
 void pool_destroy(Pool &P);
 
 // Tables of one cluster set in a pool (host copy + device copy).
@@ -69,8 +75,16 @@ struct ClusterSet {
     // pair kernel (it reads only the float planes, and writes only corr)
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    // the set's own partial-sum storage (NULL: the pool's); sets that run
+    // concurrently in one pool must each have their own
+    double *part = nullptr;
+    int64_t part_elems = 0;
 };
 int set_create(ClusterSet &C, int32_t kcap, int64_t body_cap);
+// Give the set its own partial-sum storage of at least elems doubles, grown
+// (stream-ordered allocation on st) when smaller; none of the set's work may
+// be in flight.
+int set_reserve_part(ClusterSet &C, int64_t elems, cudaStream_t st);
 void set_destroy(ClusterSet &C);
 // Clusters k = 0..K-1 at pool slots [boff[k], boff[k] + nk[k]), softening
 // eps[k] and step scale dts[k] (NULL: 1).  Host only; set_layout uploads.
@@ -154,8 +168,9 @@ DevState view(const Pool &P, const ClusterSet &C, const Plan &pl);
 // of at most DS_FULL_MAX_PAIRS pairs forms the double-single difference on
 // every pair (no near-pair pass).
 int plan_mode(const ClusterSet &C, int precision);
-// Partial slots per body a set of n bodies has in the pool's storage.
-int64_t part_slot_cap(const Pool &P, int64_t n);
+// Partial slots per body the set has in its storage (its own, else the
+// pool's) for its current bodies.
+int64_t part_slot_cap(const Pool &P, const ClusterSet &C);
 int mode_of(int precision);
 bool float_planes(int precision);
 

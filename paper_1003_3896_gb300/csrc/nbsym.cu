@@ -474,7 +474,7 @@ int nb_accel_range(nb_ctx *c, int64_t i0, int64_t i1, double *acc_out)
     const int64_t b0 = i0 / ipb, b1 = (i1 + ipb - 1) / ipb, W = b1 - b0;
     int64_t G = (int64_t)c->pool.num_sms * rl.blocks_per_sm;
     if (G > W) G = W;
-    rl.d = make_decomp(W, c->set.max_ntiles, ipb, G, part_slot_cap(c->pool, c->n), TILE, 1);
+    rl.d = make_decomp(W, c->set.max_ntiles, ipb, G, part_slot_cap(c->pool, c->set), TILE, 1);
     rl.d.b0 = b0;
     rl.d.mask_self = pl.pl.d.mask_self;
     rl.d.fpart = pl.pl.d.fpart;
@@ -515,7 +515,7 @@ int nb_substep_range(nb_ctx *c, int64_t i0, int64_t i1, double kick, double drif
     const int64_t b0 = i0 / ipb, b1 = (i1 + ipb - 1) / ipb, W = b1 - b0;
     int64_t G = (int64_t)c->pool.num_sms * rl.blocks_per_sm;
     if (G > W) G = W;
-    rl.d = make_decomp(W, c->set.max_ntiles, ipb, G, part_slot_cap(c->pool, c->n), TILE, 1);
+    rl.d = make_decomp(W, c->set.max_ntiles, ipb, G, part_slot_cap(c->pool, c->set), TILE, 1);
     rl.d.b0 = b0;
     rl.d.mask_self = pl.pl.d.mask_self;
     rl.d.fpart = pl.pl.d.fpart;

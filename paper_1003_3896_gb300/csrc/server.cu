@@ -77,8 +77,11 @@ struct Group {
 
 constexpr size_t PAIR_IV_CAP = (size_t)1 << 20;
 
-// Bytes of device memory the pool and the group scratch use per body slot.
-constexpr double BYTES_PER_BODY = 7 * 8 + 7 * 4 + 64 + 3 * 3 * 8 + 3 * 8 + 7 * 8 + 5 * (16 + 16);
+// Bytes of device memory the pool and the group scratch use per body slot:
+// state, float planes, j-stream, near-pair correction, staging, near-pair
+// scratch; plus the groups' partial sums, 2 x 24 bytes per body of a group
+// beyond a fixed part of at most 3 x 8 x SMs x 6 x 3072 bytes per group.
+constexpr double BYTES_PER_BODY = 7 * 8 + 7 * 4 + 64 + 2 * 3 * 8 + 3 * 8 + 7 * 8 + 5 * (16 + 16);
 
 }  // namespace
 
@@ -298,6 +301,8 @@ int launch_step(nb_server *s, Group &g)
         int rc = set_define(g.set, (int32_t)nk.size(), boff.data(), nk.data(), eps.data(),
                             dts.data());
         g.set.mu = mu;
+        // the group's own partial sums: groups step concurrently
+        if (!rc) rc = set_reserve_part(g.set, part_elems_for(s->pool, g.set.n), g.stream);
         if (!rc) rc = plan_make(s->pool, g.set, g.precision, g.stream, g.plan);
         if (rc) return rc;
         g.dirty = false;
@@ -431,7 +436,7 @@ int nb_server_create(const nb_server_params *p, nb_server **out)
         return set_error(NB_EINVAL, "HBM budget too small for one body");
     }
     s->cap = cap;
-    int rc = pool_create(s->pool, p->device, cap);
+    int rc = pool_create(s->pool, p->device, cap, /*own_part=*/false);
     for (int g = 0; g < 6 && !rc; ++g) {
         Group &gr = s->groups[g];
         gr.precision = g < 2 ? NB_FP64 : (g < 4 ? NB_DS : NB_DD);

@@ -104,6 +104,31 @@ def test_two_pass_group_same_alone_and_in_mix(nbs, orc):
             assert np.abs(x - rx).max() <= 1e-6, np.abs(x - rx).max()
 
 
+def test_concurrent_groups_do_not_share_scratch(nbs):
+    """Four groups (mixed and float-float, orders 2 and 6) of sizeable jobs
+    step concurrently on their own streams for tens of steps: each group's
+    pair-kernel partial sums and near-pair scratch are its own, so every
+    result equals the job run alone."""
+    jobs = [(20000, 2, "ds", 30), (18000, 6, "ds", 6), (9000, 2, "fp64", 20),
+            (8000, 6, "fp64", 4), (15000, 2, "ds", 25), (7000, 6, "ds", 8)]
+    with nbs.Server(hbm_budget_bytes=4e9, max_jobs=16) as srv:
+        ids = []
+        for k, (n, order, prec, steps) in enumerate(jobs):
+            pos, vel, m, eps = ic(n, 990 + k)
+            ids.append(srv.submit(pos, vel, m, order, 1 / 1024, steps, precision=prec, eps=eps))
+        st = [srv.wait(j, 600) for j in ids]
+        assert all(s["state"] == nbs.JOB_DONE for s in st), st
+        results = [srv.result(j) for j in ids]
+    for k, ((n, order, prec, steps), (x, v)) in enumerate(zip(jobs, results)):
+        pos, vel, m, eps = ic(n, 990 + k)
+        with nbs.Context(n, eps=eps, precision="dd" if prec == "fp64" else prec) as c:
+            c.load(pos, vel, m)
+            c.step(order, 1 / 1024, steps)
+            xa, _ = c.get_state()
+        tol = 1e-10 if prec == "fp64" else 1e-6
+        assert np.abs(x - xa).max() <= tol, (k, np.abs(x - xa).max())
+
+
 def test_admission_respects_budget_and_slots(nbs):
     """A budget for about two 1000-body jobs: never more than two resident,
     every job still completes in arrival order of admission."""
