@@ -426,7 +426,8 @@ void nb_destroy(nb_ctx *ctx);
  * same step (Sect. 3.1).  A scheduler thread admits queued jobs in arrival
  * order when a resident-job slot is free and the state pool (sized from the
  * HBM budget) has a contiguous range for the job's bodies.  Resident jobs are
- * grouped by (precision, order); each group advances one step at a time with
+ * grouped by (precision, order, and size: below 16384 bodies or not); each
+ * group advances one step at a time with
  * one pair-kernel launch per force evaluation covering all its jobs, on its
  * own stream, so groups overlap on the device.  Jobs join and leave a group
  * between two of its steps (continuous batching).  Each job is an independent
@@ -439,7 +440,7 @@ typedef struct {
     double hbm_budget_bytes;  /* device memory for resident state (> 0);
                                  about 436 bytes per body slot, plus the
                                  groups' partial sums beyond that share (at
-                                 most ~67 MB per group of the six) */
+                                 most ~67 MB per group of the twelve) */
     int max_jobs;             /* resident jobs at most, 1..65536 */
     double G;                 /* as nb_params */
     int ext_on;

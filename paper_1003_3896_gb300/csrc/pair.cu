@@ -425,8 +425,9 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P, MODE)) pair_sp_kernel(
 // Knuth's two-sum, Dekker's fast two-sum and FMA-exact products, packed over two
 // i bodies per f32x2 instruction.  Coordinates are the double-single split of
 // x - c (the paper's 14-digit format, Sect. 5.2); the coordinate difference,
-// r^2 + eps^2, 1/sqrt (a float rsqrt estimate refined by one Newton step in
-// float-float), m / r^3 and the sums are all float-float.  Against a plain FP64
+// r^2 + eps^2, (r^2 + eps^2)^(-3/2) (a float rsqrt estimate y0 corrected by
+// the series of (1 - v)^(-3/2) in the residual v = 1 - (r^2 + eps^2) y0^2),
+// m / r^3 and the sums are all float-float.  Against a plain FP64
 // sum it agrees to ~1e-14 relative (the 48-bit coordinates alone account for
 // that), so it stands in for the FP64 pipe, which on this GPU runs at 1/77 of
 // the FP32 rate.  The sums of r^2 + eps^2, whose terms are all non-negative,
@@ -503,7 +504,8 @@ template <int P, bool MASK, bool UM>
 __device__ __forceinline__ void chunk_pass_ff(const float4 (*cb)[4], int j0, int ibase,
                                               FFI<P> &q, float2 e2h, float2 e2l)
 {
-    const float2 one = make_float2(1.f, 1.f), half = make_float2(0.5f, 0.5f);
+    const float2 one = make_float2(1.f, 1.f);
+    const float2 c32 = make_float2(1.5f, 1.5f), c158 = make_float2(1.875f, 1.875f);
 #pragma unroll 2
     for (int jj = 0; jj < CH; ++jj) {
         const float4 A = cb[jj][0], B = cb[jj][1], Cl = cb[jj][2], D = cb[jj][3];
@@ -526,30 +528,31 @@ __device__ __forceinline__ void chunk_pass_ff(const float4 (*cb)[4], int j0, int
             pos_two_sum2(px, py, s1, t1);
             pos_two_sum2(s1, pz, s2, t2);
             pos_two_sum2(s2, e2h, s3, t3);
-            float2 err = __fadd2_rn(__fadd2_rn(__fadd2_rn(ex, ey), __fadd2_rn(ez, e2l)),
-                                    __fadd2_rn(__fadd2_rn(t1, t2), t3));
-            float2 rh, rl;
-            fast_two_sum2(s3, err, rh, rl);
-            // 1 / sqrt(r^2): float estimate, one Newton step in float-float
-            const float2 y0 = make_float2(rsqrt_mufu(rh.x), rsqrt_mufu(rh.y));
-            // v = 1 - (rh + rl) y0^2: w + wl = rh y0 exactly, and 1 - w y0
-            // is small (y0 is good to ~2^-22), so one FMA forms it to ~2^-46
-            const float2 w = __fmul2_rn(rh, y0);
-            const float2 wl = __ffma2_rn(rh, y0, f2neg(w));
-            float2 v = __ffma2_rn(f2neg(w), y0, one);
-            v = __ffma2_rn(f2neg(wl), y0, v);
-            v = __ffma2_rn(f2neg(__fmul2_rn(rl, y0)), y0, v);
-            float2 yh, yl;
-            fast_two_sum2(y0, __fmul2_rn(__fmul2_rn(half, y0), v), yh, yl);
-            // s = m / r^3 (UM: 1 / r^3, the caller scales by m)
-            float2 p2, e2, sh, sl;
-            ff_sq(yh, yl, p2, e2);
+            // R = r^2 + eps^2 as the unnormalised pair (s3, err), |err| <= 2^-21 s3
+            const float2 err = __fadd2_rn(__fadd2_rn(__fadd2_rn(ex, ey), __fadd2_rn(ez, e2l)),
+                                          __fadd2_rn(__fadd2_rn(t1, t2), t3));
+            // s = R^(-3/2) from the float estimate y0 of 1 / sqrt(s3): with
+            // R y0^2 = 1 - v, R^(-3/2) = y0^3 (1 - v)^(-3/2) = y0^3 (1 + 3/2 v
+            // + 15/8 v^2 + O(v^3)), |v| ~ 2^-22.  v is formed from the exact
+            // square y0^2 = q + qe (one FMA each term: 1 - s3 q cancels
+            // exactly to ~2^-22 before it rounds), y0^3 = c + ce exactly to
+            // float-float, and the series factor goes into the low word.
+            const float2 y0 = make_float2(rsqrt_mufu(s3.x), rsqrt_mufu(s3.y));
+            const float2 qh = __fmul2_rn(y0, y0);
+            const float2 qe = __ffma2_rn(y0, y0, f2neg(qh));
+            float2 v = __ffma2_rn(f2neg(s3), qh, one);
+            v = __ffma2_rn(f2neg(s3), qe, v);
+            v = __ffma2_rn(f2neg(err), qh, v);
+            const float2 c3 = __fmul2_rn(qh, y0);
+            float2 ce = __ffma2_rn(qh, y0, f2neg(c3));
+            ce = __ffma2_rn(qe, y0, ce);
+            const float2 kv = __fmul2_rn(__ffma2_rn(v, c158, c32), v);
+            float2 sh, sl;
             if (UM) {
-                ff_mul(p2, e2, yh, yl, sh, sl);
+                sh = c3;
+                sl = __ffma2_rn(c3, kv, ce);
             } else {
-                float2 p3, e3;
-                ff_mul(p2, e2, yh, yl, p3, e3);
-                ff_mul(mjh, mjl, p3, e3, sh, sl);
+                ff_mul(mjh, mjl, c3, __ffma2_rn(c3, kv, ce), sh, sl);
             }
             if (MASK) {
                 const int j = j0 + jj;
