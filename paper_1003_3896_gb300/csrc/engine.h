@@ -79,6 +79,12 @@ struct ClusterSet {
     // concurrently in one pool must each have their own
     double *part = nullptr;
     int64_t part_elems = 0;
+    // launch order of the pair kernel's blocks for the decomposition of the
+    // last plan made (grid bperm_G over bperm_W units of width bperm_jt,
+    // i-blocks of bperm_ipb bodies; bperm_G = -1: none)
+    std::vector<uint16_t> bperm;
+    int64_t bperm_G = -1, bperm_W = -1;
+    int bperm_jt = 0, bperm_ipb = 0;
 };
 int set_create(ClusterSet &C, int32_t kcap, int64_t body_cap);
 // Give the set its own partial-sum storage of at least elems doubles, grown

@@ -225,7 +225,16 @@ struct HostTab {
     const int32_t *ntiles = nullptr;
     const float *eps2f = nullptr;
     const double *mu = nullptr;
+    // launch order of the blocks (NULL: their index order): launch position
+    // q runs block perm[q] of the decomposition, nperm = its grid
+    const uint16_t *perm = nullptr;
+    int32_t nperm = 0;
 };
+
+// Grids up to this many blocks launched by value with more than one cluster
+// carry a launch order in the parameter table (uint16 entries; the table of
+// PARAM_CLUSTERS clusters plus this stays inside the 32 KB parameter space).
+constexpr int PERM_CAP = 4096;
 
 // Partial slots per body at most, whatever the storage would allow.
 constexpr int64_t MAX_PART_SLOTS = 128;

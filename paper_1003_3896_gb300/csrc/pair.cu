@@ -92,9 +92,13 @@ struct Segment {
 };
 
 // Per-cluster values by value (kernel parameter): uniform across the block.
+// The widest table also carries the blocks' launch order (nperm = 0: index
+// order).
 template <int KC>
 struct ParamTab {
     int32_t K;
+    int32_t nperm;
+    uint16_t perm[KC >= PARAM_CLUSTERS ? PERM_CAP : 1];
     int64_t uoff[KC + 1];
     int64_t boff[KC];
     int64_t noff[KC];
@@ -103,6 +107,18 @@ struct ParamTab {
     int32_t ntiles[KC];
     float eps2f[KC];
 };
+
+// Block of the decomposition this launch position runs.  Launch position q
+// runs block perm[q] when the table carries an order (the host sorts the
+// blocks by estimated work, largest first, so the blocks launched last, which
+// set the kernel's tail, are the cheap ones); every block keeps its units and
+// partial slot, so the results do not depend on the order.
+template <int KC>
+__device__ __forceinline__ int64_t block_of(const ParamTab<KC> &t)
+{
+    if (KC >= PARAM_CLUSTERS && t.nperm > 0) return t.perm[blockIdx.x];
+    return blockIdx.x;
+}
 
 // largest k in [0, K) with off[k] <= t
 template <typename T>
@@ -114,6 +130,15 @@ __device__ __forceinline__ int32_t find_in(const T *off, int32_t K, int64_t t)
         if (off[mid] <= t) lo = mid; else hi = mid;
     }
     return lo;
+}
+
+// End of a unit's j range, clipped to the cluster's bodies rounded up to 32
+// (a whole warp chunk): the last j-tile of a cluster stops there instead of
+// running 128 wide over padding that adds exactly zero.
+__device__ __forceinline__ int32_t clip_j(int32_t J1, int32_t nk)
+{
+    const int32_t jend = (nk + 31) & ~31;
+    return J1 < jend ? J1 : jend;
 }
 
 template <int KC>
@@ -135,6 +160,7 @@ __device__ __forceinline__ Segment segment_at(const Decomp &d, const ParamTab<KC
     s.base = t.boff[s.k];
     s.lbase = t.noff[s.k];
     s.nk = t.nk[s.k];
+    s.J1 = clip_j(s.J1, s.nk);
     s.slot = g - d.owner(u0 + rb * nt);
     return s;
 }
@@ -157,6 +183,7 @@ __device__ __forceinline__ Segment segment_at(const Decomp &d, const Clusters &c
     s.base = c.boff[s.k];
     s.lbase = c.noff[s.k];
     s.nk = (int32_t)c.nk[s.k];
+    s.J1 = clip_j(s.J1, s.nk);
     s.slot = g - d.owner(u0 + rb * nt);
     return s;
 }
@@ -275,7 +302,7 @@ __global__ void __launch_bounds__(TILE, sp_min_blocks(P, MODE)) pair_sp_kernel(
     const int lane = tid & 31;
     const int w = tid >> 5;
     const float4(*cb)[4] = cbuf[w];
-    const int64_t g = blockIdx.x;
+    const int64_t g = block_of(tab);
     int64_t u = d.U(g);
     const int64_t uend = d.U(g + 1);
     const float4 far4 = make_float4(FAR_F, FAR_F, FAR_F, FAR_F);
@@ -591,7 +618,7 @@ __global__ void __launch_bounds__(TILE) pair_ff_kernel(
     const int lane = tid & 31;
     const int w = tid >> 5;
     const float4(*cb)[4] = cbuf[w];
-    const int64_t g = blockIdx.x;
+    const int64_t g = block_of(tab);
     int64_t u = d.U(g);
     const int64_t uend = d.U(g + 1);
     const float4 far4 = make_float4(FAR_F, FAR_F, FAR_F, FAR_F);
@@ -821,6 +848,10 @@ static cudaError_t launch_sp(const DevState &s, const PairLaunch &pl, const Host
     if (KC > 0) {
         if (ht.K > KC) return cudaErrorInvalidValue;
         t.K = ht.K;
+        if (KC >= PARAM_CLUSTERS && ht.perm && ht.nperm == pl.d.G && ht.nperm <= PERM_CAP) {
+            t.nperm = ht.nperm;
+            std::memcpy(t.perm, ht.perm, (size_t)ht.nperm * sizeof(uint16_t));
+        }
         for (int32_t q = 0; q < ht.K; ++q) {
             t.uoff[q] = ht.uoff[q];
             t.boff[q] = ht.boff[q];

@@ -40,7 +40,7 @@ def concat(cl):
             np.concatenate([c[2] for c in cl]))
 
 
-@pytest.mark.parametrize("prec", ["fp64", "ds", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "ds", "fp32", "dd"])
 def test_batch_accel_matches_oracle_and_alone(nbs, orc, prec):
     cl = clusters(SIZES)
     pos, vel, m = concat(cl)
@@ -50,7 +50,7 @@ def test_batch_accel_matches_oracle_and_alone(nbs, orc, prec):
         b.set_cluster_params(eps=eps)
         b.load(pos, vel, m)
         a = b.accel()
-    tol = {"fp64": 1e-12, "ds": 1e-6, "fp32": 1e-4}[prec]
+    tol = {"fp64": 1e-12, "ds": 1e-6, "fp32": 1e-4, "dd": 1e-12}[prec]
     off = 0
     for (p, v, mm, e), n in zip(cl, SIZES):
         ref = orc.accel_int(p, mm, 1.0, e)
@@ -63,7 +63,7 @@ def test_batch_accel_matches_oracle_and_alone(nbs, orc, prec):
             c.load(p, v, mm)
             alone = c.accel()
         # same arithmetic, different grouping of partial sums
-        assert rel_rms(got, alone) <= (1e-14 if prec == "fp64" else 1e-6)
+        assert rel_rms(got, alone) <= (1e-14 if prec in ("fp64", "dd") else 1e-6)
         off += n
 
 
