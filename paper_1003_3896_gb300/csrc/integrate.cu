@@ -419,7 +419,9 @@ __device__ __forceinline__ void ff_add(float &h, float &l, float p, float e)
 }
 
 // Float-pair partial sums (Decomp::fpart): added in slot order in
-// float-float arithmetic, SB loads at a time, then one conversion to double.
+// float-float arithmetic, SB loads at a time, then widened to double from
+// their bits (the conversion instruction runs on the FP64 pipe, 1/77 of the
+// FP32 rate here).
 template <int SB>
 __device__ __forceinline__ void sum_slots_ff(const DevState &s, int64_t count, int64_t t,
                                              double &ax, double &ay, double &az)
@@ -446,9 +448,9 @@ __device__ __forceinline__ void sum_slots_ff(const DevState &s, int64_t count, i
                 ff_add(hz, lz, bz[q].x, bz[q].y);
             }
     }
-    ax = (double)hx + (double)lx;
-    ay = (double)hy + (double)ly;
-    az = (double)hz + (double)lz;
+    ax = widen(hx) + widen(lx);
+    ay = widen(hy) + widen(ly);
+    az = widen(hz) + widen(lz);
 }
 
 template <int SB, bool FP>

@@ -39,4 +39,23 @@ __device__ __forceinline__ void split_ds(double r, float &hi, float &lo)
     lo = __fmul_rn(__int2float_rn(sign ? -d : d), scale);
 }
 
+// The double equal to float f, from its bits: the exponent rebiased, the
+// fraction shifted into place (exact).  Zeros come from the sign bit alone;
+// subnormal and non-finite f take the conversion instruction, which on this
+// GPU runs on the FP64 pipe.
+__device__ __forceinline__ double widen(float f)
+{
+    const unsigned int u = __float_as_uint(f);
+    const unsigned int e = (u >> 23) & 0xFFu;
+    if (e == 0u || e == 0xFFu) {
+        if ((u & 0x7FFFFFFFu) == 0u)
+            return __longlong_as_double((long long)((unsigned long long)u << 32));
+        return (double)f;
+    }
+    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e + 896u) << 52) |
+                                 ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
 }  // namespace nb

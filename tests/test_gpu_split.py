@@ -2,8 +2,11 @@
 against the plain conversions hi = RN_float(r), lo = RN_float(r - hi), bit for
 bit, on the GPU: random doubles over the whole fast-path exponent range and
 both fallbacks, round-to-even ties of either parity, roundings that carry into
-the exponent, signed zeros, subnormals, infinities and NaN."""
+the exponent, signed zeros, subnormals, infinities and NaN.  The widening of
+a float to double from its bits against the conversion instruction, on every
+one of the 2^32 float bit patterns."""
 import os
+import re
 import shutil
 import subprocess
 
@@ -35,6 +38,21 @@ __global__ void check(const double *r, int n, unsigned long long *bad, int *firs
     if (!(same_h && same_l)) {
         atomicAdd(bad, 1ull);
         atomicMin(first, t);
+    }
+}
+
+__global__ void check_widen(unsigned long long *bad, unsigned int *first)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < (1ull << 32);
+         u += stride) {
+        const float f = __uint_as_float((unsigned int)u);
+        const double a = nb::widen(f), b = (double)f;
+        const bool same = __double_as_longlong(a) == __double_as_longlong(b) || (a != a && b != b);
+        if (!same) {
+            atomicAdd(bad, 1ull);
+            atomicMin(first, (unsigned int)u);
+        }
     }
 }
 
@@ -92,7 +110,18 @@ int main()
         std::memcpy(&b, &v[first], 8);
         std::printf("first mismatch bits %016llx\n", (unsigned long long)b);
     }
-    return bad ? 1 : 0;
+    unsigned long long wbad = 0;
+    unsigned int wfirst = 0xFFFFFFFFu;
+    cudaMemset(d_bad, 0, 8);
+    unsigned int *d_wfirst = nullptr;
+    if (cudaMalloc(&d_wfirst, 4)) return 2;
+    cudaMemcpy(d_wfirst, &wfirst, 4, cudaMemcpyHostToDevice);
+    check_widen<<<152 * 16, 256>>>(d_bad, d_wfirst);
+    if (cudaMemcpy(&wbad, d_bad, 8, cudaMemcpyDeviceToHost) ||
+        cudaMemcpy(&wfirst, d_wfirst, 4, cudaMemcpyDeviceToHost))
+        return 3;
+    std::printf("widen checked 4294967296 mismatches %llu first %08x\n", wbad, wfirst);
+    return (bad || wbad) ? 1 : 0;
 }
 """
 
@@ -106,4 +135,5 @@ def test_split_matches_plain_conversions(tmp_path):
                     "-I", CSRC, str(src), "-o", str(exe)], check=True)
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
-    assert "mismatches 0" in r.stdout
+    assert re.search(r"^checked \d+ mismatches 0 first", r.stdout, re.M), r.stdout
+    assert "widen checked 4294967296 mismatches 0 first" in r.stdout, r.stdout
