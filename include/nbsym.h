@@ -426,7 +426,8 @@ void nb_destroy(nb_ctx *ctx);
  * same step (Sect. 3.1).  A scheduler thread admits queued jobs in arrival
  * order when a resident-job slot is free and the state pool (sized from the
  * HBM budget) has a contiguous range for the job's bodies.  Resident jobs are
- * grouped by (precision, order, and size: below 16384 bodies or not); each
+ * grouped by (precision, order, and size: below 16384 bodies or not; the
+ * groups of smaller jobs run on higher-priority streams); each
  * group advances one step at a time with
  * one pair-kernel launch per force evaluation covering all its jobs, on its
  * own stream, so groups overlap on the device.  Jobs join and leave a group

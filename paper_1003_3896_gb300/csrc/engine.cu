@@ -105,7 +105,7 @@ namespace {
 inline size_t al(size_t b) { return (b + 255) / 256 * 256; }
 }
 
-int set_create(ClusterSet &C, int32_t kcap, int64_t body_cap)
+int set_create(ClusterSet &C, int32_t kcap, int64_t body_cap, int priority)
 {
     C.kcap = kcap;
     C.scap = (body_cap + SEG_BODIES - 1) / SEG_BODIES + kcap;
@@ -145,7 +145,7 @@ int set_create(ClusterSet &C, int32_t kcap, int64_t body_cap)
         set_destroy(C);
         return set_error(NB_ENOMEM, "cluster tables: device allocation failed");
     }
-    if (cudaStreamCreateWithFlags(&C.side, cudaStreamNonBlocking) != cudaSuccess ||
+    if (cudaStreamCreateWithPriority(&C.side, cudaStreamNonBlocking, priority) != cudaSuccess ||
         cudaEventCreateWithFlags(&C.fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&C.join, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();

@@ -86,7 +86,9 @@ struct ClusterSet {
     int64_t bperm_G = -1, bperm_W = -1;
     int bperm_jt = 0, bperm_ipb = 0;
 };
-int set_create(ClusterSet &C, int32_t kcap, int64_t body_cap);
+// priority: of the set's side stream (the near-pair pass), as for the stream
+// its steps are enqueued on (0: the default).
+int set_create(ClusterSet &C, int32_t kcap, int64_t body_cap, int priority = 0);
 // Give the set its own partial-sum storage of at least elems doubles, grown
 // (stream-ordered allocation on st) when smaller; none of the set's work may
 // be in flight.

@@ -15,7 +15,12 @@
 // in lockstep, so jobs below SMALL_JOB bodies are grouped apart from larger
 // ones: a small job then waits at each step for other small jobs only, not
 // for a step of a 131072-body job (on the bounded serving trace this lowered
-// the median latency by 7-11% at the same throughput).
+// the median latency by 7-11% at the same throughput).  The small jobs'
+// groups enqueue on streams of the device's greatest priority, the others on
+// its least: when both have kernels ready, the block scheduler hands SMs to
+// the small jobs' blocks first, which approximates shortest job first on the
+// device (bounded trace: median latency 6.3-6.6 -> 3.5-3.7 s, p99 and
+// throughput unchanged or slightly better).
 //
 // Up to two steps of a group are in flight: the next one is enqueued while
 // the current one runs whenever no member finishes at the current one and no
@@ -445,12 +450,16 @@ int nb_server_create(const nb_server_params *p, nb_server **out)
     }
     s->cap = cap;
     int rc = pool_create(s->pool, p->device, cap, /*own_part=*/false);
+    int least = 0, greatest = 0;
+    if (!rc && cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess)
+        rc = set_error(NB_ECUDA, "stream priority query failed");
     for (int g = 0; g < NGROUPS && !rc; ++g) {
         Group &gr = s->groups[g];
         gr.precision = g < 4 ? NB_FP64 : (g < 8 ? NB_DS : NB_DD);
         gr.order = (g & 2) ? 6 : 2;
-        rc = set_create(gr.set, p->max_jobs, cap);
-        if (!rc && cudaStreamCreateWithFlags(&gr.stream, cudaStreamNonBlocking) != cudaSuccess)
+        const int prio = (g & 1) ? least : greatest;   // the small jobs' groups first
+        rc = set_create(gr.set, p->max_jobs, cap, prio);
+        if (!rc && cudaStreamCreateWithPriority(&gr.stream, cudaStreamNonBlocking, prio) != cudaSuccess)
             rc = set_error(NB_ECUDA, "stream creation failed");
         for (StepSlot &sl : gr.slot) {
             if (!rc && cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess)
