@@ -451,7 +451,7 @@ int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan
     }
     int rc = set_layout(C, TILE * I, st, jt);
     if (rc) return rc;
-    pl.pl.um = pl.pl.mode != PM_FP64;
+    pl.pl.um = true;
     for (int32_t k = 0; k < C.K && pl.pl.um; ++k) pl.pl.um = C.mu[k] > 0;
     const int64_t W = C.uoff[C.K];
     int64_t G = want < W ? want : W;   // at least one unit per block

@@ -202,8 +202,8 @@ struct PairLaunch {
     int I;           // i-bodies per thread
     int blocks_per_sm;
     Decomp d;
-    // every cluster has equal masses (mu[k] > 0): the single-precision
-    // kernels leave m out of the pair term and scale the sums by mu[k]
+    // every cluster has equal masses (mu[k] > 0): the pair kernels leave m
+    // out of the pair term and scale the sums by mu[k]
     bool um = false;
 };
 

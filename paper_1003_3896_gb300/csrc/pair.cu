@@ -34,6 +34,7 @@
 #include <cstring>
 
 #include "nb_internal.cuh"
+#include "split.cuh"
 
 namespace nb {
 
@@ -710,13 +711,43 @@ __global__ void __launch_bounds__(TILE) pair_ff_kernel(
     }
 }
 
+// R^(-1/2) (POT) or R^(-3/2) in double for R >= 0, refined from the float
+// estimate y0 = rsqrt.approx(R_f): R_f is R truncated to float and y0 is
+// widened to double, both from their bits (the conversion instructions would
+// run on the FP64 pipe, which bounds this kernel).  With R y0^2 = 1 - v,
+// |v| < 2^-20 (the estimate's error and the truncation's),
+//     R^(-1/2) = y0 (1 + v/2 + 3 v^2 / 8 + O(v^3)),
+//     R^(-3/2) = y0^3 (1 + 3 v / 2 + 15 v^2 / 8 + O(v^3)),
+// the dropped terms below 2^-58 relative; y0^2 is exact (y0 has 24 bits) and
+// v is one fused multiply-add, so 5 or 6 FP64 operations replace the double
+// rsqrt and the cube.  R outside the float range (the padding's 1e300, R = 0,
+// non-finite R) takes the library rsqrt.
+template <bool POT>
+__device__ __forceinline__ double rsqrt_pow(double R)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(R);
+    const int E = (int)(b >> 52);   // R >= 0: the sign bit is clear
+    if (E < 1023 - 125 || E > 1023 + 126) {
+        const double ri = rsqrt(R);
+        return POT ? ri : ri * ri * ri;
+    }
+    const float rf = __int_as_float(((E - 1023 + 127) << 23) | (int)((b >> 29) & 0x7FFFFFu));
+    const double y0 = widen(rsqrt_mufu(rf));
+    const double q = __dmul_rn(y0, y0);
+    const double v = __fma_rn(-R, q, 1.0);
+    if (POT) return __fma_rn(y0, __dmul_rn(v, __fma_rn(v, 0.375, 0.5)), y0);
+    const double y3 = __dmul_rn(q, y0);
+    return __fma_rn(y3, __dmul_rn(v, __fma_rn(v, 1.875, 1.5)), y3);
+}
+
 // Double-precision pair kernel: the plain FP64 baseline (Sect. 4.2's DP mode
 // with structures of four doubles).  The block's j-range is staged through
 // shared memory up to TILE bodies at a time and broadcast to the threads'
-// i bodies.  With POT
-// it sums the softened potential m_j / sqrt(r^2 + eps^2) of eq. 4 instead
-// (j = i always excluded), for the energy diagnostic.
-template <int I, bool POT>
+// i bodies.  With POT it sums the softened potential m_j / sqrt(r^2 + eps^2)
+// of eq. 4 instead (j = i always excluded), for the energy diagnostic.  UM
+// (all masses of the cluster equal): the pair term is d / r^3 without m_j,
+// one multiply fewer on the FP64 pipe; the sums are scaled by G m.
+template <int I, bool POT, bool UM = false>
 __global__ void __launch_bounds__(TILE) pair_fp64_kernel(
     const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
     const double *__restrict__ m, Clusters c, Decomp d, double G, double *__restrict__ part,
@@ -774,13 +805,12 @@ __global__ void __launch_bounds__(TILE) pair_fp64_kernel(
                     double r2 = fma(dx, dx, eps2);
                     r2 = fma(dy, dy, r2);
                     r2 = fma(dz, dz, r2);
-                    const double ri = rsqrt(r2);
                     if (POT) {
-                        double wgt = mj * ri;
+                        double wgt = mj * rsqrt_pow<true>(r2);
                         if (diag && jglob + jj == idx[k]) wgt = 0.0;
                         ax[k] += wgt;
                     } else {
-                        double s = (mj * ri) * (ri * ri);
+                        double s = UM ? rsqrt_pow<false>(r2) : mj * rsqrt_pow<false>(r2);
                         if (diag && jglob + jj == idx[k]) s = 0.0;
                         ax[k] = fma(dx, s, ax[k]);
                         ay[k] = fma(dy, s, ay[k]);
@@ -789,6 +819,7 @@ __global__ void __launch_bounds__(TILE) pair_fp64_kernel(
                 }
             }
         }
+        const double Gm = UM ? G * c.mu[sg.k] : G;   // UM: the cluster's common mass
 #pragma unroll
         for (int k = 0; k < I; ++k) {
             const int i = idx[k];
@@ -797,9 +828,9 @@ __global__ void __launch_bounds__(TILE) pair_fp64_kernel(
                 if (POT) {
                     p[0] = ax[k];
                 } else {
-                    p[0] = G * ax[k];
-                    p[ps] = G * ay[k];
-                    p[2 * ps] = G * az[k];
+                    p[0] = Gm * ax[k];
+                    p[ps] = Gm * ay[k];
+                    p[2 * ps] = Gm * az[k];
                 }
             }
         }
@@ -868,10 +899,10 @@ static cudaError_t launch_sp(const DevState &s, const PairLaunch &pl, const Host
     return cudaGetLastError();
 }
 
-static dp_kernel_t dp_variant(int I)
+static dp_kernel_t dp_variant(int I, bool um = false)
 {
-    if (I == 1) return pair_fp64_kernel<1, false>;
-    if (I == 2) return pair_fp64_kernel<2, false>;
+    if (I == 1) return um ? pair_fp64_kernel<1, false, true> : pair_fp64_kernel<1, false>;
+    if (I == 2) return um ? pair_fp64_kernel<2, false, true> : pair_fp64_kernel<2, false>;
     return nullptr;
 }
 
@@ -907,7 +938,7 @@ cudaError_t launch_pair(const DevState &s, const PairLaunch &pl, const HostTab &
                         cudaStream_t st)
 {
     if (pl.mode == PM_FP64) {
-        dp_kernel_t k = dp_variant(pl.I);
+        dp_kernel_t k = dp_variant(pl.I, pl.um);
         if (!k) return cudaErrorInvalidValue;
         k<<<(unsigned)pl.d.G, TILE, 0, st>>>(s.x, s.y, s.z, s.m, s.cl, pl.d, G, s.part,
                                              s.pstride);
