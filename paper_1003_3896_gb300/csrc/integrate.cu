@@ -55,19 +55,16 @@ __device__ __forceinline__ BodyRef body_at(const Clusters &c, int64_t t)
 __device__ __forceinline__ void field_accel(const ExtField &e, double x, double y, double z,
                                             double &ax, double &ay, double &az)
 {
+    // the inverse square-root powers refined in double from float estimates
+    // (split.cuh: the FP64 pipe carries the kick here)
     const double R2 = x * x + y * y;
     const double s2 = z * z + e.bd * e.bd;
-    const double rs = rsqrt(s2);                 // 1 / sqrt(z^2 + bd^2)
+    const double rs = rsqrt_pow<true>(s2);       // 1 / sqrt(z^2 + bd^2)
     const double q = e.ad + s2 * rs;             // ad + sqrt(z^2 + bd^2)
-    const double rD = rsqrt(R2 + q * q);
-    const double kd = e.G * e.Md * (rD * rD * rD);
-    const double rB = rsqrt(R2 + z * z + e.ab * e.ab);
-    const double kb = e.G * e.Mb * (rB * rB * rB);
+    const double kd = e.G * e.Md * rsqrt_pow<false>(R2 + q * q);
+    const double kb = e.G * e.Mb * rsqrt_pow<false>(R2 + z * z + e.ab * e.ab);
     double kh = 0.0;   // softened central point mass
-    if (e.Mbh > 0) {
-        const double rH = rsqrt(R2 + z * z + e.eps2bh);
-        kh = e.G * e.Mbh * (rH * rH * rH);
-    }
+    if (e.Mbh > 0) kh = e.G * e.Mbh * rsqrt_pow<false>(R2 + z * z + e.eps2bh);
     ax = -(kd + kb + kh) * x;
     ay = -(kd + kb + kh) * y;
     az = -(kd * q * rs + kb + kh) * z;

@@ -1,5 +1,8 @@
 // split.cuh -- double-single split of a double (the paper's hi + lo
-// coordinate format, Sect. 5.2) from its bits.
+// coordinate format, Sect. 5.2) from its bits, the widening of a float from
+// its bits, and inverse square-root powers in double refined from a float
+// estimate: arithmetic kept off the FP64 pipe, which on this GPU runs at 1/77
+// of the FP32 rate.
 #pragma once
 
 namespace nb {
@@ -56,6 +59,38 @@ __device__ __forceinline__ double widen(float f)
                                  ((unsigned long long)(e + 896u) << 52) |
                                  ((unsigned long long)(u & 0x7FFFFFu) << 29);
     return __longlong_as_double((long long)b);
+}
+
+// R^(-1/2) (POT) or R^(-3/2) in double for R >= 0, refined from the float
+// estimate y0 = rsqrt.approx(R_f): R_f is R truncated to float and y0 is
+// widened to double, both from their bits (the conversion instructions would
+// run on the FP64 pipe, which bounds the FP64 pair kernel and the kick's
+// field).  With R y0^2 = 1 - v, |v| < 2^-20 (the estimate's error and the
+// truncation's),
+//     R^(-1/2) = y0 (1 + v/2 + 3 v^2 / 8 + O(v^3)),
+//     R^(-3/2) = y0^3 (1 + 3 v / 2 + 15 v^2 / 8 + O(v^3)),
+// the dropped terms below 2^-58 relative; y0^2 is exact (y0 has 24 bits) and
+// v is one fused multiply-add, so 5 or 6 FP64 operations replace the double
+// rsqrt and the cube.  R outside the float range (the padding's 1e300, R = 0,
+// non-finite R) takes the library rsqrt.
+template <bool POT>
+__device__ __forceinline__ double rsqrt_pow(double R)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(R);
+    const int E = (int)(b >> 52);   // R >= 0: the sign bit is clear
+    if (E < 1023 - 125 || E > 1023 + 126) {
+        const double ri = rsqrt(R);
+        return POT ? ri : ri * ri * ri;
+    }
+    const float rf = __int_as_float(((E - 1023 + 127) << 23) | (int)((b >> 29) & 0x7FFFFFu));
+    float yf;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(rf));
+    const double y0 = widen(yf);
+    const double q = __dmul_rn(y0, y0);
+    const double v = __fma_rn(-R, q, 1.0);
+    if (POT) return __fma_rn(y0, __dmul_rn(v, __fma_rn(v, 0.375, 0.5)), y0);
+    const double y3 = __dmul_rn(q, y0);
+    return __fma_rn(y3, __dmul_rn(v, __fma_rn(v, 1.875, 1.5)), y3);
 }
 
 }  // namespace nb
