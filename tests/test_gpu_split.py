@@ -137,3 +137,75 @@ def test_split_matches_plain_conversions(tmp_path):
     assert r.returncode == 0, r.stdout + r.stderr
     assert re.search(r"^checked \d+ mismatches 0 first", r.stdout, re.M), r.stdout
     assert "widen checked 4294967296 mismatches 0 first" in r.stdout, r.stdout
+
+
+RSQ_SRC = r"""
+#include <cmath>
+#include <cstdio>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#include <cuda_runtime.h>
+#include "split.cuh"
+
+__global__ void powers(const double *r, int n, double *p1, double *p3)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    p1[t] = nb::rsqrt_pow<true>(r[t]);
+    p3[t] = nb::rsqrt_pow<false>(r[t]);
+}
+
+int main()
+{
+    std::vector<double> v;
+    uint64_t s = 0x2545F4914F6CDD1Dull;
+    auto next = [&]() { s ^= s << 13; s ^= s >> 7; s ^= s << 17; return s; };
+    for (int k = 0; k < 400000; ++k) {   // log-uniform over [1e-30, 1e30]
+        const double u = (double)(next() >> 11) / 9007199254740992.0;
+        v.push_back(std::pow(10.0, -30.0 + 60.0 * u));
+    }
+    // both ends of the float-estimate path and beyond it (library fallback)
+    for (double e : {-125.0, -124.0, 125.0, 126.0, 127.0, -126.0, -127.0, 200.0, -200.0})
+        for (int k = -3; k <= 3; ++k) v.push_back(std::ldexp(1.0 + k * 1e-3, (int)e));
+    const int n = (int)v.size();
+    double *d_r, *d_1, *d_3;
+    if (cudaMalloc(&d_r, 8 * n) || cudaMalloc(&d_1, 8 * n) || cudaMalloc(&d_3, 8 * n)) return 2;
+    cudaMemcpy(d_r, v.data(), 8 * n, cudaMemcpyHostToDevice);
+    powers<<<(n + 255) / 256, 256>>>(d_r, n, d_1, d_3);
+    std::vector<double> p1(n), p3(n);
+    if (cudaMemcpy(p1.data(), d_1, 8 * n, cudaMemcpyDeviceToHost) ||
+        cudaMemcpy(p3.data(), d_3, 8 * n, cudaMemcpyDeviceToHost))
+        return 3;
+    double worst1 = 0, worst3 = 0;
+    for (int k = 0; k < n; ++k) {
+        const long double R = v[k], e1 = 1.0L / std::sqrt(R), e3 = e1 * e1 * e1;
+        const double u1 = (double)std::fabs((p1[k] - e1) / e1) / 0x1p-53;
+        const double u3 = (double)std::fabs((p3[k] - e3) / e3) / 0x1p-53;
+        if (u1 > worst1) worst1 = u1;
+        if (u3 > worst3) worst3 = u3;
+    }
+    std::printf("rsqrt powers checked %d worst ulp R^-1/2 %.3f R^-3/2 %.3f\n", n, worst1, worst3);
+    return 0;
+}
+"""
+
+
+def test_rsqrt_powers_against_long_double(tmp_path):
+    """The FP64 pair kernel's and the field's R^(-1/2) and R^(-3/2) (float
+    estimate, series refinement in double): within 2.5 and 4.5 units of 2^-53
+    of a long-double evaluation (quad precision on the GPU host's Arm
+    toolchain) over 60 decades, the float-range edges and the library
+    fallback beyond them (a CPU emulation of the refinement gave 1.5 and 3.3;
+    a wrong series coefficient gives thousands)."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    src = tmp_path / "rsq_check.cu"
+    src.write_text(RSQ_SRC)
+    exe = tmp_path / "rsq_check"
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-std=c++17",
+                    "-I", CSRC, str(src), "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    m = re.search(r"worst ulp R\^-1/2 ([0-9.]+) R\^-3/2 ([0-9.]+)", r.stdout)
+    assert m, r.stdout
+    assert float(m.group(1)) <= 2.5 and float(m.group(2)) <= 4.5, r.stdout
