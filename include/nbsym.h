@@ -450,7 +450,7 @@ typedef struct {
     double Mbh, eps_bh;       /* as nb_params */
     int fp64_via_dd;          /* 1 (default): jobs submitted as NB_FP64 run the
                                  NB_DD (float-float) arithmetic, which meets the
-                                 FP64 tolerance at ~9x the FP64 pipe's rate (this
+                                 FP64 tolerance at ~8x the FP64 kernel's rate (this
                                  GPU's FP64 pipe runs at 1/77 of its FP32 rate);
                                  0: the plain FP64 kernel */
 } nb_server_params;
