@@ -351,7 +351,7 @@ bool float_planes(int precision) { return precision != NB_FP64; }
 // of the j-stream loads; each segment (a run of one i-block's units) adds
 // the cost of 16 j of a full i-block for its set-up and write-out.  Only the
 // order depends on these estimates: any order gives the same sums.
-static void block_order(ClusterSet &C, const Decomp &d, int I, bool partial)
+void block_order(ClusterSet &C, const Decomp &d, int I, bool partial)
 {
     const int64_t G = d.G;
     const double full = (TILE / 32) * (I / 2 + 0.5);

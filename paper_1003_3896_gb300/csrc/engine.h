@@ -89,6 +89,11 @@ struct ClusterSet {
 // priority: of the set's side stream (the near-pair pass), as for the stream
 // its steps are enqueued on (0: the default).
 int set_create(ClusterSet &C, int32_t kcap, int64_t body_cap, int priority = 0);
+// Launch order of the pair kernel's blocks for decomposition d over C's
+// clusters (host only; fills C.bperm, a permutation of [0, d.G), and its key):
+// largest estimated work first.  I: bodies per thread; partial: the kernel
+// evaluates only the packed i-pairs that hold bodies.
+void block_order(ClusterSet &C, const Decomp &d, int I, bool partial);
 // Give the set its own partial-sum storage of at least elems doubles, grown
 // (stream-ordered allocation on st) when smaller; none of the set's work may
 // be in flight.
