@@ -471,7 +471,9 @@ int nb_server_create(const nb_server_params *p, nb_server **out)
         }
     }
     if (!rc) rc = set_create(s->io, 1, cap);
-    if (!rc && cudaStreamCreateWithFlags(&s->io_stream, cudaStreamNonBlocking) != cudaSuccess)
+    // uploads and downloads are synchronised by the scheduler thread, which
+    // feeds no group while it waits: their pack / unpack kernels go first
+    if (!rc && cudaStreamCreateWithPriority(&s->io_stream, cudaStreamNonBlocking, greatest) != cudaSuccess)
         rc = set_error(NB_ECUDA, "stream creation failed");
     if (!rc && (cudaEventCreate(&s->ref) != cudaSuccess ||
                 cudaEventRecord(s->ref, s->io_stream) != cudaSuccess ||
