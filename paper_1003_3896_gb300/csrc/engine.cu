@@ -400,7 +400,7 @@ void block_order(ClusterSet &C, const Decomp &d, int I, bool partial)
 }
 
 int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan &out,
-              const PairShape *force, bool use_table)
+              const PairShape *force, bool use_table, int waves)
 {
     Plan pl;
     pl.precision = precision;
@@ -436,6 +436,7 @@ int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan
     pl.pl.I = I;
     int occ = pair_occupancy(pl.pl.mode, I);
     if (occ < 1) occ = 1;
+    if (waves > 0) bps = (waves < MAX_WAVES ? waves : MAX_WAVES) * occ;
     pl.pl.blocks_per_sm = bps > 0 ? (bps < MAX_WAVES * occ ? bps : MAX_WAVES * occ)
                                   : DEFAULT_WAVES * occ;
     const int64_t want = (int64_t)P.num_sms * pl.pl.blocks_per_sm;

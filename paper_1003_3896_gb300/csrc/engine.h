@@ -133,8 +133,11 @@ struct PairShape {
 // Choose the pair kernel variant and decompositions for a cluster set and
 // lay the set out for it.  The shape is `force` when given, else the tuned
 // entry for the set's shape (when use_table), else the built-in heuristic.
+// waves > 0: that many waves of resident blocks whatever the shape's own
+// grid (the bodies per thread still come from force, the table or the
+// heuristic).
 int plan_make(const Pool &P, ClusterSet &C, int precision, cudaStream_t st, Plan &out,
-              const PairShape *force = nullptr, bool use_table = true);
+              const PairShape *force = nullptr, bool use_table = true, int waves = 0);
 
 // ---- autotuner (tune.cu) -----------------------------------------------------
 struct TuneKey {

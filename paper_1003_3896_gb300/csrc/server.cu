@@ -316,17 +316,12 @@ int launch_step(nb_server *s, Group &g)
         g.set.mu = mu;
         // the group's own partial sums: groups step concurrently
         if (!rc) rc = set_reserve_part(g.set, part_elems_for(s->pool, g.set.n), g.stream);
-        if (!rc) rc = plan_make(s->pool, g.set, g.precision, g.stream, g.plan);
-        if (!rc && ((&g - s->groups) & 1)) {
-            // the large jobs' groups: the most waves, so their blocks are
-            // short and free SM slots for the small jobs' kernels sooner
-            const int occ = pair_occupancy(g.plan.pl.mode, g.plan.pl.I);
-            PairShape sh;
-            sh.I = g.plan.pl.I;
-            sh.blocks_per_sm = MAX_WAVES * (occ > 0 ? occ : 1);
-            sh.jt = 0;
-            rc = plan_make(s->pool, g.set, g.precision, g.stream, g.plan, &sh, false);
-        }
+        // the large jobs' groups: the most waves, so their blocks are short
+        // and free SM slots for the small jobs' kernels sooner
+        const bool large = ((&g - s->groups) & 1) != 0;
+        if (!rc)
+            rc = plan_make(s->pool, g.set, g.precision, g.stream, g.plan, nullptr, true,
+                           large ? MAX_WAVES : 0);
         if (rc) return rc;
         g.dirty = false;
     }
